@@ -1,0 +1,211 @@
+/*
+ * hmat.h — C ABI of the GB300 (sm_103a) biquaternion matrix-product library.
+ *
+ * Operation (arXiv 2609.02081, "Biquaternion Algebra with Bilinear
+ * Multiplication"):
+ *
+ *     C <- alpha * op(A) * op(B) + beta * C
+ *
+ * for matrix-valued biquaternions, computed with the paper's bilinear scheme
+ * (Sec. III B, Eq. bilinearH with Gauss's three-product complex
+ * multiplication, Eq. cmplx-3-real-mult): 24 real matrix products in place of
+ * the component-wise 64, fewer when subalgebra flags mark components absent.
+ *
+ * Storage (Sec. III, Eq. biquat-repres): a rows x cols biquaternion matrix is
+ * eight real FP64 matrices [M1..M8] = [E_R, E_I, F_R, F_I, G_I, -G_R, H_I,
+ * -H_R]; the complex coefficient of basis element 1, i, j, k is
+ * q_e = M_e + i M_{e+4} (Eq. main-biquat-eqn).  Here component c (0-based)
+ * starts at ptr + c * stride and element (r, q) of that component is at
+ * r * ld + q (row-major), all offsets counted in doubles.  A is stored m x k
+ * for op N, C, QC and k x m for op T, H; likewise B is k x n or n x k; C is
+ * m x n.  Requirements: ld >= stored column count, stride >= rows * ld when
+ * the components do not overlap (overlap is the caller's business), pointers
+ * 8-byte aligned.
+ *
+ * Ownership: the caller owns every device buffer (A, B, C, workspace) and the
+ * CUDA stream; the library owns only its handle.  Calls are asynchronous on
+ * the given stream (a cudaStream_t passed as void*, NULL = legacy default
+ * stream).  Pointers A, B, C and workspace are DEVICE pointers.
+ *
+ * Errors: every call returns an hmat_status; argument errors are detected on
+ * the host before any launch and launch nothing.  No C++ exception crosses
+ * this ABI.  Device-side bounded waits that give up set a device error word
+ * that hmat_get_device_error() reads and clears.
+ */
+#ifndef HMAT_H
+#define HMAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HMAT_STATUS_SUCCESS = 0,
+    HMAT_STATUS_INVALID_VALUE = 1,      /* bad size, op, flag, mode or pointer */
+    HMAT_STATUS_UNSUPPORTED = 2,        /* valid request this build cannot serve */
+    HMAT_STATUS_MISALIGNED = 3,         /* a pointer or stride violates alignment */
+    HMAT_STATUS_WORKSPACE_TOO_SMALL = 4,/* workspace smaller than hmat_workspace_size() */
+    HMAT_STATUS_CUDA_ERROR = 5,         /* a CUDA runtime call failed */
+    HMAT_STATUS_DEVICE_TIMEOUT = 6,     /* a bounded device wait gave up */
+    HMAT_STATUS_NOT_INITIALIZED = 7,    /* NULL or destroyed handle */
+    HMAT_STATUS_TOLERANCE_UNREACHABLE = 8, /* split mode cannot promise tol */
+    HMAT_STATUS_INTERNAL = 9
+} hmat_status;
+
+/* op(X): a sign per stored component plus, for T and H, a transposition of
+ * every component (Sec. III transposition, complex-conjugation and
+ * Hermitian-conjugation equations).  QC is the quaternion conjugate
+ * q1 - q2 i - q3 j - q4 k (vector part negated, no transposition). */
+typedef enum {
+    HMAT_OP_N = 0,   /* X                                   */
+    HMAT_OP_T = 1,   /* X^T       [+,+,-,+,+,+,-,+], transposed */
+    HMAT_OP_C = 2,   /* X^*       [+,-,+,-,-,+,-,+]        */
+    HMAT_OP_H = 3,   /* X^dagger  [+,-,-,-,-,+,+,+], transposed */
+    HMAT_OP_QC = 4   /* X-bar     [+,-,-,-,+,-,-,-]        */
+} hmat_op;
+
+/* Component activity flags: bit c-1 set = stored component c present
+ * (the paper's [1,0,0,0,0,0,0,0] ... [1,1,1,1,1,1,1,1] notation, Tables I-II).
+ * Absent components are never read (their memory may hold anything) and the
+ * product terms they would feed are omitted (Sec. III B, last paragraph).
+ * Any 8-bit pattern is accepted; the named ones are the subalgebras. */
+enum {
+    HMAT_REAL = 0x01,     /* real matrix                         */
+    HMAT_COMPLEX = 0x11,  /* complex matrix                      */
+    HMAT_TRS = 0x0F,      /* real quaternion (time-reversal symmetric)   */
+    HMAT_TRA = 0xF0,      /* i * real quaternion (time-reversal antisymmetric) */
+    HMAT_BQ = 0xFF        /* full biquaternion                   */
+};
+
+typedef enum {
+    /* Plain FP64: the bilinear products in FP64 arithmetic, pre-additions in
+     * the GEMM prologue and the recombination in its epilogue. Needs no
+     * workspace. */
+    HMAT_MODE_FP64 = 0,
+    /* Split precision (Ozaki-type, integer modular): op(A), op(B) scaled by
+     * per-row / per-column powers of two and rounded to integers; the
+     * bilinear products run as exact BF16 tensor-core (tcgen05) GEMMs on
+     * residues modulo several small coprime moduli, with FP32 accumulation
+     * kept exact; the Chinese remainder theorem recovers the exact integer
+     * products, which are rescaled in FP64.  The only rounding is the initial
+     * scaling to integers, sized from `tol` (target relative Frobenius error).
+     * Needs workspace. */
+    HMAT_MODE_SPLIT = 1
+} hmat_mode;
+
+typedef struct hmat_context *hmat_handle;
+
+/* One product C <- alpha op(A) op(B) + beta C for the grouped call. */
+typedef struct {
+    int32_t opA, opB;           /* hmat_op                                  */
+    uint32_t flagsA, flagsB;    /* component activity flags                 */
+    int64_t m, n, k;            /* op(A) is m x k, op(B) is k x n           */
+    double alpha_re, alpha_im;  /* complex alpha                            */
+    double beta_re, beta_im;    /* complex beta; beta == 0: C is not read   */
+    const double *A; int64_t lda; int64_t strideA;
+    const double *B; int64_t ldb; int64_t strideB;
+    double *C;       int64_t ldc; int64_t strideC;
+} hmat_gemm_desc;
+
+/* Library version as major*10000 + minor*100 + patch. */
+int32_t hmat_version(void);
+
+/* Text for a status code (static storage, never NULL). */
+const char *hmat_status_string(hmat_status s);
+
+/* Create a handle bound to the current CUDA device.  Allocates host-side
+ * state only (pinned staging for grouped descriptors).  Errors:
+ * INVALID_VALUE (NULL out pointer), CUDA_ERROR. */
+hmat_status hmat_create(hmat_handle *handle);
+
+/* Destroy a handle (NULL is accepted).  Synchronises nothing; the caller
+ * must not destroy a handle whose work is still queued on a stream. */
+hmat_status hmat_destroy(hmat_handle handle);
+
+/* Workspace bytes that hmat_bq_gemm / hmat_bq_gemm_grouped need for these
+ * problems in this mode (0 for FP64).  descs is a HOST array of `count`
+ * descriptors (only op, flags, m, n, k are read).  tol: as for the call. */
+hmat_status hmat_workspace_size(hmat_handle handle, int32_t count,
+                                const hmat_gemm_desc *descs, int32_t mode,
+                                double tol, size_t *bytes);
+
+/* C <- alpha op(A) op(B) + beta C  (Sec. III B; storage, ops, flags above).
+ *   mode: hmat_mode.  tol: split-mode target relative Frobenius error of the
+ *   result (ignored for FP64; 0 means 1e-12).  workspace/workspace_bytes: a
+ *   device buffer of at least hmat_workspace_size() bytes, 256-byte aligned
+ *   (may be NULL/0 for FP64).  stream: cudaStream_t or NULL.
+ * m, n or k == 0 returns SUCCESS after, for k == 0, scaling C by beta.
+ * Errors: NOT_INITIALIZED, INVALID_VALUE, MISALIGNED, WORKSPACE_TOO_SMALL,
+ * TOLERANCE_UNREACHABLE, UNSUPPORTED, CUDA_ERROR. */
+hmat_status hmat_bq_gemm(hmat_handle handle, int32_t opA, int32_t opB,
+                         uint32_t flagsA, uint32_t flagsB,
+                         int64_t m, int64_t n, int64_t k,
+                         double alpha_re, double alpha_im,
+                         const double *A, int64_t lda, int64_t strideA,
+                         const double *B, int64_t ldb, int64_t strideB,
+                         double beta_re, double beta_im,
+                         double *C, int64_t ldc, int64_t strideC,
+                         int32_t mode, double tol,
+                         void *workspace, size_t workspace_bytes, void *stream);
+
+/* `count` independent products of any shapes, ops and flags in one grouped
+ * persistent launch per stage (Sec. III B per product; the grouping is this
+ * library's).  descs: HOST array, copied before the call returns.  The C
+ * matrices must not overlap each other.  use_graph != 0: the stage launches
+ * are captured once into a CUDA graph keyed by the descriptor set and replayed
+ * on later calls with identical descriptors (the handle keeps the graph).
+ * Errors as hmat_bq_gemm; the index of the first bad descriptor is reported
+ * by hmat_last_bad_index(). */
+hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
+                                 const hmat_gemm_desc *descs, int32_t mode,
+                                 double tol, void *workspace,
+                                 size_t workspace_bytes, void *stream,
+                                 int32_t use_graph);
+
+/* Index of the descriptor that made the last grouped call fail, or -1. */
+int32_t hmat_last_bad_index(hmat_handle handle);
+
+/* The product plan used for (opA, opB, flagsA, flagsB) — host only, for
+ * tests and tools.  On return *n_products = P (<= 24) and, for p < P,
+ *   U[p*8 + c]  in {-1,0,1}: coefficient of STORED component c of A in the
+ *               left factor of real product p (op signs folded in);
+ *   V[p*8 + d]  likewise for B;
+ *   W[e*24 + p] coefficient of product p in output component e (exact
+ *               dyadic rationals: 0, +-1/4, +-1/2, +-1, +-2, ...),
+ * so that output_e = sum_p W[e,p] (sum_c U[p,c] A_c)(sum_d V[p,d] B_d).
+ * strategy (may be NULL): 0 = the paper's bilinear scheme (Eq. bilinearH +
+ * Gauss), 1 = component-wise terms with Gauss (chosen when fewer products).
+ * U, V, W may be NULL to query only the count. */
+hmat_status hmat_plan_info(int32_t opA, int32_t opB, uint32_t flagsA,
+                           uint32_t flagsB, int32_t *n_products, int8_t *U,
+                           int8_t *V, double *W, int32_t *strategy);
+
+/* Split-mode parameters for inner dimension k and target tol — host only.
+ * On return *n_moduli = L, moduli[0..L-1] the moduli (caller array of >= 32),
+ * *bits = the integer width b of the scaled operands (|X| <= 2^b). */
+hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
+                            int32_t *moduli, int32_t *bits);
+
+/* Read and clear the device error word (0 = none; otherwise a bit mask of
+ * which bounded wait gave up).  Synchronises the device. */
+hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
+
+/* Kernel profiling: when enabled, every library kernel launch on the handle
+ * is bracketed by CUDA events on its launch stream; hmat_get_profile returns,
+ * per kernel id, the number of launches and the summed event time (ms) since
+ * the last reset (it synchronises on the recorded events).  Kernel ids:
+ * 0 fp64 bilinear, 1 split exponents, 2 split encode, 3 split residue GEMM,
+ * 4 split CRT/recombine, 5 beta-scale. */
+hmat_status hmat_set_profiling(hmat_handle handle, int32_t enable);
+hmat_status hmat_get_profile(hmat_handle handle, int32_t kernel_id,
+                             int64_t *launches, double *total_ms);
+hmat_status hmat_reset_profile(hmat_handle handle);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HMAT_H */

@@ -1,0 +1,310 @@
+"""Python binding of libhmat (include/hmat.h): GB300 biquaternion matrix products.
+
+The binding only marshals arguments: every step of the computation runs in the
+library's CUDA kernels.  PyTorch supplies device memory and streams.  There is
+no CPU fallback; if the library cannot be built or loaded, :func:`lib` raises.
+
+Matrices are torch float64 tensors of shape (8, rows, cols) on the GPU: the
+eight real components [M1..M8] = [E_R, E_I, F_R, F_I, G_I, -G_R, H_I, -H_R] of
+a biquaternion matrix (arXiv 2609.02081, Sec. III), each component row-major
+(last stride 1); ``stride(1)`` is the leading dimension, ``stride(0)`` the
+component stride.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+HMAT_OP_N, HMAT_OP_T, HMAT_OP_C, HMAT_OP_H, HMAT_OP_QC = 0, 1, 2, 3, 4
+OPS = {"N": HMAT_OP_N, "T": HMAT_OP_T, "C": HMAT_OP_C, "H": HMAT_OP_H, "QC": HMAT_OP_QC}
+HMAT_REAL, HMAT_COMPLEX, HMAT_TRS, HMAT_TRA, HMAT_BQ = 0x01, 0x11, 0x0F, 0xF0, 0xFF
+HMAT_MODE_FP64, HMAT_MODE_SPLIT = 0, 1
+MODES = {"fp64": HMAT_MODE_FP64, "split": HMAT_MODE_SPLIT}
+KERNEL_IDS = {"fp64_bilinear": 0, "split_exponents": 1, "split_encode": 2, "split_residue_gemm": 3,
+              "split_crt": 4, "beta_scale": 5}
+STATUS = {0: "SUCCESS", 1: "INVALID_VALUE", 2: "UNSUPPORTED", 3: "MISALIGNED", 4: "WORKSPACE_TOO_SMALL",
+          5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "NOT_INITIALIZED", 8: "TOLERANCE_UNREACHABLE", 9: "INTERNAL"}
+
+
+class HmatError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = int(status)
+        super().__init__(f"{what}: hmat status {status} ({STATUS.get(int(status), '?')})")
+
+
+class hmat_gemm_desc(ctypes.Structure):
+    _fields_ = [("opA", ctypes.c_int32), ("opB", ctypes.c_int32),
+                ("flagsA", ctypes.c_uint32), ("flagsB", ctypes.c_uint32),
+                ("m", ctypes.c_int64), ("n", ctypes.c_int64), ("k", ctypes.c_int64),
+                ("alpha_re", ctypes.c_double), ("alpha_im", ctypes.c_double),
+                ("beta_re", ctypes.c_double), ("beta_im", ctypes.c_double),
+                ("A", ctypes.c_void_p), ("lda", ctypes.c_int64), ("strideA", ctypes.c_int64),
+                ("B", ctypes.c_void_p), ("ldb", ctypes.c_int64), ("strideB", ctypes.c_int64),
+                ("C", ctypes.c_void_p), ("ldc", ctypes.c_int64), ("strideC", ctypes.c_int64)]
+
+
+_i32, _u32, _i64, _dbl, _ptr, _sz = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64, ctypes.c_double,
+                                     ctypes.c_void_p, ctypes.c_size_t)
+# name -> (restype, argtypes), mirroring include/hmat.h
+SIGNATURES = {
+    "hmat_version": (_i32, []),
+    "hmat_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hmat_create": (ctypes.c_int, [ctypes.POINTER(_ptr)]),
+    "hmat_destroy": (ctypes.c_int, [_ptr]),
+    "hmat_workspace_size": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc), _i32, _dbl,
+                                           ctypes.POINTER(_sz)]),
+    "hmat_bq_gemm": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _dbl, _dbl,
+                                    _ptr, _i64, _i64, _ptr, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
+                                    _i32, _dbl, _ptr, _sz, _ptr]),
+    "hmat_bq_gemm_grouped": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc), _i32, _dbl, _ptr, _sz,
+                                            _ptr, _i32]),
+    "hmat_last_bad_index": (_i32, [_ptr]),
+    "hmat_plan_info": (ctypes.c_int, [_i32, _i32, _u32, _u32, ctypes.POINTER(_i32), ctypes.c_void_p,
+                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_i32)]),
+    "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
+    "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
+    "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
+    "hmat_get_profile": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
+    "hmat_reset_profile": (ctypes.c_int, [_ptr]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """The loaded libhmat.so (built in-tree with nvcc on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build() if build_if_missing else _build.LIB
+            if not os.path.exists(path):
+                raise RuntimeError(f"libhmat.so not found at {path}; run __graft_entry__.build()")
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise HmatError(status, what)
+
+
+# ----------------------------------------------------------------------------- host-only queries
+def plan_info(opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ):
+    """(n_products, U[P,8], V[P,8], W[8,P], strategy) of the product plan (hmat_plan_info)."""
+    L = lib()
+    n = _i32()
+    st = _i32()
+    U = np.zeros((24, 8), dtype=np.int8)
+    V = np.zeros((24, 8), dtype=np.int8)
+    W = np.zeros((8, 24), dtype=np.float64)
+    _check(L.hmat_plan_info(_op(opA), _op(opB), flagsA, flagsB, ctypes.byref(n), U.ctypes.data, V.ctypes.data,
+                            W.ctypes.data, ctypes.byref(st)), "hmat_plan_info")
+    P = n.value
+    return P, U[:P].copy(), V[:P].copy(), W[:, :P].copy(), st.value
+
+
+def split_info(k: int, tol: float = 0.0):
+    """(moduli list, bits) that split mode uses for inner dimension k and tolerance tol."""
+    L = lib()
+    n = _i32()
+    bits = _i32()
+    mods = np.zeros(32, dtype=np.int32)
+    _check(L.hmat_split_info(int(k), float(tol), ctypes.byref(n), mods.ctypes.data, ctypes.byref(bits)),
+           "hmat_split_info")
+    return [int(x) for x in mods[:n.value]], bits.value
+
+
+def _op(op) -> int:
+    return OPS[op] if isinstance(op, str) else int(op)
+
+
+def _mode(mode) -> int:
+    return MODES[mode] if isinstance(mode, str) else int(mode)
+
+
+# ----------------------------------------------------------------------------- handle and calls
+class Handle:
+    """An hmat_handle bound to the current CUDA device."""
+
+    def __init__(self):
+        self._h = _ptr()
+        _check(lib().hmat_create(ctypes.byref(self._h)), "hmat_create")
+
+    @property
+    def value(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib().hmat_destroy(self._h)
+            self._h = _ptr()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- profiling / errors
+    def set_profiling(self, on: bool):
+        _check(lib().hmat_set_profiling(self._h, 1 if on else 0), "hmat_set_profiling")
+
+    def profile(self, kernel: str):
+        n = _i64()
+        ms = _dbl()
+        _check(lib().hmat_get_profile(self._h, KERNEL_IDS[kernel], ctypes.byref(n), ctypes.byref(ms)),
+               "hmat_get_profile")
+        return n.value, ms.value
+
+    def reset_profile(self):
+        _check(lib().hmat_reset_profile(self._h), "hmat_reset_profile")
+
+    def device_error(self) -> int:
+        code = _u32()
+        _check(lib().hmat_get_device_error(self._h, ctypes.byref(code)), "hmat_get_device_error")
+        return code.value
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _mat_args(X, rows, cols, name):
+    """(ptr, ld, stride) of an 8 x rows x cols float64 CUDA tensor."""
+    import torch
+    if X is None:
+        return None, max(cols, 1), 0
+    if not isinstance(X, torch.Tensor) or X.dtype != torch.float64 or not X.is_cuda:
+        raise TypeError(f"{name} must be a float64 CUDA tensor")
+    if X.dim() != 3 or X.shape[0] != 8 or X.shape[1] != rows or X.shape[2] != cols:
+        raise ValueError(f"{name} must have shape (8, {rows}, {cols}), got {tuple(X.shape)}")
+    if cols > 1 and X.stride(2) != 1:
+        raise ValueError(f"{name} components must be row-major (last stride 1)")
+    return X.data_ptr(), max(X.stride(1), cols, 1), X.stride(0)
+
+
+def make_desc(A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, alpha=1.0, beta=0.0, m=None, n=None,
+              k=None) -> hmat_gemm_desc:
+    """A descriptor for C <- alpha op(A) op(B) + beta C over torch tensors."""
+    oa, ob = _op(opA), _op(opB)
+    ta, tb = oa in (HMAT_OP_T, HMAT_OP_H), ob in (HMAT_OP_T, HMAT_OP_H)
+    if m is None:
+        m = A.shape[2] if ta else A.shape[1]
+    if k is None:
+        k = A.shape[1] if ta else A.shape[2]
+    if n is None:
+        n = B.shape[1] if tb else B.shape[2]
+    a_ptr, lda, sa = _mat_args(A, *((k, m) if ta else (m, k)), "A")
+    b_ptr, ldb, sb = _mat_args(B, *((n, k) if tb else (k, n)), "B")
+    c_ptr, ldc, sc = _mat_args(C, m, n, "C")
+    alpha, beta = complex(alpha), complex(beta)
+    d = hmat_gemm_desc()
+    d.opA, d.opB, d.flagsA, d.flagsB = oa, ob, int(flagsA), int(flagsB)
+    d.m, d.n, d.k = int(m), int(n), int(k)
+    d.alpha_re, d.alpha_im, d.beta_re, d.beta_im = alpha.real, alpha.imag, beta.real, beta.imag
+    d.A, d.lda, d.strideA = a_ptr, lda, sa
+    d.B, d.ldb, d.strideB = b_ptr, ldb, sb
+    d.C, d.ldc, d.strideC = c_ptr, ldc, sc
+    return d
+
+
+def hmat_workspace_size(handle: Handle, descs, mode="fp64", tol=0.0) -> int:
+    arr = (hmat_gemm_desc * len(descs))(*descs)
+    out = _sz()
+    _check(lib().hmat_workspace_size(handle.value, len(descs), arr, _mode(mode), float(tol), ctypes.byref(out)),
+           "hmat_workspace_size")
+    return out.value
+
+
+def _workspace(nbytes, device):
+    import torch
+    if nbytes == 0:
+        return None, 0
+    return torch.empty(nbytes, dtype=torch.uint8, device=device), nbytes
+
+
+def hmat_bq_gemm(handle: Handle, A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, alpha=1.0, beta=0.0,
+                 mode="fp64", tol=0.0, workspace=None, stream=None):
+    """C <- alpha op(A) op(B) + beta C (hmat_bq_gemm); returns C.
+
+    workspace: a uint8 CUDA tensor of at least hmat_workspace_size() bytes, or
+    None to allocate one for this call (split mode)."""
+    d = make_desc(A, B, C, opA, opB, flagsA, flagsB, alpha, beta)
+    md = _mode(mode)
+    ws = workspace
+    if ws is None and md == HMAT_MODE_SPLIT:
+        ws, _ = _workspace(hmat_workspace_size(handle, [d], md, tol), C.device)
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() if ws is not None else 0
+    _check(lib().hmat_bq_gemm(handle.value, d.opA, d.opB, d.flagsA, d.flagsB, d.m, d.n, d.k, d.alpha_re,
+                              d.alpha_im, d.A, d.lda, d.strideA, d.B, d.ldb, d.strideB, d.beta_re, d.beta_im,
+                              d.C, d.ldc, d.strideC, md, float(tol), ws_ptr, ws_bytes, _stream_ptr(stream)),
+           "hmat_bq_gemm")
+    return C
+
+
+def hmat_bq_gemm_grouped(handle: Handle, descs, mode="fp64", tol=0.0, workspace=None, stream=None,
+                         use_graph=False, device=None):
+    """Grouped products (hmat_bq_gemm_grouped) over a list of hmat_gemm_desc."""
+    md = _mode(mode)
+    arr = (hmat_gemm_desc * len(descs))(*descs)
+    ws = workspace
+    if ws is None and md == HMAT_MODE_SPLIT:
+        import torch
+        ws, _ = _workspace(hmat_workspace_size(handle, descs, md, tol), device or torch.device("cuda"))
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() if ws is not None else 0
+    st = lib().hmat_bq_gemm_grouped(handle.value, len(descs), arr, md, float(tol), ws_ptr, ws_bytes,
+                                    _stream_ptr(stream), 1 if use_graph else 0)
+    if st != 0:
+        bad = lib().hmat_last_bad_index(handle.value)
+        raise HmatError(st, f"hmat_bq_gemm_grouped (descriptor {bad})")
+
+
+def bq_gemm_host(handle: Handle, A_host, B_host, C_host, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ,
+                 alpha=1.0, beta=0.0, mode="split", tol=0.0, device_buffers=None, workspace=None, stream=None):
+    """End-to-end product on HOST tensors: copy A, B (and C if beta != 0) to the
+    device, run hmat_bq_gemm, copy C back.  device_buffers=(dA, dB, dC) reuses
+    device storage.  Returns (C_host, h2d_bytes, d2h_bytes)."""
+    import torch
+    dA, dB, dC = device_buffers if device_buffers is not None else (
+        torch.empty_like(A_host, device="cuda"), torch.empty_like(B_host, device="cuda"),
+        torch.empty_like(C_host, device="cuda"))
+    dA.copy_(A_host, non_blocking=True)
+    dB.copy_(B_host, non_blocking=True)
+    h2d = A_host.numel() * 8 + B_host.numel() * 8
+    if complex(beta) != 0:
+        dC.copy_(C_host, non_blocking=True)
+        h2d += C_host.numel() * 8
+    hmat_bq_gemm(handle, dA, dB, dC, opA, opB, flagsA, flagsB, alpha, beta, mode, tol, workspace, stream)
+    C_host.copy_(dC, non_blocking=True)
+    return C_host, h2d, C_host.numel() * 8
+
+
+__all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gemm_grouped", "hmat_workspace_size",
+           "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",
+           "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]

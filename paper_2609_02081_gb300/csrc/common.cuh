@@ -1,0 +1,54 @@
+// common.cuh — descriptors and small device helpers shared by the library's kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace hmat {
+
+// Bits of the device error word (set by bounded waits that gave up).
+enum : uint32_t {
+  kErrWaitProducer = 1u << 0,
+  kErrWaitMma = 1u << 1,
+  kErrWaitEpilogue = 1u << 2,
+  kErrWaitTmem = 1u << 3,
+  kErrNonFinite = 1u << 4,   // split mode met an Inf/NaN input
+};
+
+// Device address of the library's error word (defined in hmat_capi.cu); kernels
+// that can give up a bounded wait receive it as a parameter.
+uint32_t* device_error_ptr();
+
+// One product as the kernels see it (device copy of a validated descriptor).
+struct JobDesc {
+  const double* A;
+  const double* B;
+  double* C;
+  int64_t lda, sA, ldb, sB, ldc, sC;
+  int32_t m, n, k;
+  int32_t transA, transB;
+  uint32_t fa, fb;
+  int32_t plan;          // index into the plan table
+  int8_t signA[8], signB[8];
+  double alpha_re, alpha_im, beta_re, beta_im;
+  int32_t tiles_m, tiles_n;
+  int64_t tile_begin;    // first global tile of this job (FP64 kernel)
+};
+
+// Locate the job owning global tile t (jobs sorted by tile_begin).
+__device__ __forceinline__ int find_job(const JobDesc* jobs, int njobs, int64_t t) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].tile_begin <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+}  // namespace hmat

@@ -1,0 +1,578 @@
+// hmat_capi.cu — the C ABI (include/hmat.h): validation, plans, job upload,
+// kernel dispatch, profiling and the device error word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "../../include/hmat.h"
+#include "common.cuh"
+#include "split.hpp"
+
+namespace hmat {
+
+__device__ uint32_t g_hmat_device_error = 0;
+
+static uint32_t* g_err_ptr = nullptr;
+uint32_t* device_error_ptr() { return g_err_ptr; }
+
+size_t fp64_smem_bytes();
+cudaError_t fp64_configure();
+cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* d_plans, int64_t total_tiles,
+                                 int grid, cudaStream_t stream);
+int fp64_tile_m();
+int fp64_tile_n();
+
+constexpr int kPlanSlots = 256;
+constexpr int kStageSlots = 8;
+constexpr int kKernelIds = 6;
+constexpr size_t kGraphCache = 8;
+
+}  // namespace hmat
+
+using namespace hmat;
+
+struct hmat_context {
+  int device = 0;
+  int sm_count = 0;
+  std::mutex mu;
+  // product plans: host pinned copy (immutable once filled) and device table
+  KPlan* h_plans = nullptr;
+  KPlan* d_plans = nullptr;
+  uint32_t plan_key[kPlanSlots];
+  int n_plans = 0;
+  // job-descriptor staging ring
+  struct Slot {
+    JobDesc* h = nullptr;
+    JobDesc* d = nullptr;
+    size_t cap = 0;
+    cudaEvent_t done = nullptr;
+    bool used = false;
+  } slots[kStageSlots];
+  int next_slot = 0;
+  // profiling
+  bool profiling = false;
+  struct Rec { int kernel; cudaEvent_t a, b; };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t launches[kKernelIds] = {0};
+  double total_ms[kKernelIds] = {0};
+  int32_t last_bad = -1;
+  SplitState split;
+  // CUDA graphs of grouped calls (use_graph), keyed by the call arguments
+  struct GraphEntry {
+    std::vector<unsigned char> key;
+    cudaGraphExec_t exec = nullptr;
+    JobDesc* d_fp64 = nullptr;
+    SplitJob* d_split = nullptr;
+    void release() {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (d_fp64) cudaFree(d_fp64);
+      if (d_split) cudaFree(d_split);
+      exec = nullptr; d_fp64 = nullptr; d_split = nullptr;
+    }
+  };
+  std::vector<GraphEntry> graphs;
+};
+
+namespace {
+
+hmat_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return HMAT_STATUS_SUCCESS;
+  (void)cudaGetLastError();
+  return HMAT_STATUS_CUDA_ERROR;
+}
+
+cudaEvent_t take_event(hmat_context* h) {
+  if (!h->event_pool.empty()) {
+    cudaEvent_t e = h->event_pool.back();
+    h->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Validate one descriptor; on success fill the kernel-side JobDesc (except plan / tiles).
+hmat_status validate(const hmat_gemm_desc& d, JobDesc* out) {
+  if (d.opA < 0 || d.opA > 4 || d.opB < 0 || d.opB > 4) return HMAT_STATUS_INVALID_VALUE;
+  if (d.flagsA > 0xFFu || d.flagsB > 0xFFu) return HMAT_STATUS_INVALID_VALUE;
+  if (d.m < 0 || d.n < 0 || d.k < 0) return HMAT_STATUS_INVALID_VALUE;
+  const int64_t kLim = (int64_t)1 << 30;
+  if (d.m > kLim || d.n > kLim || d.k > kLim) return HMAT_STATUS_UNSUPPORTED;
+  if (!std::isfinite(d.alpha_re) || !std::isfinite(d.alpha_im) || !std::isfinite(d.beta_re) ||
+      !std::isfinite(d.beta_im))
+    return HMAT_STATUS_INVALID_VALUE;
+  const bool ta = op_transposes(d.opA), tb = op_transposes(d.opB);
+  const bool need_ab = d.m > 0 && d.n > 0 && d.k > 0;
+  const bool need_c = d.m > 0 && d.n > 0;
+  if (need_ab) {
+    if (d.flagsA && !d.A) return HMAT_STATUS_INVALID_VALUE;
+    if (d.flagsB && !d.B) return HMAT_STATUS_INVALID_VALUE;
+    const int64_t acols = ta ? d.m : d.k, bcols = tb ? d.k : d.n;
+    if (d.flagsA && (d.lda < std::max<int64_t>(1, acols) || d.strideA < 0)) return HMAT_STATUS_INVALID_VALUE;
+    if (d.flagsB && (d.ldb < std::max<int64_t>(1, bcols) || d.strideB < 0)) return HMAT_STATUS_INVALID_VALUE;
+    if ((reinterpret_cast<uintptr_t>(d.A) & 7u) || (reinterpret_cast<uintptr_t>(d.B) & 7u))
+      return HMAT_STATUS_MISALIGNED;
+  }
+  if (need_c) {
+    if (!d.C) return HMAT_STATUS_INVALID_VALUE;
+    if (d.ldc < std::max<int64_t>(1, d.n) || d.strideC < 0) return HMAT_STATUS_INVALID_VALUE;
+    if (reinterpret_cast<uintptr_t>(d.C) & 7u) return HMAT_STATUS_MISALIGNED;
+  }
+  JobDesc j;
+  std::memset(&j, 0, sizeof(j));
+  j.A = d.A; j.B = d.B; j.C = d.C;
+  j.lda = d.lda; j.sA = d.strideA; j.ldb = d.ldb; j.sB = d.strideB; j.ldc = d.ldc; j.sC = d.strideC;
+  j.m = (int32_t)d.m; j.n = (int32_t)d.n; j.k = (int32_t)d.k;
+  j.transA = ta; j.transB = tb;
+  j.fa = d.k > 0 ? d.flagsA : 0u;
+  j.fb = d.k > 0 ? d.flagsB : 0u;
+  for (int c = 0; c < 8; ++c) {
+    j.signA[c] = (int8_t)op_sign(d.opA, c);
+    j.signB[c] = (int8_t)op_sign(d.opB, c);
+  }
+  j.alpha_re = d.alpha_re; j.alpha_im = d.alpha_im; j.beta_re = d.beta_re; j.beta_im = d.beta_im;
+  *out = j;
+  return HMAT_STATUS_SUCCESS;
+}
+
+// Plan slot for (fa, fb); uploads a new plan on `stream` the first time.
+hmat_status plan_slot(hmat_context* h, uint32_t fa, uint32_t fb, cudaStream_t stream, int* slot) {
+  const uint32_t key = (fa << 8) | fb;
+  for (int i = 0; i < h->n_plans; ++i)
+    if (h->plan_key[i] == key) { *slot = i; return HMAT_STATUS_SUCCESS; }
+  if (h->n_plans >= kPlanSlots) return HMAT_STATUS_UNSUPPORTED;
+  KPlan p;
+  if (!build_plan(fa, fb, &p)) return HMAT_STATUS_INTERNAL;
+  const int i = h->n_plans;
+  h->h_plans[i] = p;
+  cudaError_t e = cudaMemcpyAsync(h->d_plans + i, h->h_plans + i, sizeof(KPlan), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  h->plan_key[i] = key;
+  h->n_plans = i + 1;
+  *slot = i;
+  return HMAT_STATUS_SUCCESS;
+}
+
+// Copy jobs to the device through the staging ring; returns the device pointer.
+hmat_status upload_jobs(hmat_context* h, const std::vector<JobDesc>& jobs, cudaStream_t stream,
+                        JobDesc** d_out, int* slot_out) {
+  const int si = h->next_slot;
+  h->next_slot = (h->next_slot + 1) % kStageSlots;
+  auto& s = h->slots[si];
+  if (s.used) {
+    cudaError_t e = cudaEventSynchronize(s.done);   // previous user of this slot is finished
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  if (s.cap < jobs.size()) {
+    size_t cap = std::max<size_t>(jobs.size(), 64);
+    if (s.h) cudaFreeHost(s.h);
+    if (s.d) cudaFree(s.d);
+    s.h = nullptr; s.d = nullptr; s.cap = 0;
+    cudaError_t e = cudaMallocHost(&s.h, cap * sizeof(JobDesc));
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMalloc(&s.d, cap * sizeof(JobDesc));
+    if (e != cudaSuccess) return cuda_status(e);
+    s.cap = cap;
+  }
+  std::memcpy(s.h, jobs.data(), jobs.size() * sizeof(JobDesc));
+  cudaError_t e = cudaMemcpyAsync(s.d, s.h, jobs.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  *d_out = s.d;
+  *slot_out = si;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status finish_slot(hmat_context* h, int si, cudaStream_t stream) {
+  auto& s = h->slots[si];
+  cudaError_t e = cudaEventRecord(s.done, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  s.used = true;
+  return HMAT_STATUS_SUCCESS;
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- profiling hooks
+namespace hmat {
+
+ProfScope::ProfScope(hmat_context* h, int kernel, cudaStream_t stream) : h_(h), kernel_(kernel), stream_(stream) {
+  if (h_ && h_->profiling) {
+    a_ = take_event(h_);
+    b_ = take_event(h_);
+    if (a_) cudaEventRecord(a_, stream_);
+  }
+}
+ProfScope::~ProfScope() {
+  if (h_ && h_->profiling && a_ && b_) {
+    cudaEventRecord(b_, stream_);
+    h_->pending.push_back({kernel_, a_, b_});
+  }
+}
+
+int handle_sm_count(hmat_context* h) { return h->sm_count; }
+SplitState& handle_split(hmat_context* h) { return h->split; }
+
+}  // namespace hmat
+
+// ----------------------------------------------------------------- dispatch
+namespace {
+
+// A validated call: FP64 jobs (with tile prefixes) and split jobs (with layouts).
+struct Prepared {
+  std::vector<JobDesc> f;
+  int64_t f_tiles = 0;
+  SplitPrep sp;
+  bool has_split = false;
+};
+
+hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
+                    size_t ws_bytes, cudaStream_t stream, Prepared* out) {
+  if (count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
+  if (tol < 0 || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) return HMAT_STATUS_INVALID_VALUE;
+  std::vector<JobDesc> split_jobs;
+  for (int32_t i = 0; i < count; ++i) {
+    JobDesc j;
+    hmat_status st = validate(descs[i], &j);
+    if (st != HMAT_STATUS_SUCCESS) { h->last_bad = i; return st; }
+    if (j.m == 0 || j.n == 0) continue;
+    int slot = 0;
+    st = plan_slot(h, j.fa, j.fb, stream, &slot);
+    if (st != HMAT_STATUS_SUCCESS) { h->last_bad = i; return st; }
+    j.plan = slot;
+    // k == 0 or an all-absent operand: the product vanishes; the FP64 kernel applies beta.
+    const bool trivial = (j.k == 0) || h->h_plans[slot].np == 0;
+    if (mode == HMAT_MODE_SPLIT && !trivial) split_jobs.push_back(j);
+    else out->f.push_back(j);
+  }
+  const int tm = fp64_tile_m(), tn = fp64_tile_n();
+  for (auto& j : out->f) {
+    j.tiles_m = (j.m + tm - 1) / tm;
+    j.tiles_n = (j.n + tn - 1) / tn;
+    j.tile_begin = out->f_tiles;
+    out->f_tiles += (int64_t)j.tiles_m * j.tiles_n;
+  }
+  if (!split_jobs.empty()) {
+    hmat_status st = split_prepare(split_jobs, h->h_plans, tol, ws_bytes, &out->sp);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+    out->has_split = true;
+  }
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status launch_fp64(hmat_context* h, const Prepared& pr, const JobDesc* d_jobs, cudaStream_t stream) {
+  const int grid = (int)std::min<int64_t>(pr.f_tiles, h->sm_count);
+  ProfScope ps(h, 0, stream);
+  return cuda_status(launch_fp64_bilinear(d_jobs, (int)pr.f.size(), h->d_plans, pr.f_tiles, grid, stream));
+}
+
+hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
+                void* workspace, size_t ws_bytes, void* stream_ptr) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->last_bad = -1;
+  Prepared pr;
+  hmat_status st = prepare(h, count, descs, mode, tol, ws_bytes, stream, &pr);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  if (pr.has_split) {
+    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
+    st = run_split(h, pr.sp, h->d_plans, workspace, stream);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+  }
+  if (pr.f_tiles > 0) {
+    JobDesc* d_jobs = nullptr;
+    int slot = 0;
+    st = upload_jobs(h, pr.f, stream, &d_jobs, &slot);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+    st = launch_fp64(h, pr, d_jobs, stream);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+    return finish_slot(h, slot, stream);
+  }
+  return HMAT_STATUS_SUCCESS;
+}
+
+// Grouped call replayed from a CUDA graph keyed by the exact call arguments.
+hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
+                      void* workspace, size_t ws_bytes, void* stream_ptr) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  if (stream == nullptr)   // the legacy default stream cannot be captured: run eagerly
+    return run(h, count, descs, mode, tol, workspace, ws_bytes, stream_ptr);
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->last_bad = -1;
+  // key: descriptors + mode + tol + workspace
+  std::vector<unsigned char> key(sizeof(int32_t) * 2 + sizeof(double) + sizeof(void*) + sizeof(size_t) +
+                                 (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc));
+  {
+    unsigned char* k = key.data();
+    std::memcpy(k, &count, 4); k += 4;
+    std::memcpy(k, &mode, 4); k += 4;
+    std::memcpy(k, &tol, 8); k += 8;
+    std::memcpy(k, &workspace, sizeof(void*)); k += sizeof(void*);
+    std::memcpy(k, &ws_bytes, sizeof(size_t)); k += sizeof(size_t);
+    if (count > 0 && descs) std::memcpy(k, descs, (size_t)count * sizeof(hmat_gemm_desc));
+  }
+  for (auto& g : h->graphs) {
+    if (g.key == key) return cuda_status(cudaGraphLaunch(g.exec, stream));
+  }
+  Prepared pr;
+  hmat_status st = prepare(h, count, descs, mode, tol, ws_bytes, stream, &pr);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  if (pr.has_split && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return HMAT_STATUS_MISALIGNED;
+  hmat_context::GraphEntry ge;
+  ge.key = key;
+  cudaError_t e = cudaSuccess;
+  if (pr.f_tiles > 0) {
+    e = cudaMalloc(&ge.d_fp64, pr.f.size() * sizeof(JobDesc));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ge.d_fp64, pr.f.data(), pr.f.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, stream);
+  }
+  if (e == cudaSuccess && pr.has_split) {
+    e = cudaMalloc(&ge.d_split, pr.sp.jobs.size() * sizeof(SplitJob));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ge.d_split, pr.sp.jobs.data(), pr.sp.jobs.size() * sizeof(SplitJob),
+                          cudaMemcpyHostToDevice, stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);   // tables (and any new plans) resident
+  if (e != cudaSuccess) {
+    ge.release();
+    return cuda_status(e);
+  }
+  const bool prof = h->profiling;
+  h->profiling = false;   // no event records inside the captured graph
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    if (pr.has_split)
+      st = split_launch(h, pr.sp, ge.d_split, h->d_plans, static_cast<unsigned char*>(workspace), stream);
+    if (st == HMAT_STATUS_SUCCESS && pr.f_tiles > 0) st = launch_fp64(h, pr, ge.d_fp64, stream);
+    const cudaError_t e2 = cudaStreamEndCapture(stream, &graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  h->profiling = prof;
+  if (e == cudaSuccess && st == HMAT_STATUS_SUCCESS) e = cudaGraphInstantiate(&ge.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess || st != HMAT_STATUS_SUCCESS) {
+    ge.release();
+    return st != HMAT_STATUS_SUCCESS ? st : cuda_status(e);
+  }
+  if (h->graphs.size() >= kGraphCache) {
+    cudaStreamSynchronize(stream);
+    h->graphs.front().release();
+    h->graphs.erase(h->graphs.begin());
+  }
+  h->graphs.push_back(std::move(ge));
+  return cuda_status(cudaGraphLaunch(h->graphs.back().exec, stream));
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- C ABI
+extern "C" {
+
+int32_t hmat_version(void) { return 100; }
+
+const char* hmat_status_string(hmat_status s) {
+  switch (s) {
+    case HMAT_STATUS_SUCCESS: return "success";
+    case HMAT_STATUS_INVALID_VALUE: return "invalid value";
+    case HMAT_STATUS_UNSUPPORTED: return "unsupported";
+    case HMAT_STATUS_MISALIGNED: return "misaligned pointer or stride";
+    case HMAT_STATUS_WORKSPACE_TOO_SMALL: return "workspace too small";
+    case HMAT_STATUS_CUDA_ERROR: return "CUDA error";
+    case HMAT_STATUS_DEVICE_TIMEOUT: return "device wait timed out";
+    case HMAT_STATUS_NOT_INITIALIZED: return "handle not initialized";
+    case HMAT_STATUS_TOLERANCE_UNREACHABLE: return "tolerance unreachable in split mode";
+    case HMAT_STATUS_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+hmat_status hmat_create(hmat_handle* handle) {
+  if (!handle) return HMAT_STATUS_INVALID_VALUE;
+  *handle = nullptr;
+  hmat_context* h = new (std::nothrow) hmat_context();
+  if (!h) return HMAT_STATUS_INTERNAL;
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+  if (e == cudaSuccess) e = cudaMallocHost(&h->h_plans, kPlanSlots * sizeof(KPlan));
+  if (e == cudaSuccess) e = cudaMalloc(&h->d_plans, kPlanSlots * sizeof(KPlan));
+  for (int i = 0; e == cudaSuccess && i < kStageSlots; ++i) e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_err_ptr), g_hmat_device_error);
+  if (e == cudaSuccess) e = fp64_configure();
+  if (e == cudaSuccess) e = split_configure();
+  if (e != cudaSuccess) {
+    hmat_destroy(h);
+    return cuda_status(e);
+  }
+  *handle = h;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_destroy(hmat_handle h) {
+  if (!h) return HMAT_STATUS_SUCCESS;
+  for (auto& s : h->slots) {
+    if (s.used && s.done) cudaEventSynchronize(s.done);
+    if (s.done) cudaEventDestroy(s.done);
+    if (s.h) cudaFreeHost(s.h);
+    if (s.d) cudaFree(s.d);
+  }
+  for (auto& r : h->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : h->event_pool) cudaEventDestroy(e);
+  cudaDeviceSynchronize();
+  for (auto& g : h->graphs) g.release();
+  split_release(h->split);
+  if (h->h_plans) cudaFreeHost(h->h_plans);
+  if (h->d_plans) cudaFree(h->d_plans);
+  delete h;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_workspace_size(hmat_handle h, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
+                                double tol, size_t* bytes) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (!bytes || count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
+  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
+  *bytes = 0;
+  if (mode == HMAT_MODE_FP64) return HMAT_STATUS_SUCCESS;
+  std::vector<SplitShape> shapes;
+  for (int32_t i = 0; i < count; ++i) {
+    const hmat_gemm_desc& d = descs[i];
+    if (d.m < 0 || d.n < 0 || d.k < 0 || d.flagsA > 0xFFu || d.flagsB > 0xFFu) return HMAT_STATUS_INVALID_VALUE;
+    if (d.m == 0 || d.n == 0 || d.k == 0) continue;
+    KPlan p;
+    if (!build_plan(d.flagsA, d.flagsB, &p)) return HMAT_STATUS_INTERNAL;
+    if (p.np == 0) continue;
+    shapes.push_back({d.m, d.n, d.k, p.np, p.nlf, p.nrf});
+  }
+  return split_workspace_bytes(shapes, tol, bytes);
+}
+
+hmat_status hmat_bq_gemm(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
+                         int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A, int64_t lda,
+                         int64_t strideA, const double* B, int64_t ldb, int64_t strideB, double beta_re,
+                         double beta_im, double* C, int64_t ldc, int64_t strideC, int32_t mode, double tol,
+                         void* workspace, size_t workspace_bytes, void* stream) {
+  hmat_gemm_desc d;
+  d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB;
+  d.m = m; d.n = n; d.k = k;
+  d.alpha_re = alpha_re; d.alpha_im = alpha_im; d.beta_re = beta_re; d.beta_im = beta_im;
+  d.A = A; d.lda = lda; d.strideA = strideA;
+  d.B = B; d.ldb = ldb; d.strideB = strideB;
+  d.C = C; d.ldc = ldc; d.strideC = strideC;
+  return run(h, 1, &d, mode, tol, workspace, workspace_bytes, stream);
+}
+
+hmat_status hmat_bq_gemm_grouped(hmat_handle h, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
+                                 double tol, void* workspace, size_t workspace_bytes, void* stream,
+                                 int32_t use_graph) {
+  if (!use_graph) return run(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
+  return run_graph(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
+}
+
+int32_t hmat_last_bad_index(hmat_handle h) { return h ? h->last_bad : -1; }
+
+hmat_status hmat_plan_info(int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int32_t* n_products,
+                           int8_t* U, int8_t* V, double* W, int32_t* strategy) {
+  if (!n_products || opA < 0 || opA > 4 || opB < 0 || opB > 4 || flagsA > 0xFFu || flagsB > 0xFFu)
+    return HMAT_STATUS_INVALID_VALUE;
+  KPlan p;
+  if (!build_plan(flagsA, flagsB, &p)) return HMAT_STATUS_INTERNAL;
+  *n_products = p.np;
+  if (strategy) *strategy = p.strategy;
+  for (int q = 0; q < p.np; ++q) {
+    int8_t row[8];
+    if (U) {
+      factor_row(p, 0, p.pl[q], opA, row);
+      std::memcpy(U + q * 8, row, 8);
+    }
+    if (V) {
+      factor_row(p, 1, p.pr[q], opB, row);
+      std::memcpy(V + q * 8, row, 8);
+    }
+  }
+  if (W)
+    for (int e = 0; e < 8; ++e)
+      for (int q = 0; q < kMaxProducts; ++q) W[e * kMaxProducts + q] = q < p.np ? 0.25 * p.w4[e][q] : 0.0;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_split_info(int64_t k, double tol, int32_t* n_moduli, int32_t* moduli, int32_t* bits) {
+  if (!n_moduli || !moduli || !bits || k < 0 || tol < 0 || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
+  SplitParams sp;
+  hmat_status st = split_params(k, tol, &sp);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  *n_moduli = sp.nmod;
+  *bits = sp.bits;
+  for (int i = 0; i < sp.nmod; ++i) moduli[i] = sp.moduli[i];
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_get_device_error(hmat_handle h, uint32_t* code) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (!code) return HMAT_STATUS_INVALID_VALUE;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpyFromSymbol(code, g_hmat_device_error, sizeof(uint32_t));
+  if (e == cudaSuccess) {
+    const uint32_t zero = 0;
+    e = cudaMemcpyToSymbol(g_hmat_device_error, &zero, sizeof(uint32_t));
+  }
+  return cuda_status(e);
+}
+
+hmat_status hmat_set_profiling(hmat_handle h, int32_t enable) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->profiling = enable != 0;
+  return HMAT_STATUS_SUCCESS;
+}
+
+static hmat_status drain_profile(hmat_context* h) {
+  for (auto& r : h->pending) {
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e != cudaSuccess) return cuda_status(e);
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (r.kernel >= 0 && r.kernel < kKernelIds) {
+      h->launches[r.kernel] += 1;
+      h->total_ms[r.kernel] += ms;
+    }
+    h->event_pool.push_back(r.a);
+    h->event_pool.push_back(r.b);
+  }
+  h->pending.clear();
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_get_profile(hmat_handle h, int32_t kernel_id, int64_t* launches, double* total_ms) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (kernel_id < 0 || kernel_id >= kKernelIds || !launches || !total_ms) return HMAT_STATUS_INVALID_VALUE;
+  std::lock_guard<std::mutex> lock(h->mu);
+  hmat_status st = drain_profile(h);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  *launches = h->launches[kernel_id];
+  *total_ms = h->total_ms[kernel_id];
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_reset_profile(hmat_handle h) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  std::lock_guard<std::mutex> lock(h->mu);
+  hmat_status st = drain_profile(h);
+  for (int i = 0; i < kKernelIds; ++i) { h->launches[i] = 0; h->total_ms[i] = 0; }
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,336 @@
+// plan.hpp — product plans for the biquaternion matrix product (host side).
+//
+// A plan lists the real matrix products a kernel forms and how their results
+// recombine into the eight output components.  It is built from the paper's
+// bilinear scheme (Sec. III B, Eq. bilinearH: eight complex products P1..P8
+// whose left/right factors are single complex coefficients or their Hadamard
+// (+-1) sums, recombined as Q1 = 2P1 - (P5+P6+P7+P8)/4, Q2 = -2P2 + ..., and
+// Gauss's three-product complex multiplication, Eq. cmplx-3-real-mult).
+// When subalgebra flags mark components absent, the terms they feed are
+// omitted (Sec. III B, last paragraph): a complex factor whose real or
+// imaginary part is structurally zero needs one or two real products instead
+// of three.  For mixed subalgebras a second strategy — the component-wise
+// terms a_f b_g expanded from the same bilinear equations, each with the
+// reduced Gauss rule — is sometimes cheaper (e.g. real x biquaternion: 8
+// products instead of 10); the plan with fewer products is kept.
+//
+// Everything is exact integer bookkeeping: left/right factors are +-1 sums of
+// op(A)/op(B) components, recombination weights are stored times 4 (the
+// paper's weights are 2 and 1/4).
+#pragma once
+#include <array>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+namespace hmat {
+
+constexpr int kMaxProducts = 24;
+
+// Real-valued linear combination of the 8 components of op(X): sign per component.
+struct Comb8 {
+  int8_t s[8];
+  bool operator==(const Comb8& o) const { return std::memcmp(s, o.s, 8) == 0; }
+  bool zero() const {
+    for (int c = 0; c < 8; ++c)
+      if (s[c]) return false;
+    return true;
+  }
+};
+
+// Kernel-facing plan, independent of op (op signs are applied when loading).
+//
+// Each side (left = op(A), right = op(B)) has up to 8 groups.  A group is a
+// +-1 combination x of the complex coefficients a_1..a_4 restricted to the
+// present components: re[e] weights component e (Re a_{e+1}), im[e] weights
+// component e+4 (Im a_{e+1}).  A group yields up to three real factors, each
+// written to a factor slot: Re = sum_e re[e] X_e, Im = sum_e im[e] X_{e+4},
+// and Re+Im (the Gauss factor).  Product p multiplies left slot pl[p] by right
+// slot pr[p]; its result enters output component e with weight w4[e][p] / 4.
+struct KPlan {
+  int32_t np = 0;            // real products (<= 24)
+  int32_t strategy = 0;      // 0 bilinear (Eq. bilinearH + Gauss), 1 component-wise + Gauss
+  int32_t nlg = 0, nrg = 0;  // groups per side (<= 8)
+  int32_t nlf = 0, nrf = 0;  // factor slots per side (<= 24)
+  int8_t lre[8][4], lim[8][4], lslot[8][3];  // slot of Re, Im, Re+Im (-1: not needed)
+  int8_t rre[8][4], rim[8][4], rslot[8][3];
+  int8_t pl[kMaxProducts], pr[kMaxProducts];
+  int8_t w4[8][kMaxProducts];
+};
+
+namespace detail {
+
+enum { CLS_ZERO = 0, CLS_RE = 1, CLS_IM = 2, CLS_CX = 3 };
+enum { PART_RE = 0, PART_IM = 1, PART_SUM = 2 };
+
+// A complex combination x over the complex coefficients a_1..a_4 (+-1 each).
+struct CComb { int8_t x[4]; };
+
+inline int cls_of(const CComb& x, unsigned flags) {
+  int c = 0;
+  for (int e = 0; e < 4; ++e) {
+    if (!x.x[e]) continue;
+    if ((flags >> e) & 1u) c |= CLS_RE;
+    if ((flags >> (e + 4)) & 1u) c |= CLS_IM;
+  }
+  return c;
+}
+
+// A real factor: part (Re, Im or Re+Im) of a complex combination restricted to
+// the present components.
+struct Factor {
+  int8_t re[4], im[4];
+  int part;
+  bool same_group(const Factor& o) const {
+    return std::memcmp(re, o.re, 4) == 0 && std::memcmp(im, o.im, 4) == 0;
+  }
+  bool operator==(const Factor& o) const { return same_group(o) && part == o.part; }
+};
+
+inline Factor make_factor(const CComb& x, unsigned flags, int part) {
+  Factor f;
+  for (int e = 0; e < 4; ++e) {
+    f.re[e] = ((flags >> e) & 1u) ? x.x[e] : 0;
+    f.im[e] = ((flags >> (e + 4)) & 1u) ? x.x[e] : 0;
+  }
+  f.part = part;
+  return f;
+}
+
+// Coefficients of the 8 components in a factor.
+inline Comb8 factor_comb(const Factor& f) {
+  Comb8 c{};
+  for (int e = 0; e < 4; ++e) {
+    if (f.part != PART_IM) c.s[e] = f.re[e];
+    if (f.part != PART_RE) c.s[e + 4] = f.im[e];
+  }
+  return c;
+}
+
+struct Product {
+  Factor l, r;
+  int w4[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// Add the real products of the complex product X*Y, contributing w4[e] * P to
+// complex output Q_e (real part -> component e, imaginary -> e+4).
+inline void add_complex_product(std::vector<Product>& out, const CComb& X, const CComb& Y,
+                                const int w4[4], unsigned fa, unsigned fb) {
+  const int cx = cls_of(X, fa), cy = cls_of(Y, fb);
+  if (cx == CLS_ZERO || cy == CLS_ZERO) return;
+  auto L = [&](int part) { return make_factor(X, fa, part); };
+  auto R = [&](int part) { return make_factor(Y, fb, part); };
+  // (left factor, right factor, coefficient in Re P, coefficient in Im P)
+  struct T { Factor l, r; int cre, cim; };
+  std::vector<T> terms;
+  if (cx == CLS_CX && cy == CLS_CX) {
+    // Gauss: P = (T1 - T2) + i (T3 - T1 - T2)
+    terms.push_back({L(PART_RE), R(PART_RE), +1, -1});
+    terms.push_back({L(PART_IM), R(PART_IM), -1, -1});
+    terms.push_back({L(PART_SUM), R(PART_SUM), 0, +1});
+  } else if (cx == CLS_RE) {
+    if (cy & CLS_RE) terms.push_back({L(PART_RE), R(PART_RE), +1, 0});
+    if (cy & CLS_IM) terms.push_back({L(PART_RE), R(PART_IM), 0, +1});
+  } else if (cx == CLS_IM) {
+    if (cy & CLS_IM) terms.push_back({L(PART_IM), R(PART_IM), -1, 0});
+    if (cy & CLS_RE) terms.push_back({L(PART_IM), R(PART_RE), 0, +1});
+  } else if (cy == CLS_RE) {  // X complex, Y real
+    terms.push_back({L(PART_RE), R(PART_RE), +1, 0});
+    terms.push_back({L(PART_IM), R(PART_RE), 0, +1});
+  } else {                    // X complex, Y imaginary
+    terms.push_back({L(PART_IM), R(PART_IM), -1, 0});
+    terms.push_back({L(PART_RE), R(PART_IM), 0, +1});
+  }
+  for (const T& t : terms) {
+    Product p;
+    p.l = t.l;
+    p.r = t.r;
+    for (int e = 0; e < 4; ++e) {
+      p.w4[e] = w4[e] * t.cre;
+      p.w4[e + 4] = w4[e] * t.cim;
+    }
+    out.push_back(p);
+  }
+}
+
+// The paper's bilinear scheme, Eq. bilinearH: left/right complex factors of
+// P1..P8 and the weights (times 4) of P_r in Q_1..Q_4.
+inline void bilinear_tables(CComb X[8], CComb Y[8], int w4[8][4]) {
+  static const int8_t xs[8][4] = {
+      {1, 0, 0, 0},    // P1: M1
+      {0, 0, 0, 1},    // P2: M4
+      {0, 1, 0, 0},    // P3: M2
+      {0, 0, 1, 0},    // P4: M3
+      {1, 1, 1, 1},    // P5: M1+M2+M3+M4
+      {1, 1, -1, -1},  // P6: M1+M2-M3-M4
+      {1, -1, 1, -1},  // P7: M1-M2+M3-M4
+      {1, -1, -1, 1}}; // P8: M1-M2-M3+M4
+  static const int8_t ys[8][4] = {
+      {1, 0, 0, 0},    // P1: N1
+      {0, 0, 1, 0},    // P2: N3
+      {0, 0, 0, 1},    // P3: N4
+      {0, 1, 0, 0},    // P4: N2
+      {1, 1, 1, 1}, {1, 1, -1, -1}, {1, -1, 1, -1}, {1, -1, -1, 1}};
+  // Q1 = 2P1 - (P5+P6+P7+P8)/4; Q2 = -2P2 + (P5+P6-P7-P8)/4;
+  // Q3 = -2P3 + (P5-P6+P7-P8)/4; Q4 = -2P4 + (P5-P6-P7+P8)/4  (times 4 below)
+  static const int wt[8][4] = {
+      {8, 0, 0, 0}, {0, -8, 0, 0}, {0, 0, -8, 0}, {0, 0, 0, -8},
+      {-1, 1, 1, 1}, {-1, 1, -1, -1}, {-1, -1, 1, -1}, {-1, -1, -1, 1}};
+  for (int r = 0; r < 8; ++r) {
+    for (int e = 0; e < 4; ++e) {
+      X[r].x[e] = xs[r][e];
+      Y[r].x[e] = ys[r][e];
+      w4[r][e] = wt[r][e];
+    }
+  }
+}
+
+// Merge products with identical factors (their weights add) and drop products
+// whose weights all vanish.
+inline std::vector<Product> merge(const std::vector<Product>& in) {
+  std::vector<Product> out;
+  for (const Product& p : in) {
+    bool merged = false;
+    for (Product& q : out) {
+      if (q.l == p.l && q.r == p.r) {
+        for (int e = 0; e < 8; ++e) q.w4[e] += p.w4[e];
+        merged = true;
+        break;
+      }
+    }
+    if (!merged) out.push_back(p);
+  }
+  std::vector<Product> kept;
+  for (const Product& p : out) {
+    bool any = false;
+    for (int e = 0; e < 8; ++e) any |= (p.w4[e] != 0);
+    if (any) kept.push_back(p);
+  }
+  return kept;
+}
+
+inline std::vector<Product> bilinear_products(unsigned fa, unsigned fb) {
+  CComb X[8], Y[8];
+  int w4[8][4];
+  bilinear_tables(X, Y, w4);
+  std::vector<Product> ps;
+  for (int r = 0; r < 8; ++r) add_complex_product(ps, X[r], Y[r], w4[r], fa, fb);
+  return merge(ps);
+}
+
+// Component-wise terms h[e][f][g] a_f b_g, expanded from the same bilinear
+// equations: 4 h[e][f][g] = sum_r w4[r][e] X_r[f] Y_r[g] (each 0 or +-4).
+inline std::vector<Product> direct_products(unsigned fa, unsigned fb) {
+  CComb X[8], Y[8];
+  int w4[8][4];
+  bilinear_tables(X, Y, w4);
+  std::vector<Product> ps;
+  for (int f = 0; f < 4; ++f)
+    for (int g = 0; g < 4; ++g) {
+      int w[4] = {0, 0, 0, 0};
+      bool any = false;
+      for (int e = 0; e < 4; ++e) {
+        int h = 0;
+        for (int r = 0; r < 8; ++r) h += w4[r][e] * X[r].x[f] * Y[r].x[g];
+        w[e] = h;
+        any |= (h != 0);
+      }
+      if (!any) continue;
+      CComb uf{}, ug{};
+      uf.x[f] = 1;
+      ug.x[g] = 1;
+      add_complex_product(ps, uf, ug, w, fa, fb);
+    }
+  return merge(ps);
+}
+
+// Assign factor slots and groups for one side.
+inline bool layout_side(const std::vector<Factor>& uniq, int8_t re[8][4], int8_t im[8][4],
+                        int8_t slot[8][3], int32_t* ngroups) {
+  std::vector<Factor> groups;
+  for (size_t f = 0; f < uniq.size(); ++f) {
+    int g = -1;
+    for (size_t i = 0; i < groups.size(); ++i)
+      if (groups[i].same_group(uniq[f])) { g = (int)i; break; }
+    if (g < 0) {
+      if (groups.size() >= 8) return false;
+      groups.push_back(uniq[f]);
+      g = (int)groups.size() - 1;
+      std::memcpy(re[g], uniq[f].re, 4);
+      std::memcpy(im[g], uniq[f].im, 4);
+      slot[g][0] = slot[g][1] = slot[g][2] = -1;
+    }
+    slot[g][uniq[f].part] = (int8_t)f;
+  }
+  *ngroups = (int32_t)groups.size();
+  return true;
+}
+
+}  // namespace detail
+
+// Build the kernel plan for component activity flags fa (of A) and fb (of B).
+inline bool build_plan(unsigned fa, unsigned fb, KPlan* out) {
+  using namespace detail;
+  fa &= 0xFFu;
+  fb &= 0xFFu;
+  std::vector<Product> bl = bilinear_products(fa, fb);
+  std::vector<Product> dr = direct_products(fa, fb);
+  const bool use_direct = dr.size() < bl.size();
+  const std::vector<Product>& ps = use_direct ? dr : bl;
+  if (ps.size() > (size_t)kMaxProducts) return false;
+  KPlan p;
+  std::memset(&p, 0, sizeof(p));
+  p.strategy = use_direct ? 1 : 0;
+  p.np = (int32_t)ps.size();
+  std::vector<Factor> lu, ru;
+  auto index_of = [](std::vector<Factor>& v, const Factor& f) {
+    for (size_t i = 0; i < v.size(); ++i)
+      if (v[i] == f) return (int)i;
+    v.push_back(f);
+    return (int)v.size() - 1;
+  };
+  for (size_t i = 0; i < ps.size(); ++i) {
+    p.pl[i] = (int8_t)index_of(lu, ps[i].l);
+    p.pr[i] = (int8_t)index_of(ru, ps[i].r);
+    for (int e = 0; e < 8; ++e) p.w4[e][i] = (int8_t)ps[i].w4[e];
+  }
+  p.nlf = (int32_t)lu.size();
+  p.nrf = (int32_t)ru.size();
+  if (!layout_side(lu, p.lre, p.lim, p.lslot, &p.nlg)) return false;
+  if (!layout_side(ru, p.rre, p.rim, p.rslot, &p.nrg)) return false;
+  *out = p;
+  return true;
+}
+
+// Sign of stored component c under op (Sec. III op equations; QC = vector part negated).
+inline int op_sign(int op, int c) {
+  static const int8_t m[5][8] = {
+      {+1, +1, +1, +1, +1, +1, +1, +1},   // N
+      {+1, +1, -1, +1, +1, +1, -1, +1},   // T
+      {+1, -1, +1, -1, -1, +1, -1, +1},   // C (complex conjugate)
+      {+1, -1, -1, -1, -1, +1, +1, +1},   // H (dagger)
+      {+1, -1, -1, -1, +1, -1, -1, -1}};  // QC (quaternion conjugate)
+  return m[op][c];
+}
+inline bool op_transposes(int op) { return op == 1 || op == 3; }
+
+// Coefficient of stored component c in left (side 0) or right (side 1) factor
+// slot f, op signs folded in (for tests and hmat_plan_info).
+inline void factor_row(const KPlan& p, int side, int f, int op, int8_t row[8]) {
+  const int ng = side ? p.nrg : p.nlg;
+  for (int c = 0; c < 8; ++c) row[c] = 0;
+  for (int g = 0; g < ng; ++g) {
+    const int8_t* slot = side ? p.rslot[g] : p.lslot[g];
+    const int8_t* re = side ? p.rre[g] : p.lre[g];
+    const int8_t* im = side ? p.rim[g] : p.lim[g];
+    for (int part = 0; part < 3; ++part) {
+      if (slot[part] != f) continue;
+      for (int e = 0; e < 4; ++e) {
+        if (part != 1) row[e] = (int8_t)(re[e] * op_sign(op, e));
+        if (part != 0) row[e + 4] = (int8_t)(im[e] * op_sign(op, e + 4));
+      }
+    }
+  }
+}
+
+}  // namespace hmat

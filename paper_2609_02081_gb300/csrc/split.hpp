@@ -1,0 +1,137 @@
+// split.hpp — split-precision (integer modular, Ozaki-type) mode: host-side interface.
+//
+// The exact integer products behind the bilinear scheme are computed on the
+// BF16 tensor cores:
+//   1. exponents : per row i of op(A) a power of two 2^s_i, per column j of
+//                  op(B) 2^t_j, so that every component scaled by it is < 2^b
+//                  in magnitude (one exponent shared by all eight components,
+//                  so the pre-additions of the bilinear scheme stay exact);
+//   2. encode    : X = round(op(A) 2^s) as integers, and for every modulus p
+//                  the residues of the plan's left factors (the Hadamard and
+//                  Gauss sums of Eq. bilinearH / Eq. cmplx-3-real-mult) in
+//                  [-128, 128], stored as BF16 in the tensor-core tile layout;
+//                  likewise the right factors of op(B);
+//   3. residue GEMM (tcgen05): every real product of the plan for every
+//                  modulus, BF16 x BF16 -> FP32 in tensor memory; FP32 sums of
+//                  integers below 2^24 are exact, so the accumulator is drained
+//                  every 1024 inner steps into int32 and reduced mod p at the end;
+//   4. CRT       : per output element the plan's recombination (weights 2,
+//                  -1/4, ... taken mod p), the Chinese remainder theorem over
+//                  the moduli (exact integer of up to ~140 bits), conversion to
+//                  FP64, the 2^-(s_i + t_j) rescaling and the complex alpha/beta
+//                  update (Sec. III scaling and addition).
+// The only rounding is step 2's scaling to b-bit integers; b and the modulus
+// count follow from the requested tolerance and k.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/hmat.h"
+#include "common.cuh"
+
+struct hmat_context;
+
+namespace hmat {
+
+constexpr int kMaxModuli = 18;
+constexpr int kModTable = 24;
+constexpr int kLimbs = 5;          // 160-bit CRT accumulators (32-bit limbs)
+constexpr int kTileM = 128;        // tcgen05 M (one TMEM lane per output row)
+constexpr int kTileK = 64;         // BF16 elements per 128-byte swizzled row
+constexpr int kChunkK = 1024;      // inner steps per exact FP32 accumulation chunk
+
+struct SplitParams {
+  int nmod = 0;
+  int bits = 0;
+  int moduli[kMaxModuli];
+  double log2P = 0.0;
+};
+
+// Moduli count and integer width for inner dimension k and target tolerance.
+hmat_status split_params(int64_t k, double tol, SplitParams* out);
+
+struct SplitShape {
+  int64_t m, n, k;
+  int np, nlf, nrf;
+};
+
+// Per-problem layout inside the caller's workspace.
+struct SplitJob {
+  JobDesc d;
+  int32_t nmod, bits, bn;           // moduli, integer width, tile N
+  int32_t tiles_m, tiles_n, nkb;    // 128-row tiles, bn-column tiles, 64-wide k blocks
+  int32_t np, nlf, nrf;
+  int8_t pl[kMaxProducts], pr[kMaxProducts];
+  int64_t off_sexp, off_texp;       // int32 exponents (bytes into workspace)
+  int64_t off_encA, off_encB;       // BF16 factor tiles
+  int64_t off_res;                  // int8 product residues
+  int64_t item_begin;               // residue-GEMM work items before this job
+  int64_t encA_begin, encB_begin;   // encode work units before this job
+  int64_t crt_begin;                // CRT work units before this job
+  int64_t exp_begin;                // exponent work units before this job
+};
+
+// Workspace bytes for a set of problems (sum of the per-problem layouts).
+hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, size_t* bytes);
+
+// Handle-owned state of the split path (job-table staging).
+struct SplitState {
+  SplitJob* h_jobs = nullptr;
+  SplitJob* d_jobs = nullptr;
+  size_t cap = 0;
+  cudaEvent_t done = nullptr;
+  bool used = false;
+};
+
+cudaError_t split_configure();
+void split_release(SplitState& s);
+
+// Split-mode jobs of one call with their layouts and per-stage unit counts.
+struct SplitPrep {
+  std::vector<SplitJob> jobs;
+  int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
+  int64_t ws_needed = 0;
+};
+
+// Lay the jobs out in a workspace of ws_bytes (WORKSPACE_TOO_SMALL if it does not fit).
+hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
+                          SplitPrep* out);
+// Launch the four stages reading the device job table d_jobs.
+hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d_jobs, const KPlan* d_plans,
+                         unsigned char* ws, cudaStream_t stream);
+// Upload the job table through the handle's staging buffer, then split_launch.
+hmat_status run_split(hmat_context* h, const SplitPrep& sp, const KPlan* d_plans, void* workspace,
+                      cudaStream_t stream);
+
+// Profiling bracket around one kernel launch (no-op unless profiling is on).
+class ProfScope {
+ public:
+  ProfScope(hmat_context* h, int kernel, cudaStream_t stream);
+  ~ProfScope();
+
+ private:
+  hmat_context* h_;
+  int kernel_;
+  cudaStream_t stream_;
+  cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
+int handle_sm_count(hmat_context* h);
+SplitState& handle_split(hmat_context* h);
+
+
+// Device-side kernel launchers (split_kernels.cu).
+struct SplitConsts;
+cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int grid, cudaStream_t s,
+                                   unsigned char* ws);
+cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int side, int64_t units,
+                                cudaStream_t s, unsigned char* ws);
+cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
+                              unsigned char* ws);
+cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
+                             cudaStream_t s, unsigned char* ws);
+cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint32_t* crt_c, const uint32_t* crt_P);
+
+}  // namespace hmat

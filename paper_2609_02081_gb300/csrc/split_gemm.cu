@@ -1,0 +1,418 @@
+// split_gemm.cu — residue GEMM of the split mode on the 5th-generation tensor cores.
+//
+// Work item = (problem, modulus l, product p, 128 x bn output tile).  For the
+// item the kernel computes T = L_f R_g^T over the padded inner dimension, where
+// L_f / R_g are the BF16-encoded residues of the plan's left / right factors
+// (values in [-128, 128]), and stores T mod p_l (centred int8).
+//
+// Exactness: every BF16 product is an integer of magnitude <= 2^14 and FP32
+// partial sums of at most 1024 of them stay <= 2^24, so the tensor-memory
+// accumulator is exact chunk by chunk; each 1024-deep chunk is drained into
+// int32 registers (exact), and the sum is reduced mod p at the end of the item.
+//
+// Structure (one persistent CTA per SM, 320 threads):
+//   warp 0      producer: 1-D bulk copies (cp.async.bulk, TMA engine) of the
+//               pre-swizzled 16 KB A tile and bn x 128 B B tile per 64-deep
+//               k-block into a 4-stage shared-memory ring (mbarrier tx counts);
+//   warp 1      allocates 512 TMEM columns; one lane issues tcgen05.mma
+//               (kind::f16, BF16 in, FP32 accumulate, M=128, N=bn, K=16) into
+//               one of two accumulator buffers, commits stages and chunks;
+//   warps 2..9  epilogue: tcgen05.ld of finished chunks (each warp its 32-lane
+//               quadrant and half the columns), int32 accumulation, mod p,
+//               int8 stores.  Two accumulator buffers let chunk c+1 run on the
+//               tensor core while chunk c is drained.
+// Every mbarrier wait is bounded (~2 s); on timeout the CTA raises the device
+// error word, stops, waits (bounded) for its own copies and MMAs and frees TMEM.
+#include <cuda_runtime.h>
+
+#include "split.hpp"
+
+namespace hmat {
+
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kBnMax = 256;
+constexpr int kATileBytes = kTileM * kTileK * 2;       // 16 KB
+constexpr int kBTileBytesMax = kBnMax * kTileK * 2;    // 32 KB
+constexpr int kThreads = 320;
+constexpr int kEpiWarps = 8;
+constexpr int kTmemCols = 2 * kBnMax;
+constexpr int kKbPerChunk = kChunkK / kTileK;          // 16
+constexpr long long kWaitCycles = 4000000000ll;        // ~2 s at 2 GHz
+constexpr int kRasterGroup = 16;                        // tile rows per raster group
+
+struct GemmSmem {
+  uint8_t a[kStages][kATileBytes];
+  uint8_t b[kStages][kBTileBytesMax];
+  uint64_t full[kStages];
+  uint64_t empty[kStages];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t final_bar;
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: true when the phase with `parity` completed; false on abort/timeout.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* err,
+                                          uint32_t err_bit) {
+  long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try(bar, parity)) return true;
+    if ((it & 63u) == 63u) {
+      if (*abort_flag) return false;
+      const long long now = clock64();
+      if (t0 == 0) t0 = now;
+      else if (now - t0 > kWaitCycles) {
+        *abort_flag = 1;
+        atomicOr(err, err_bit);
+        return false;
+      }
+    }
+  }
+}
+__device__ __forceinline__ void mbar_arrive_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);      // start address
+  d |= (uint64_t)1u << 16;                      // leading-dimension byte offset (unused for this swizzle)
+  d |= (uint64_t)(1024u >> 4) << 32;            // stride-dimension byte offset: 1024 B
+  d |= (uint64_t)1u << 46;                      // descriptor version
+  d |= (uint64_t)2u << 61;                      // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n.
+__device__ __forceinline__ uint32_t instr_desc(int n) {
+  return (1u << 4)                      // D format F32
+         | (1u << 7)                    // A format BF16
+         | (1u << 10)                   // B format BF16
+         | ((uint32_t)(n >> 3) << 17)   // N / 8
+         | ((uint32_t)(kTileM >> 4) << 24);  // M / 16
+}
+
+#define TMEM_LD32(taddr, r)                                                                                        \
+  asm volatile(                                                                                                    \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18," \
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                                               \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),     \
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),   \
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])    \
+      : "r"(taddr))
+
+struct Item {
+  const uint8_t* a;   // first k-block tile of the left factor
+  const uint8_t* b;   // first k-block tile of the right factor
+  int8_t* out;        // residue tile origin (row 0, column 0 of the tile)
+  int64_t ncols;      // residue row pitch
+  int nkb, bn, l;
+};
+
+__device__ __forceinline__ int find_item_job(const SplitJob* jobs, int njobs, int64_t u) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].item_begin <= u) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ Item decode_item(const SplitJob* jobs, int njobs, int64_t item, uint8_t* ws) {
+  const SplitJob& sj = jobs[find_item_job(jobs, njobs, item)];
+  const int64_t local = item - sj.item_begin;
+  const int64_t ntile = (int64_t)sj.tiles_m * sj.tiles_n;
+  const int64_t tile = local % ntile;
+  const int64_t rest = local / ntile;
+  const int p = (int)(rest % sj.np);
+  const int l = (int)(rest / sj.np);
+  // grouped raster: kRasterGroup tile rows, column-major inside the group
+  const int64_t per_group = (int64_t)kRasterGroup * sj.tiles_n;
+  const int grp = (int)(tile / per_group);
+  const int64_t within = tile % per_group;
+  const int rows_here = min(kRasterGroup, sj.tiles_m - grp * kRasterGroup);
+  const int tm = grp * kRasterGroup + (int)(within % rows_here);
+  const int tn = (int)(within / rows_here);
+  Item it;
+  it.nkb = sj.nkb;
+  it.bn = sj.bn;
+  it.l = l;
+  const int64_t a_tile = (int64_t)kATileBytes;
+  const int64_t b_tile = (int64_t)sj.bn * kTileK * 2;
+  it.a = ws + sj.off_encA + ((((int64_t)l * sj.nlf + sj.pl[p]) * sj.tiles_m + tm) * sj.nkb) * a_tile;
+  it.b = ws + sj.off_encB + ((((int64_t)l * sj.nrf + sj.pr[p]) * sj.tiles_n + tn) * sj.nkb) * b_tile;
+  it.ncols = (int64_t)sj.tiles_n * sj.bn;
+  const int64_t plane = (int64_t)sj.tiles_m * kTileM * it.ncols;
+  it.out = reinterpret_cast<int8_t*>(ws + sj.off_res) + ((int64_t)l * sj.np + p) * plane +
+           (int64_t)tm * kTileM * it.ncols + (int64_t)tn * sj.bn;
+  return it;
+}
+
+// Centred residue of a signed 32-bit value modulo p (exact, any magnitude).
+__device__ __forceinline__ int cmod32(int x, int p, unsigned long long fm) {
+  auto fmod_u = [&](uint32_t v) { return (uint32_t)__umul64hi(fm * (unsigned long long)v, (unsigned long long)p); };
+  const uint32_t lo = (uint32_t)x & 0xFFFFu;
+  const int hi = x >> 16;
+  const uint32_t rhi = fmod_u((uint32_t)(hi + 256 * p));
+  const uint32_t r = fmod_u(rhi * fmod_u(65536u) + fmod_u(lo));
+  return (int)r > ((p - 1) >> 1) ? (int)r - p : (int)r;
+}
+
+}  // namespace
+
+struct GemmModConst {
+  int p;
+  unsigned long long fm;
+};
+__constant__ GemmModConst c_gmod[kModTable];
+
+__global__ void __launch_bounds__(kThreads, 1)
+split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t total_items, uint8_t* ws,
+                          uint32_t* err) {
+  extern __shared__ uint8_t smem_dyn[];
+  // 1024-byte alignment for the swizzled operand tiles
+  const uint32_t raw = smem_u32(smem_dyn);
+  const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+  GemmSmem& s = *reinterpret_cast<GemmSmem*>(smem_dyn + pad);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort_flag = &s.abort_flag;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(smem_u32(&s.full[i]), 1);
+      mbar_init(smem_u32(&s.empty[i]), 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(smem_u32(&s.tfull[i]), 1);
+      mbar_init(smem_u32(&s.tempty[i]), kEpiWarps);
+    }
+    mbar_init(smem_u32(&s.final_bar), 1);
+    s.abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s.tmem_base)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s.tmem_base;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    int armed[kStages];
+#pragma unroll
+    for (int i = 0; i < kStages; ++i) armed[i] = -1;
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
+        const Item it = decode_item(jobs, njobs, item, ws);
+        const uint32_t bbytes = (uint32_t)it.bn * kTileK * 2;
+        for (int kb = 0; kb < it.nkb; ++kb) {
+          if (!mbar_wait(smem_u32(&s.empty[stage]), phase ^ 1u, abort_flag, err, kErrWaitProducer)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&s.full[stage]);
+          mbar_arrive_tx(fb, (uint32_t)kATileBytes + bbytes);
+          bulk_g2s(smem_u32(s.a[stage]), it.a + (int64_t)kb * kATileBytes, (uint32_t)kATileBytes, fb);
+          bulk_g2s(smem_u32(s.b[stage]), it.b + (int64_t)kb * bbytes, bbytes, fb);
+          armed[stage] = (int)phase;
+          if (++stage == kStages) { stage = 0; phase ^= 1u; }
+        }
+      }
+      if (!ok) {
+        // wait (bounded, no abort check) for copies this thread started
+        for (int i = 0; i < kStages; ++i) {
+          if (armed[i] < 0) continue;
+          long long t0 = clock64();
+          while (!mbar_try(smem_u32(&s.full[i]), (uint32_t)armed[i]) && clock64() - t0 < kWaitCycles / 8) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t chunk_ctr = 0;
+      bool ok = true;
+      bool issued = false;
+      for (int64_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
+        const Item it = decode_item(jobs, njobs, item, ws);
+        const uint32_t idesc = instr_desc(it.bn);
+        const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
+        for (int c = 0; ok && c < nchunks; ++c) {
+          const uint32_t buf = chunk_ctr & 1u, aph = (chunk_ctr >> 1) & 1u;
+          if (!mbar_wait(smem_u32(&s.tempty[buf]), aph ^ 1u, abort_flag, err, kErrWaitMma)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d_tmem = tmem + buf * kBnMax;
+          const int kb0 = c * kKbPerChunk, kb1 = min(it.nkb, kb0 + kKbPerChunk);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(smem_u32(&s.full[stage]), phase, abort_flag, err, kErrWaitMma)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t ad = smem_desc(smem_u32(s.a[stage]));
+            const uint64_t bd = smem_desc(smem_u32(s.b[stage]));
+#pragma unroll
+            for (int kk = 0; kk < kTileK / 16; ++kk) {
+              // advance 16 BF16 = 32 bytes along K inside the swizzled row (+2 in 16-byte units)
+              tc_mma(d_tmem, ad + 2ull * kk, bd + 2ull * kk, idesc, (kb > kb0 || kk > 0) ? 1u : 0u);
+            }
+            issued = true;
+            tc_commit(smem_u32(&s.empty[stage]));
+            if (++stage == kStages) { stage = 0; phase ^= 1u; }
+          }
+          if (!ok) break;
+          tc_commit(smem_u32(&s.tfull[buf]));
+          ++chunk_ctr;
+        }
+      }
+      if (!ok && issued) {
+        // let every issued MMA finish before TMEM is released
+        tc_commit(smem_u32(&s.final_bar));
+        long long t0 = clock64();
+        while (!mbar_try(smem_u32(&s.final_bar), 0u) && clock64() - t0 < kWaitCycles / 8) {
+        }
+      }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;               // TMEM lane quadrant of this warp
+    const int half = (warp - 2) >> 2;     // which half of the tile's columns
+    const int row = q * 32 + lane;
+    uint32_t chunk_ctr = 0;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
+      const Item it = decode_item(jobs, njobs, item, ws);
+      const int cols = it.bn >> 1;        // columns handled by this thread: 32, 64 or 128
+      const int col0 = half * cols;
+      const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
+      int acc[kBnMax / 2];
+#pragma unroll
+      for (int i = 0; i < kBnMax / 2; ++i) acc[i] = 0;
+      for (int c = 0; c < nchunks; ++c) {
+        const uint32_t buf = chunk_ctr & 1u, aph = (chunk_ctr >> 1) & 1u;
+        // one lane waits, the warp follows (tcgen05.ld is warp-collective)
+        int got = 0;
+        if (lane == 0) got = mbar_wait(smem_u32(&s.tfull[buf]), aph, abort_flag, err, kErrWaitEpilogue) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * kBnMax + (uint32_t)col0;
+#pragma unroll
+        for (int g = 0; g < kBnMax / 2 / 32; ++g) {
+          if (g * 32 < cols) {
+            uint32_t r[32];
+            TMEM_LD32(taddr + (uint32_t)(g * 32), r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int i = 0; i < 32; ++i) acc[g * 32 + i] += __float2int_rn(__uint_as_float(r[i]));
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s.tempty[buf]));
+        ++chunk_ctr;
+      }
+      if (!ok) break;
+      // reduce mod p and store this row's residues (16-byte stores)
+      const int p = c_gmod[it.l].p;
+      const unsigned long long fm = c_gmod[it.l].fm;
+      int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
+#pragma unroll
+      for (int g = 0; g < kBnMax / 2 / 16; ++g) {
+        if (g * 16 < cols) {
+          uint32_t w[4];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            uint32_t packed = 0;
+#pragma unroll
+            for (int bidx = 0; bidx < 4; ++bidx) {
+              const int rr = cmod32(acc[g * 16 + v * 4 + bidx], p, fm);
+              packed |= ((uint32_t)(rr & 0xFF)) << (8 * bidx);
+            }
+            w[v] = packed;
+          }
+          *reinterpret_cast<uint4*>(dst + g * 16) = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+size_t split_gemm_smem_bytes() { return sizeof(GemmSmem) + 1024; }
+
+cudaError_t split_gemm_configure(const int* moduli, int n) {
+  GemmModConst g[kModTable];
+  for (int l = 0; l < kModTable; ++l) {
+    const int p = l < n ? moduli[l] : 255;
+    g[l].p = p;
+    g[l].fm = ~0ull / (unsigned long long)p + 1ull;
+  }
+  cudaError_t e = cudaMemcpyToSymbol(c_gmod, g, sizeof(g));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(split_residue_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)split_gemm_smem_bytes());
+}
+
+cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
+                              unsigned char* ws) {
+  if (items <= 0) return cudaSuccess;
+  split_residue_gemm_kernel<<<grid, kThreads, split_gemm_smem_bytes(), s>>>(d_jobs, njobs, items, ws,
+                                                                             device_error_ptr());
+  return cudaGetLastError();
+}
+
+}  // namespace hmat

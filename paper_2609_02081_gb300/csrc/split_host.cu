@@ -1,0 +1,254 @@
+// split_host.cu — split-mode parameters, CRT constants, workspace layout and launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "split.hpp"
+
+namespace hmat {
+
+size_t split_gemm_smem_bytes();
+cudaError_t split_gemm_configure(const int* moduli, int n);
+
+// Odd, pairwise coprime moduli <= 255 (largest first): 255 = 3*5*17,
+// 253 = 11*23, 247 = 13*19, 217 = 7*31, the rest prime.  Residues are centred
+// in [-(p-1)/2, (p-1)/2] = [-127, 127] (exact in BF16, fit int8) and p >= 149.
+static const int kModuli[kModTable] = {255, 253, 251, 247, 241, 239, 233, 229, 227, 223, 217, 211,
+                                       199, 197, 193, 191, 181, 179, 173, 167, 163, 157, 151, 149};
+
+// Margin (bits) between the requested tolerance and the integer width: the
+// scaling error of one operand element is <= 2^-b of its row/column maximum,
+// and sums over k of such errors relative to the result stay well below 2^6.
+static constexpr int kBitsMargin = 6;
+
+hmat_status split_params(int64_t k, double tol, SplitParams* out) {
+  if (tol == 0.0) tol = 1e-12;
+  if (!(tol > 0.0) || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
+  // drained int32 accumulators hold up to 127 chunks of 1024
+  if (k > (int64_t)127 * kChunkK) return HMAT_STATUS_UNSUPPORTED;
+  SplitParams sp;
+  const int want = (int)std::ceil(-std::log2(tol));
+  // operands are rounded to at most 52-bit integers: below ~2^-50 nothing is promised
+  if (want + 2 > 52) return HMAT_STATUS_TOLERANCE_UNREACHABLE;
+  int bits = std::max(10, std::min(52, want + kBitsMargin));
+  // the exact integer result of one output component is a sum of at most 8 real
+  // products over k of b-bit integers: |Q| <= 8 k 2^(2b); CRT needs P > 2 |Q|
+  const double need = 2.0 * bits + std::log2((double)std::max<int64_t>(k, 1)) + 4.0 + 0.25;
+  double acc = 0.0;
+  int n = 0;
+  while (acc <= need) {
+    if (n >= kMaxModuli) return HMAT_STATUS_TOLERANCE_UNREACHABLE;
+    sp.moduli[n] = kModuli[n];
+    acc += std::log2((double)kModuli[n]);
+    ++n;
+  }
+  sp.nmod = n;
+  sp.bits = bits;
+  sp.log2P = acc;
+  *out = sp;
+  return HMAT_STATUS_SUCCESS;
+}
+
+// ----------------------------------------------------------------- tiny big integers (32-bit limbs)
+namespace {
+
+void big_mul_small(uint32_t* x, uint32_t m) {
+  unsigned long long c = 0;
+  for (int q = 0; q < kLimbs; ++q) {
+    const unsigned long long t = (unsigned long long)x[q] * m + c;
+    x[q] = (uint32_t)t;
+    c = t >> 32;
+  }
+}
+uint32_t big_mod_small(const uint32_t* x, uint32_t m) {
+  unsigned long long r = 0;
+  for (int q = kLimbs - 1; q >= 0; --q) r = ((r << 32) | x[q]) % m;
+  return (uint32_t)r;
+}
+uint32_t inv_mod(uint32_t a, uint32_t m) {
+  for (uint32_t x = 1; x < m; ++x)
+    if ((unsigned long long)a * x % m == 1) return x;
+  return 0;
+}
+
+}  // namespace
+
+cudaError_t split_configure() {
+  static uint32_t crt[kMaxModuli + 1][kMaxModuli][kLimbs];
+  static uint32_t P[kMaxModuli + 1][kLimbs];
+  std::memset(crt, 0, sizeof(crt));
+  std::memset(P, 0, sizeof(P));
+  for (int n = 1; n <= kMaxModuli; ++n) {
+    P[n][0] = 1;
+    for (int l = 0; l < n; ++l) big_mul_small(P[n], (uint32_t)kModuli[l]);
+    for (int l = 0; l < n; ++l) {
+      // c_l = (P / p_l) * ((P / p_l)^-1 mod p_l)
+      uint32_t Ml[kLimbs] = {1, 0, 0, 0, 0};
+      for (int j = 0; j < n; ++j)
+        if (j != l) big_mul_small(Ml, (uint32_t)kModuli[j]);
+      const uint32_t inv = inv_mod(big_mod_small(Ml, (uint32_t)kModuli[l]), (uint32_t)kModuli[l]);
+      big_mul_small(Ml, inv);
+      std::memcpy(crt[n][l], Ml, sizeof(Ml));
+    }
+  }
+  cudaError_t e = split_upload_constants(kModuli, kModTable, &crt[0][0][0], &P[0][0]);
+  if (e != cudaSuccess) return e;
+  return split_gemm_configure(kModuli, kModTable);
+}
+
+void split_release(SplitState& s) {
+  if (s.used && s.done) cudaEventSynchronize(s.done);
+  if (s.done) cudaEventDestroy(s.done);
+  if (s.h_jobs) cudaFreeHost(s.h_jobs);
+  if (s.d_jobs) cudaFree(s.d_jobs);
+  s = SplitState();
+}
+
+// ----------------------------------------------------------------- layout
+static int pick_bn(int64_t n) {
+  if (n > 128) return 256;
+  if (n > 64) return 128;
+  return 64;
+}
+
+static inline int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+// Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
+static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, SplitJob* sj, int64_t* offset) {
+  SplitParams sp;
+  hmat_status st = split_params(sh.k, tol, &sp);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  sj->nmod = sp.nmod;
+  sj->bits = sp.bits;
+  sj->bn = pick_bn(sh.n);
+  sj->tiles_m = (int32_t)((sh.m + kTileM - 1) / kTileM);
+  sj->tiles_n = (int32_t)((sh.n + sj->bn - 1) / sj->bn);
+  sj->nkb = (int32_t)((sh.k + kTileK - 1) / kTileK);
+  sj->np = sh.np;
+  sj->nlf = sh.nlf;
+  sj->nrf = sh.nrf;
+  if (plan) {
+    for (int p = 0; p < kMaxProducts; ++p) {
+      sj->pl[p] = plan->pl[p];
+      sj->pr[p] = plan->pr[p];
+    }
+  }
+  int64_t off = *offset;
+  sj->off_sexp = off;
+  off = align256(off + 4 * sh.m);
+  sj->off_texp = off;
+  off = align256(off + 4 * sh.n);
+  sj->off_encA = off;
+  off = align256(off + (int64_t)sj->nmod * sj->nlf * sj->tiles_m * sj->nkb * kTileM * kTileK * 2);
+  sj->off_encB = off;
+  off = align256(off + (int64_t)sj->nmod * sj->nrf * sj->tiles_n * sj->nkb * sj->bn * kTileK * 2);
+  sj->off_res = off;
+  off = align256(off + (int64_t)sj->nmod * sj->np * ((int64_t)sj->tiles_m * kTileM) * ((int64_t)sj->tiles_n * sj->bn));
+  *offset = off;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, size_t* bytes) {
+  int64_t off = 0;
+  for (const SplitShape& sh : shapes) {
+    SplitJob sj;
+    std::memset(&sj, 0, sizeof(sj));
+    hmat_status st = layout_job(sh, nullptr, tol, &sj, &off);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+  }
+  *bytes = (size_t)off;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
+                          SplitPrep* out) {
+  SplitPrep sp;
+  int64_t off = 0;
+  for (const JobDesc& d : jobs) {
+    const KPlan& P = h_plans[d.plan];
+    SplitJob sj;
+    std::memset(&sj, 0, sizeof(sj));
+    sj.d = d;
+    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf};
+    hmat_status st = layout_job(sh, &P, tol, &sj, &off);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+    sj.exp_begin = sp.exp_units;
+    sp.exp_units += (d.m + 31) / 32 + (d.n + 31) / 32;
+    sj.encA_begin = sp.encA_units;
+    sp.encA_units += (int64_t)sj.nmod * sj.tiles_m * kTileM * sj.nkb * (kTileK / 8);
+    sj.encB_begin = sp.encB_units;
+    sp.encB_units += (int64_t)sj.nmod * sj.tiles_n * sj.bn * sj.nkb * (kTileK / 8);
+    sj.item_begin = sp.items;
+    sp.items += (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
+    sj.crt_begin = sp.crt_units;
+    sp.crt_units += (int64_t)d.m * d.n;
+    sp.jobs.push_back(sj);
+  }
+  if ((size_t)off > ws_bytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
+  sp.ws_needed = off;
+  *out = std::move(sp);
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d_jobs, const KPlan* d_plans,
+                         unsigned char* ws, cudaStream_t stream) {
+  const int njobs = (int)sp.jobs.size();
+  cudaError_t e;
+  {
+    ProfScope ps(h, 1, stream);
+    e = launch_split_exponents(d_jobs, njobs, sp.exp_units, 0, stream, ws);
+  }
+  if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  {
+    ProfScope ps(h, 2, stream);
+    e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws);
+    if (e == cudaSuccess) e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws);
+  }
+  if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  {
+    ProfScope ps(h, 3, stream);
+    const int grid = (int)std::min<int64_t>(sp.items, handle_sm_count(h));
+    e = launch_split_gemm(d_jobs, njobs, sp.items, grid, stream, ws);
+  }
+  if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  {
+    ProfScope ps(h, 4, stream);
+    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws);
+  }
+  return e == cudaSuccess ? HMAT_STATUS_SUCCESS : HMAT_STATUS_CUDA_ERROR;
+}
+
+// Upload the job table through the handle's staging buffer and launch.
+hmat_status run_split(hmat_context* h, const SplitPrep& sp, const KPlan* d_plans, void* workspace,
+                      cudaStream_t stream) {
+  SplitState& s = handle_split(h);
+  if (s.used) {
+    if (cudaEventSynchronize(s.done) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  }
+  if (!s.done && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess)
+    return HMAT_STATUS_CUDA_ERROR;
+  if (s.cap < sp.jobs.size()) {
+    if (s.h_jobs) cudaFreeHost(s.h_jobs);
+    if (s.d_jobs) cudaFree(s.d_jobs);
+    s.h_jobs = nullptr;
+    s.d_jobs = nullptr;
+    s.cap = 0;
+    const size_t cap = std::max<size_t>(sp.jobs.size(), 16);
+    if (cudaMallocHost(&s.h_jobs, cap * sizeof(SplitJob)) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+    if (cudaMalloc(&s.d_jobs, cap * sizeof(SplitJob)) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+    s.cap = cap;
+  }
+  std::memcpy(s.h_jobs, sp.jobs.data(), sp.jobs.size() * sizeof(SplitJob));
+  if (cudaMemcpyAsync(s.d_jobs, s.h_jobs, sp.jobs.size() * sizeof(SplitJob), cudaMemcpyHostToDevice, stream) !=
+      cudaSuccess)
+    return HMAT_STATUS_CUDA_ERROR;
+  hmat_status st = split_launch(h, sp, s.d_jobs, d_plans, static_cast<unsigned char*>(workspace), stream);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  if (cudaEventRecord(s.done, stream) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  s.used = true;
+  return HMAT_STATUS_SUCCESS;
+}
+
+}  // namespace hmat

@@ -1,0 +1,132 @@
+"""Host-side checks (no GPU): the C-ABI library, the product plans, split-mode parameters."""
+import itertools
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import bq_inputs as bi
+import oracle
+import paper_2609_02081_gb300 as hm
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "hmat.h")
+FLAGS = [bi.REAL, bi.COMPLEX, bi.TRS, bi.TRA, bi.BQ]
+FLAG_NAME = {bi.REAL: "R", bi.COMPLEX: "C", bi.TRS: "TRS", bi.TRA: "TRA", bi.BQ: "BQ"}
+OPS = ["N", "T", "C", "H", "QC"]
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(hmat_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = hm.lib()
+    names = declared_functions()
+    assert len(names) >= 14
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in hm.SIGNATURES, f"binding lacks {name}"
+    assert set(hm.SIGNATURES) == set(names)
+    assert L.hmat_version() >= 100
+    assert L.hmat_status_string(0) == b"success"
+    assert L.hmat_status_string(4) == b"workspace too small"
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(hm.HmatError) as ei:
+        hm.Handle()
+    assert ei.value.status == 5   # CUDA_ERROR
+
+
+def structure_tensor(opA, opB):
+    """T[e, c, d]: component e of op(a) op(b) for one-hot 1x1 a (component c), b (component d)."""
+    T = np.zeros((8, 8, 8))
+    for c in range(8):
+        a = np.zeros((8, 1, 1)); a[c] = 1.0
+        for d in range(8):
+            b = np.zeros((8, 1, 1)); b[d] = 1.0
+            T[:, c, d] = oracle.bq_gemm(a, b, opA, opB)[:, 0, 0]
+    return T
+
+
+@pytest.mark.parametrize("fa,fb", list(itertools.product(FLAGS, FLAGS)))
+def test_plan_reproduces_structure_tensor(fa, fb):
+    for opA, opB in [("N", "N"), ("T", "H"), ("C", "QC"), ("H", "N")]:
+        P, U, V, W, _ = hm.plan_info(opA, opB, fa, fb)
+        T = structure_tensor(opA, opB)
+        got = np.einsum("ep,pc,pd->ecd", W, U.astype(float), V.astype(float))
+        mask = np.zeros((8, 8, 8), bool)
+        for c in range(8):
+            for d in range(8):
+                mask[:, c, d] = bool((fa >> c) & 1) and bool((fb >> d) & 1)
+        np.testing.assert_array_equal(got[mask], T[mask])
+        # absent components are never read
+        for c in range(8):
+            if not (fa >> c) & 1:
+                assert np.all(U[:, c] == 0)
+            if not (fb >> c) & 1:
+                assert np.all(V[:, c] == 0)
+
+
+def test_bilinear_24_and_reduced_counts():
+    """Sec. III B: 64 -> 24 for full biquaternions, 16 -> 8 for real / imaginary quaternions."""
+    counts = {(FLAG_NAME[a], FLAG_NAME[b]): hm.plan_info("N", "N", a, b)[0] for a in FLAGS for b in FLAGS}
+    assert counts[("BQ", "BQ")] == 24
+    assert hm.plan_info("N", "N", bi.BQ, bi.BQ)[4] == 0          # the paper's bilinear scheme
+    for pair in [("TRS", "TRS"), ("TRA", "TRA"), ("TRS", "TRA"), ("TRA", "TRS")]:
+        assert counts[pair] == 8
+    want = {("R", "R"): 1, ("R", "C"): 2, ("R", "TRS"): 4, ("R", "TRA"): 4, ("R", "BQ"): 8,
+            ("C", "C"): 3, ("C", "TRS"): 8, ("C", "TRA"): 8, ("C", "BQ"): 12,
+            ("TRS", "BQ"): 16, ("TRA", "BQ"): 16}
+    for (a, b), n in want.items():
+        assert counts[(a, b)] == n, (a, b, counts[(a, b)])
+        assert counts[(b, a)] == n, (b, a, counts[(b, a)])
+
+
+def test_bq_plan_weights_are_the_papers():
+    """Full plan: 8 complex products, weights 2 or 1/4 (Eq. bilinearH), Gauss triplets."""
+    P, U, V, W, _ = hm.plan_info("N", "N", bi.BQ, bi.BQ)
+    vals = set(np.round(np.abs(W[W != 0]), 6))
+    assert vals <= {2.0, 0.25}
+    # Gauss: every product is Re*Re, Im*Im or (Re+Im)*(Re+Im) of one complex factor
+    kinds = []
+    for p in range(P):
+        re_l, im_l = U[p, :4] != 0, U[p, 4:] != 0
+        re_r, im_r = V[p, :4] != 0, V[p, 4:] != 0
+        kinds.append((re_l.any(), im_l.any(), re_r.any(), im_r.any()))
+    assert kinds.count((True, False, True, False)) == 8
+    assert kinds.count((False, True, False, True)) == 8
+    assert kinds.count((True, True, True, True)) == 8
+
+
+def _coprime(a, b):
+    return math.gcd(a, b) == 1
+
+
+@pytest.mark.parametrize("k,tol", [(1, 1e-12), (256, 1e-12), (4096, 1e-12), (8192, 1e-12), (24576, 1e-12),
+                                   (1024, 1e-6), (8192, 1e-14)])
+def test_split_parameters(k, tol):
+    mods, bits = hm.split_info(k, tol)
+    assert all(m % 2 == 1 and 129 < m <= 255 for m in mods)
+    assert all(_coprime(a, b) for a, b in itertools.combinations(mods, 2))
+    log2P = sum(math.log2(m) for m in mods)
+    # CRT range covers the exact integer outputs: |Q| <= 8 k 2^(2b), P > 2|Q|
+    assert log2P > 2 * bits + math.log2(max(k, 1)) + 4
+    # the scaling error 2^-b sits below the target
+    assert 2.0 ** (-bits) < tol / 16
+    # residues in [-127, 127]: 1024-deep FP32 sums of products stay exact
+    assert 1024 * 127 * 127 < 2 ** 24
+
+
+def test_split_limits():
+    with pytest.raises(hm.HmatError):
+        hm.split_info(200000, 1e-12)           # beyond the int32 drained accumulators
+    with pytest.raises(hm.HmatError):
+        hm.split_info(8192, 1e-30)             # beyond the modulus table

@@ -1,0 +1,195 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact on small-integer inputs (every FP64 step and every residue step is
+exact there); within the relative-Frobenius tolerance 1e-12 on random data.
+"""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import bq_inputs as bi
+import oracle
+import paper_2609_02081_gb300 as hm
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+OPS = ["N", "T", "C", "H", "QC"]
+MODES = ["fp64", "split"]
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    with hm.Handle() as h:
+        yield h
+        assert h.device_error() == 0
+
+
+def stored(op, rows, cols):
+    return (cols, rows) if op in ("T", "H") else (rows, cols)
+
+
+def run(handle, A, B, opA="N", opB="N", fa=bi.BQ, fb=bi.BQ, alpha=1.0, beta=0.0, C0=None, mode="fp64",
+        m=None, n=None):
+    dev = torch.device("cuda")
+    if m is None:
+        m = A.shape[2] if opA in ("T", "H") else A.shape[1]
+    if n is None:
+        n = B.shape[1] if opB in ("T", "H") else B.shape[2]
+    C = (C0.clone() if C0 is not None else torch.full((8, m, n), float("nan"), dtype=torch.float64)).to(dev)
+    hm.hmat_bq_gemm(handle, A.to(dev), B.to(dev), C, opA, opB, fa, fb, alpha, beta, mode=mode, tol=TOL)
+    torch.cuda.synchronize()
+    return C.cpu().numpy()
+
+
+def rel(got, want):
+    return np.linalg.norm(got - want) / max(np.linalg.norm(want), 1e-300)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("opA,opB", list(itertools.product(OPS, OPS)))
+def test_exact_integers_all_ops(handle, mode, opA, opB):
+    m, n, k = 37, 45, 83
+    A = bi.small_int(10, *stored(opA, m, k))
+    B = bi.small_int(11, *stored(opB, k, n))
+    C0 = bi.small_int(12, m, n)
+    want = oracle.bq_gemm(A.numpy(), B.numpy(), opA, opB, alpha=2 - 3j, beta=-1 + 2j, C=C0.numpy())
+    got = run(handle, A, B, opA, opB, alpha=2 - 3j, beta=-1 + 2j, C0=C0, mode=mode)
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("m,n,k", [(1, 1, 1), (7, 129, 257), (130, 33, 1025), (255, 300, 64), (128, 256, 2049)])
+def test_exact_integers_ragged_shapes(handle, mode, m, n, k):
+    A = bi.small_int(20, m, k)
+    B = bi.small_int(21, k, n)
+    want = oracle.bq_gemm(A.numpy(), B.numpy())
+    np.testing.assert_array_equal(run(handle, A, B, mode=mode), want)
+
+
+FLAGS = [bi.REAL, bi.COMPLEX, bi.TRS, bi.TRA, bi.BQ]
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("fa,fb", list(itertools.product(FLAGS, FLAGS)))
+def test_subalgebra_flags_exact(handle, mode, fa, fb):
+    m, n, k = 40, 24, 70
+    A = bi.small_int(30, m, k, flags=fa)
+    B = bi.small_int(31, k, n, flags=fb)
+    want = oracle.bq_gemm(A.numpy(), B.numpy())
+    # absent components hold garbage: the library must not read them
+    Ag, Bg = A.clone(), B.clone()
+    for c in range(8):
+        if not (fa >> c) & 1:
+            Ag[c].fill_(float("nan"))
+        if not (fb >> c) & 1:
+            Bg[c].fill_(float("nan"))
+    np.testing.assert_array_equal(run(handle, Ag, Bg, fa=fa, fb=fb, mode=mode), want)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("opA,opB", [("N", "N"), ("H", "N"), ("T", "QC"), ("C", "H")])
+def test_random_within_tolerance(handle, mode, opA, opB):
+    m, n, k = 200, 150, 700
+    A = bi.uniform(40, *stored(opA, m, k))
+    B = bi.uniform(41, *stored(opB, k, n))
+    C0 = bi.uniform(42, m, n)
+    al, be = bi.complex_scalar(43), bi.complex_scalar(44)
+    want = oracle.bq_gemm(A.numpy(), B.numpy(), opA, opB, alpha=al, beta=be, C=C0.numpy())
+    got = run(handle, A, B, opA, opB, alpha=al, beta=be, C0=C0, mode=mode)
+    err = rel(got, want)
+    assert err <= (1e-14 if mode == "fp64" else TOL), err
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_fock_like_row_scaled(handle, mode):
+    """The precision workload's structure (banded, rows scaled over 6 decades) at a small size."""
+    m = n = k = 384
+    A = bi.fock_like(50, m, k, row_scale=True)
+    B = bi.fock_like(51, k, n, row_scale=True)
+    want = oracle.bq_gemm(A.numpy(), B.numpy())
+    err = rel(run(handle, A, B, mode=mode), want)
+    assert err <= TOL, err
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_beta_zero_ignores_nan_and_k_zero_scales(handle, mode):
+    m, n, k = 33, 17, 5
+    A = bi.uniform(60, m, k)
+    B = bi.uniform(61, k, n)
+    got = run(handle, A, B, mode=mode)      # C pre-filled with NaN, beta = 0
+    assert np.isfinite(got).all()
+    C0 = bi.uniform(62, m, n)
+    Aa = torch.empty((8, m, 0), dtype=torch.float64)
+    Bb = torch.empty((8, 0, n), dtype=torch.float64)
+    got = run(handle, Aa, Bb, beta=0.5 - 0.25j, C0=C0, mode=mode, m=m, n=n)
+    want = oracle.bq_gemm(np.zeros((8, m, 1)), np.zeros((8, 1, n)), beta=0.5 - 0.25j, C=C0.numpy())
+    np.testing.assert_array_equal(got, want)
+
+
+def test_strided_views(handle):
+    """ld > columns and component strides larger than rows * ld."""
+    dev = torch.device("cuda")
+    m, n, k = 50, 40, 60
+    Abig = bi.small_int(70, m + 5, k + 9).to(dev)
+    Bbig = bi.small_int(71, k + 3, n + 11).to(dev)
+    A = Abig[:, :m, :k]
+    B = Bbig[:, :k, :n]
+    Cbig = torch.zeros((8, m + 2, n + 7), dtype=torch.float64, device=dev)
+    C = Cbig[:, :m, :n]
+    for mode in MODES:
+        hm.hmat_bq_gemm(handle, A, B, C, mode=mode)
+        torch.cuda.synchronize()
+        want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy())
+        np.testing.assert_array_equal(C.cpu().numpy(), want)
+        assert torch.all(Cbig[:, m:, :] == 0) and torch.all(Cbig[:, :, n:] == 0)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_grouped_mixed_shapes(handle, mode, use_graph):
+    dev = torch.device("cuda")
+    shapes = [(33, 70, 129), (128, 64, 64), (5, 300, 17), (260, 100, 1100), (64, 64, 1)]
+    flags = [(bi.BQ, bi.BQ), (bi.TRS, bi.TRA), (bi.BQ, bi.COMPLEX), (bi.TRS, bi.BQ), (bi.REAL, bi.BQ)]
+    ops = [("N", "N"), ("H", "N"), ("T", "QC"), ("N", "C"), ("C", "T")]
+    probs, descs = [], []
+    for i, ((m, n, k), (fa, fb), (oa, ob)) in enumerate(zip(shapes, flags, ops)):
+        A = bi.small_int(80 + i, *stored(oa, m, k), flags=fa)
+        B = bi.small_int(90 + i, *stored(ob, k, n), flags=fb)
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        dA, dB = A.to(dev), B.to(dev)
+        probs.append((A, B, C, oa, ob, dA, dB))
+        descs.append(hm.make_desc(dA, dB, C, oa, ob, fa, fb))
+    for _ in range(2):          # the second call replays the graph
+        for p in probs:
+            p[2].fill_(float("nan"))
+        hm.hmat_bq_gemm_grouped(handle, descs, mode=mode, tol=TOL, use_graph=use_graph,
+                                stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for A, B, C, oa, ob, _, _ in probs:
+            np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy(), oa, ob))
+
+
+def test_argument_errors(handle):
+    dev = torch.device("cuda")
+    A = torch.zeros((8, 4, 4), dtype=torch.float64, device=dev)
+    C = torch.zeros((8, 4, 4), dtype=torch.float64, device=dev)
+    L = hm.lib()
+    st = L.hmat_bq_gemm(handle.value, 9, 0, 0xFF, 0xFF, 4, 4, 4, 1.0, 0.0, A.data_ptr(), 4, 16, A.data_ptr(), 4, 16,
+                        0.0, 0.0, C.data_ptr(), 4, 16, 0, 0.0, None, 0, None)
+    assert st == 1                                        # bad op
+    st = L.hmat_bq_gemm(handle.value, 0, 0, 0xFF, 0xFF, 4, 4, 4, 1.0, 0.0, A.data_ptr(), 3, 16, A.data_ptr(), 4, 16,
+                        0.0, 0.0, C.data_ptr(), 4, 16, 0, 0.0, None, 0, None)
+    assert st == 1                                        # lda < k
+    st = L.hmat_bq_gemm(handle.value, 0, 0, 0xFF, 0xFF, 4, 4, 4, 1.0, 0.0, A.data_ptr() + 4, 4, 16, A.data_ptr(),
+                        4, 16, 0.0, 0.0, C.data_ptr(), 4, 16, 0, 0.0, None, 0, None)
+    assert st == 3                                        # misaligned
+    st = L.hmat_bq_gemm(handle.value, 0, 0, 0xFF, 0xFF, 4, 4, 4, 1.0, 0.0, A.data_ptr(), 4, 16, A.data_ptr(), 4, 16,
+                        0.0, 0.0, C.data_ptr(), 4, 16, 1, 0.0, None, 0, None)
+    assert st == 4                                        # split mode without workspace
+    st = L.hmat_bq_gemm(None, 0, 0, 0xFF, 0xFF, 4, 4, 4, 1.0, 0.0, A.data_ptr(), 4, 16, A.data_ptr(), 4, 16,
+                        0.0, 0.0, C.data_ptr(), 4, 16, 0, 0.0, None, 0, None)
+    assert st == 7                                        # no handle
