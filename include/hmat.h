@@ -165,6 +165,42 @@ hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
                                  size_t workspace_bytes, void *stream,
                                  int32_t use_graph);
 
+/* Split-mode product that allocates nothing: C <- alpha op(A) op(B) + beta C
+ * exactly as hmat_bq_gemm with mode HMAT_MODE_SPLIT, but its workspace is a
+ * fixed array compiled into this library instead of caller memory.  The paper
+ * has no counterpart; it is for callers that cannot allocate device memory
+ * (code running under a stream capture or a foreign memory manager, or an
+ * embedding that owns every cudaMalloc) and whose products are small.
+ *   - Capacity: hmat_split_noalloc_capacity() bytes (48 MiB), held on every
+ *     GPU that loads the library until the process exits.  A product whose
+ *     split workspace (hmat_workspace_size) exceeds it is rejected with
+ *     HMAT_STATUS_WORKSPACE_TOO_SMALL before anything is launched (full
+ *     biquaternions fit up to about m = n = 128 with k <= 256).
+ *   - k == 0, or an operand without a present component, returns
+ *     HMAT_STATUS_UNSUPPORTED (use hmat_bq_gemm).
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Nothing in the array needs to start at zero: every byte a call reads was
+ *     written earlier in the same call.  Every call shares the one array (and
+ *     one job-table entry), which keeps the last call's contents: calls whose
+ *     execution overlaps on the GPU (different streams, or different handles)
+ *     race; serialise them on one stream.
+ *   - No cudaMalloc, cudaFree or other allocating routine is called; the
+ *     handle's plan table (allocated by hmat_create) is reused.
+ * Arguments, layout and the remaining errors as hmat_bq_gemm. */
+hmat_status hmat_bq_gemm_split_noalloc(hmat_handle handle, int32_t opA, int32_t opB,
+                                       uint32_t flagsA, uint32_t flagsB,
+                                       int64_t m, int64_t n, int64_t k,
+                                       double alpha_re, double alpha_im,
+                                       const double *A, int64_t lda, int64_t strideA,
+                                       const double *B, int64_t ldb, int64_t strideB,
+                                       double beta_re, double beta_im,
+                                       double *C, int64_t ldc, int64_t strideC,
+                                       double tol, void *stream);
+
+/* Bytes of the fixed scratch array used by hmat_bq_gemm_split_noalloc. */
+size_t hmat_split_noalloc_capacity(void);
+
 /* Index of the descriptor that made the last grouped call fail, or -1. */
 int32_t hmat_last_bad_index(hmat_handle handle);
 

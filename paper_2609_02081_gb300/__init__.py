@@ -63,6 +63,10 @@ SIGNATURES = {
                                     _i32, _dbl, _ptr, _sz, _ptr]),
     "hmat_bq_gemm_grouped": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc), _i32, _dbl, _ptr, _sz,
                                             _ptr, _i32]),
+    "hmat_bq_gemm_split_noalloc": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _dbl, _dbl,
+                                                  _ptr, _i64, _i64, _ptr, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
+                                                  _dbl, _ptr]),
+    "hmat_split_noalloc_capacity": (_sz, []),
     "hmat_last_bad_index": (_i32, [_ptr]),
     "hmat_plan_info": (ctypes.c_int, [_i32, _i32, _u32, _u32, ctypes.POINTER(_i32), ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_i32)]),
@@ -285,6 +289,20 @@ def hmat_bq_gemm_grouped(handle: Handle, descs, mode="fp64", tol=0.0, workspace=
         raise HmatError(st, f"hmat_bq_gemm_grouped (descriptor {bad})")
 
 
+def hmat_bq_gemm_split_noalloc(handle: Handle, A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ,
+                               alpha=1.0, beta=0.0, tol=0.0, stream=None):
+    """Split-mode product whose workspace is the library's fixed scratch array
+    (no allocation by the library or by this binding); returns C.  For callers
+    that cannot allocate device memory; limited to small products."""
+    d = make_desc(A, B, C, opA, opB, flagsA, flagsB, alpha, beta)
+    _check(lib().hmat_bq_gemm_split_noalloc(handle.value, d.opA, d.opB, d.flagsA, d.flagsB, d.m, d.n, d.k,
+                                            d.alpha_re, d.alpha_im, d.A, d.lda, d.strideA, d.B, d.ldb, d.strideB,
+                                            d.beta_re, d.beta_im, d.C, d.ldc, d.strideC, float(tol),
+                                            _stream_ptr(stream)),
+           "hmat_bq_gemm_split_noalloc")
+    return C
+
+
 def bq_gemm_host(handle: Handle, A_host, B_host, C_host, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ,
                  alpha=1.0, beta=0.0, mode="split", tol=0.0, device_buffers=None, workspace=None, stream=None):
     """End-to-end product on HOST tensors: copy A, B (and C if beta != 0) to the
@@ -306,5 +324,6 @@ def bq_gemm_host(handle: Handle, A_host, B_host, C_host, opA="N", opB="N", flags
 
 
 __all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gemm_grouped", "hmat_workspace_size",
+           "hmat_bq_gemm_split_noalloc",
            "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",
            "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]

@@ -21,6 +21,43 @@ __device__ uint32_t g_hmat_device_error = 0;
 static uint32_t* g_err_ptr = nullptr;
 uint32_t* device_error_ptr() { return g_err_ptr; }
 
+// Fixed device scratch for hmat_bq_gemm_split_noalloc: the split-mode
+// workspace (scale exponents, encoded factor tiles, product residues) and the
+// one-entry job table live here instead of in caller-provided memory.  Every
+// GPU that loads the library holds these bytes until the process exits.
+constexpr size_t kNoAllocScratchBytes = (size_t)48 << 20;   // 48 MiB
+constexpr int kNoAllocMaxDevices = 64;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static __device__ __align__(256) SplitJob g_noalloc_job;
+
+// Device addresses of the two arrays, looked up once per device (host code
+// cannot use the symbols themselves as device addresses).
+struct NoAllocAddrs {
+  unsigned char* scratch = nullptr;
+  SplitJob* job = nullptr;
+};
+static NoAllocAddrs g_noalloc_addrs[kNoAllocMaxDevices];
+static std::mutex g_noalloc_mu;
+
+static cudaError_t noalloc_setup(int device, NoAllocAddrs* out) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  NoAllocAddrs& a = g_noalloc_addrs[device];
+  if (!a.scratch) {
+    // called with `device` current (the handle's device)
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    void* q = nullptr;
+    e = cudaGetSymbolAddress(&q, g_noalloc_job);
+    if (e != cudaSuccess) return e;
+    a.scratch = static_cast<unsigned char*>(p);
+    a.job = static_cast<SplitJob*>(q);
+  }
+  *out = a;
+  return cudaSuccess;
+}
+
 size_t fp64_smem_bytes();
 cudaError_t fp64_configure();
 cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* d_plans, int64_t total_tiles,
@@ -480,6 +517,56 @@ hmat_status hmat_bq_gemm_grouped(hmat_handle h, int32_t count, const hmat_gemm_d
   if (!use_graph) return run(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
   return run_graph(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
 }
+
+hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+                                       int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im,
+                                       const double* A, int64_t lda, int64_t strideA, const double* B, int64_t ldb,
+                                       int64_t strideB, double beta_re, double beta_im, double* C, int64_t ldc,
+                                       int64_t strideC, double tol, void* stream_ptr) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (tol < 0 || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
+  std::lock_guard<std::mutex> lock(h->mu);
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) return HMAT_STATUS_INVALID_VALUE;
+  hmat_gemm_desc d;
+  d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB;
+  d.m = m; d.n = n; d.k = k;
+  d.alpha_re = alpha_re; d.alpha_im = alpha_im; d.beta_re = beta_re; d.beta_im = beta_im;
+  d.A = A; d.lda = lda; d.strideA = strideA;
+  d.B = B; d.ldb = ldb; d.strideB = strideB;
+  d.C = C; d.ldc = ldc; d.strideC = strideC;
+  JobDesc j;
+  hmat_status st = validate(d, &j);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  if (j.m == 0 || j.n == 0) return HMAT_STATUS_SUCCESS;
+  int slot = 0;
+  st = plan_slot(h, j.fa, j.fb, stream, &slot);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  j.plan = slot;
+  // the fixed scratch serves the split pipeline only: an empty product (k == 0
+  // or an operand with no present component) is not handled here
+  if (j.k == 0 || h->h_plans[slot].np == 0) return HMAT_STATUS_UNSUPPORTED;
+  SplitJob sj;
+  SplitUnits u;
+  st = split_layout_single(j, h->h_plans[slot], tol, &sj, &u);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  if ((size_t)u.ws_bytes > kNoAllocScratchBytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
+  NoAllocAddrs a;
+  cudaError_t e = noalloc_setup(h->device, &a);
+  if (e != cudaSuccess) return cuda_status(e);
+  // the job table is copied from this stack frame (staged by the runtime before the call returns)
+  e = cudaMemcpyAsync(a.job, &sj, sizeof(SplitJob), cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = launch_split_exponents(a.job, 1, u.exp, 0, stream, a.scratch);
+  if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 0, u.encA, stream, a.scratch);
+  if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 1, u.encB, stream, a.scratch);
+  if (e == cudaSuccess)
+    e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch);
+  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch);
+  return cuda_status(e);
+}
+
+size_t hmat_split_noalloc_capacity(void) { return kNoAllocScratchBytes; }
 
 int32_t hmat_last_bad_index(hmat_handle h) { return h ? h->last_bad : -1; }
 

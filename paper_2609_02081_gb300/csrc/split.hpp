@@ -98,6 +98,12 @@ struct SplitPrep {
 // Lay the jobs out in a workspace of ws_bytes (WORKSPACE_TOO_SMALL if it does not fit).
 hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
                           SplitPrep* out);
+// Layout of one job at workspace offset 0 with its per-stage unit counts;
+// uses no heap memory (for the entry point that allocates nothing).
+struct SplitUnits {
+  int64_t exp = 0, encA = 0, encB = 0, items = 0, crt = 0, ws_bytes = 0;
+};
+hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, SplitJob* out, SplitUnits* units);
 // Launch the four stages reading the device job table d_jobs.
 hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d_jobs, const KPlan* d_plans,
                          unsigned char* ws, cudaStream_t stream);

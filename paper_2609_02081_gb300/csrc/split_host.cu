@@ -192,6 +192,24 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
   return HMAT_STATUS_SUCCESS;
 }
 
+hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, SplitJob* out, SplitUnits* units) {
+  SplitJob sj;
+  std::memset(&sj, 0, sizeof(sj));
+  sj.d = d;
+  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf};
+  int64_t off = 0;
+  hmat_status st = layout_job(sh, &P, tol, &sj, &off);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  units->exp = (d.m + 31) / 32 + (d.n + 31) / 32;
+  units->encA = (int64_t)sj.nmod * sj.tiles_m * kTileM * sj.nkb * (kTileK / 8);
+  units->encB = (int64_t)sj.nmod * sj.tiles_n * sj.bn * sj.nkb * (kTileK / 8);
+  units->items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
+  units->crt = (int64_t)d.m * d.n;
+  units->ws_bytes = off;
+  *out = sj;
+  return HMAT_STATUS_SUCCESS;
+}
+
 hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d_jobs, const KPlan* d_plans,
                          unsigned char* ws, cudaStream_t stream) {
   const int njobs = (int)sp.jobs.size();
