@@ -42,6 +42,10 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=103)
+    ap.add_argument("--workload", choices=["single", "grouped"], default="single",
+                    help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]")
+    ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
+    ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
     return ap.parse_args()
 
 
@@ -322,11 +326,81 @@ def ours(args, rank, world, local):
     h.close()
 
 
+def grouped(args, rank, world, local):
+    """512 independent products of log-uniform shapes in one grouped call per step."""
+    import numpy as np
+    import torch
+    import bq_inputs as bi
+    import oracle
+    import paper_2609_02081_gb300 as hm
+
+    dev = torch.device("cuda", local if torch.cuda.device_count() > local else 0)
+    torch.cuda.set_device(dev)
+    shapes = bi.batch_shapes(104, 512)
+    mats, descs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A = bi.uniform(10_000 + i, m, k, device=dev)
+        B = bi.uniform(20_000 + i, k, n, device=dev)
+        C = torch.empty((8, m, n), dtype=torch.float64, device=dev)
+        mats.append((A, B, C))
+        descs.append(hm.make_desc(A, B, C))
+    h = hm.Handle()
+    if args.tile_table:
+        from paper_2609_02081_gb300 import autotune
+        h.set_tile_table(autotune.load(args.tile_table))
+    ws_bytes = hm.hmat_workspace_size(h, descs, args.mode, args.tol)
+    ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        hm.hmat_bq_gemm_grouped(h, descs, args.mode, args.tol, workspace=ws, stream=stream, use_graph=args.graph)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev.index)
+    barrier(world)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    flops64 = sum(64 * 2.0 * m * n * k for m, n, k in shapes)
+    value = world * flops64 / (ms * 1e-3) / 1e12
+    if rank == 0:
+        # accuracy: 16 sampled problems against the oracle
+        rng = np.random.default_rng(5)
+        errs = []
+        small = [i for i, (m, n, k) in enumerate(shapes) if m * n * k <= (1 << 25)]
+        for i in rng.choice(small, size=16, replace=False):
+            A, B, C = mats[i]
+            want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy())
+            errs.append(float(np.linalg.norm(C.cpu().numpy() - want) / np.linalg.norm(want)))
+        line = {"metric": "grouped biquaternion GEMM TFLOP/s (64-GEMM-equiv.)", "value": value, "unit": "TFLOP/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if args.mode == "split" else "f64", "data": "synthetic",
+                "config": {"workload": "512 products, m,n,k log-uniform in [32,1024] (seed 104), iid U[-1,1], "
+                                       "full biquaternions", "mode": args.mode, "graph": args.graph,
+                           "tol": args.tol, "total_flops_64equiv": flops64,
+                           "tile_table": args.tile_table, "workspace_bytes": ws_bytes},
+                "max_rel_fro_err_16_sampled": max(errs), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    barrier(world)
+    h.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     try:
-        if args.impl == "reference":
+        if args.workload == "grouped" and args.impl == "ours":
+            grouped(args, rank, world, local)
+        elif args.impl == "reference":
             reference_arm(args, rank, world)
         else:
             ours(args, rank, world, local)

@@ -229,6 +229,14 @@ hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
  * which bounded wait gave up).  Synchronises the device. */
 hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
 
+/* Tile-width table for split mode (written by the autotuner,
+ * paper_2609_02081_gb300/autotune.py).  table: 16 x 16 int8 codes indexed
+ * [min(15, ceil(log2 m))][min(15, ceil(log2 n))]: 0 = built-in size rule,
+ * 1/2/3 = output tiles 128 x 64 / 128 x 128 / 128 x 256.  NULL restores the
+ * built-in rule.  Affects later calls and hmat_workspace_size on this handle.
+ * Errors: NOT_INITIALIZED, INVALID_VALUE (a code outside 0..3). */
+hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
+
 /* Kernel profiling: when enabled, every library kernel launch on the handle
  * is bracketed by CUDA events on its launch stream; hmat_get_profile returns,
  * per kernel id, the number of launches and the summed event time (ms) since

@@ -72,6 +72,7 @@ SIGNATURES = {
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
+    "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
     "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
     "hmat_get_profile": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "hmat_reset_profile": (ctypes.c_int, [_ptr]),
@@ -183,6 +184,14 @@ class Handle:
 
     def reset_profile(self):
         _check(lib().hmat_reset_profile(self._h), "hmat_reset_profile")
+
+    def set_tile_table(self, table):
+        """Install a 16 x 16 tile-width code table (None: built-in rule); see autotune.py."""
+        if table is None:
+            _check(lib().hmat_set_tile_table(self._h, None), "hmat_set_tile_table")
+            return
+        t = np.ascontiguousarray(table, dtype=np.int8).reshape(16, 16)
+        _check(lib().hmat_set_tile_table(self._h, t.ctypes.data), "hmat_set_tile_table")
 
     def device_error(self) -> int:
         code = _u32()

@@ -1,0 +1,108 @@
+"""Autotuner for the split-mode output tile width (hmat_set_tile_table).
+
+For every (ceil(log2 m), ceil(log2 n)) bin that a set of problem shapes
+touches, the tuner times one representative product of that bin on the GPU
+with each tile width (128 x 64, 128 x 128, 128 x 256) and keeps the fastest.
+The result is a 16 x 16 table of codes (0 = built-in rule, 1/2/3 = 64/128/256
+columns) that :meth:`Handle.set_tile_table` installs; it is saved as JSON.
+
+    python -m paper_2609_02081_gb300.autotune --out tile_table.json          # the 512-shape batch
+    python -m paper_2609_02081_gb300.autotune --shapes 256x256x256,1024x64x512
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+
+import numpy as np
+
+from . import Handle, hmat_bq_gemm, hmat_workspace_size, make_desc
+
+BINS = 16
+CODES = {1: 64, 2: 128, 3: 256}
+
+
+def _bin(x: int) -> int:
+    return min(BINS - 1, max(0, math.ceil(math.log2(max(x, 1)))))
+
+
+def _time_call(h, A, B, C, ws, tol, reps):
+    import torch
+    stream = torch.cuda.current_stream()
+    hmat_bq_gemm(h, A, B, C, mode="split", tol=tol, workspace=ws, stream=stream)   # warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        hmat_bq_gemm(h, A, B, C, mode="split", tol=tol, workspace=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune(shapes, tol: float = 1e-12, reps: int = 5, seed: int = 0):
+    """Return (table, report) for the given (m, n, k) shapes."""
+    import torch
+    dev = torch.device("cuda")
+    groups = {}
+    for m, n, k in shapes:
+        groups.setdefault((_bin(m), _bin(n)), []).append((m, n, k))
+    table = np.zeros((BINS, BINS), dtype=np.int8)
+    report = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    with Handle() as h:
+        for (bm, bn_), members in sorted(groups.items()):
+            members.sort(key=lambda s: s[0] * s[1] * s[2])
+            m, n, k = members[len(members) // 2]                    # median-work representative
+            A = torch.rand((8, m, k), generator=g, device=dev, dtype=torch.float64) * 2 - 1
+            B = torch.rand((8, k, n), generator=g, device=dev, dtype=torch.float64) * 2 - 1
+            C = torch.empty((8, m, n), dtype=torch.float64, device=dev)
+            times = {}
+            for code, width in CODES.items():
+                t = np.zeros((BINS, BINS), dtype=np.int8)
+                t[bm, bn_] = code
+                h.set_tile_table(t)
+                nbytes = hmat_workspace_size(h, [make_desc(A, B, C)], "split", tol)
+                ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
+                times[width] = _time_call(h, A, B, C, ws, tol, reps)
+                del ws
+            best = min(times, key=times.get)
+            table[bm, bn_] = {64: 1, 128: 2, 256: 3}[best]
+            report[f"{bm},{bn_}"] = {"shape": [m, n, k], "ms": times, "best": best, "members": len(members)}
+    return table, report
+
+
+def save(table, report, path):
+    with open(path, "w") as f:
+        json.dump({"table": np.asarray(table).astype(int).tolist(), "report": report}, f, indent=1)
+
+
+def load(path):
+    with open(path) as f:
+        return np.asarray(json.load(f)["table"], dtype=np.int8)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shapes", default="batch512",
+                    help="'batch512' (512 log-uniform shapes in [32,1024], seed 104) or 'MxNxK,MxNxK,...'")
+    ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--out", default="tile_table.json")
+    args = ap.parse_args()
+    if args.shapes == "batch512":
+        import sys
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        import bq_inputs
+        shapes = bq_inputs.batch_shapes(104, 512)
+    else:
+        shapes = [tuple(int(x) for x in s.split("x")) for s in args.shapes.split(",")]
+    table, report = tune(shapes, args.tol, args.reps)
+    save(table, report, args.out)
+    print(json.dumps({"bins": len(report), "out": args.out}))
+
+
+if __name__ == "__main__":
+    main()

@@ -262,6 +262,8 @@ SplitState& handle_split(hmat_context* h) { return h->split; }
 // ----------------------------------------------------------------- dispatch
 namespace {
 
+const int8_t* split_table(hmat_context* h) { return h->split.has_table ? h->split.tile_table : nullptr; }
+
 // A validated call: FP64 jobs (with tile prefixes) and split jobs (with layouts).
 struct Prepared {
   std::vector<JobDesc> f;
@@ -300,7 +302,7 @@ hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs,
     out->f_tiles += (int64_t)j.tiles_m * j.tiles_n;
   }
   if (!split_jobs.empty()) {
-    hmat_status st = split_prepare(split_jobs, h->h_plans, tol, ws_bytes, &out->sp);
+    hmat_status st = split_prepare(split_jobs, h->h_plans, tol, ws_bytes, split_table(h), &out->sp);
     if (st != HMAT_STATUS_SUCCESS) return st;
     out->has_split = true;
   }
@@ -493,7 +495,7 @@ hmat_status hmat_workspace_size(hmat_handle h, int32_t count, const hmat_gemm_de
     if (p.np == 0) continue;
     shapes.push_back({d.m, d.n, d.k, p.np, p.nlf, p.nrf});
   }
-  return split_workspace_bytes(shapes, tol, bytes);
+  return split_workspace_bytes(shapes, tol, split_table(h), bytes);
 }
 
 hmat_status hmat_bq_gemm(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
@@ -549,7 +551,7 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   if (j.k == 0 || h->h_plans[slot].np == 0) return HMAT_STATUS_UNSUPPORTED;
   SplitJob sj;
   SplitUnits u;
-  st = split_layout_single(j, h->h_plans[slot], tol, &sj, &u);
+  st = split_layout_single(j, h->h_plans[slot], tol, split_table(h), &sj, &u);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if ((size_t)u.ws_bytes > kNoAllocScratchBytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
   NoAllocAddrs a;
@@ -558,11 +560,11 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   // the job table is copied from this stack frame (staged by the runtime before the call returns)
   e = cudaMemcpyAsync(a.job, &sj, sizeof(SplitJob), cudaMemcpyHostToDevice, stream);
   if (e == cudaSuccess) e = launch_split_exponents(a.job, 1, u.exp, 0, stream, a.scratch);
-  if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 0, u.encA, stream, a.scratch);
-  if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 1, u.encB, stream, a.scratch);
+  if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 0, u.encA, stream, a.scratch, u.max_bits);
+  if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 1, u.encB, stream, a.scratch, u.max_bits);
   if (e == cudaSuccess)
     e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch);
-  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch);
+  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod);
   return cuda_status(e);
 }
 
@@ -616,6 +618,21 @@ hmat_status hmat_get_device_error(hmat_handle h, uint32_t* code) {
     e = cudaMemcpyToSymbol(g_hmat_device_error, &zero, sizeof(uint32_t));
   }
   return cuda_status(e);
+}
+
+hmat_status hmat_set_tile_table(hmat_handle h, const int8_t* table) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (!table) {
+    h->split.has_table = false;
+    std::memset(h->split.tile_table, 0, sizeof(h->split.tile_table));
+    return HMAT_STATUS_SUCCESS;
+  }
+  for (int i = 0; i < kTileBins * kTileBins; ++i)
+    if (table[i] < 0 || table[i] > 3) return HMAT_STATUS_INVALID_VALUE;
+  std::memcpy(h->split.tile_table, table, sizeof(h->split.tile_table));
+  h->split.has_table = true;
+  return HMAT_STATUS_SUCCESS;
 }
 
 hmat_status hmat_set_profiling(hmat_handle h, int32_t enable) {

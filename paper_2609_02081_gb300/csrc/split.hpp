@@ -41,6 +41,8 @@ constexpr int kLimbs = 5;          // 160-bit CRT accumulators (32-bit limbs)
 constexpr int kTileM = 128;        // tcgen05 M (one TMEM lane per output row)
 constexpr int kTileK = 64;         // BF16 elements per 128-byte swizzled row
 constexpr int kChunkK = 1024;      // inner steps per exact FP32 accumulation chunk
+constexpr int kTileBins = 16;      // tile-width table: bins of ceil(log2 m) x ceil(log2 n)
+constexpr int kCrtThreads = 128;   // CRT block size (elements per block)
 
 struct SplitParams {
   int nmod = 0;
@@ -67,14 +69,19 @@ struct SplitJob {
   int64_t off_sexp, off_texp;       // int32 exponents (bytes into workspace)
   int64_t off_encA, off_encB;       // BF16 factor tiles
   int64_t off_res;                  // int8 product residues
+  int64_t encA_plane, encB_plane;   // bytes between consecutive (modulus, factor) tile planes
+  int64_t res_plane;                // bytes between consecutive (modulus, product) residue planes
   int64_t item_begin;               // residue-GEMM work items before this job
-  int64_t encA_begin, encB_begin;   // encode work units before this job
-  int64_t crt_begin;                // CRT work units before this job
+  int64_t encA_begin, encB_begin;   // encode blocks before this job
+  int64_t crt_begin;                // CRT blocks before this job
   int64_t exp_begin;                // exponent work units before this job
 };
 
 // Workspace bytes for a set of problems (sum of the per-problem layouts).
-hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, size_t* bytes);
+hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const int8_t* table,
+                                  size_t* bytes);
+// Bin index of a dimension in the tile-width table.
+int tile_bin(int64_t x);
 
 // Handle-owned state of the split path (job-table staging).
 struct SplitState {
@@ -83,6 +90,8 @@ struct SplitState {
   size_t cap = 0;
   cudaEvent_t done = nullptr;
   bool used = false;
+  bool has_table = false;
+  int8_t tile_table[kTileBins * kTileBins] = {};   // tuned tile widths (0: default rule)
 };
 
 cudaError_t split_configure();
@@ -93,17 +102,20 @@ struct SplitPrep {
   std::vector<SplitJob> jobs;
   int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
   int64_t ws_needed = 0;
+  int max_bits = 0, max_nmod = 0;
 };
 
 // Lay the jobs out in a workspace of ws_bytes (WORKSPACE_TOO_SMALL if it does not fit).
 hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
-                          SplitPrep* out);
+                          const int8_t* table, SplitPrep* out);
 // Layout of one job at workspace offset 0 with its per-stage unit counts;
 // uses no heap memory (for the entry point that allocates nothing).
 struct SplitUnits {
   int64_t exp = 0, encA = 0, encB = 0, items = 0, crt = 0, ws_bytes = 0;
+  int max_bits = 0, max_nmod = 0;
 };
-hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, SplitJob* out, SplitUnits* units);
+hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
+                                SplitUnits* units);
 // Launch the four stages reading the device job table d_jobs.
 hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d_jobs, const KPlan* d_plans,
                          unsigned char* ws, cudaStream_t stream);
@@ -132,12 +144,13 @@ SplitState& handle_split(hmat_context* h);
 struct SplitConsts;
 cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int grid, cudaStream_t s,
                                    unsigned char* ws);
+// units are blocks: encode tiles of 32 rows x 32 k, CRT blocks of 256 elements
 cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int side, int64_t units,
-                                cudaStream_t s, unsigned char* ws);
+                                cudaStream_t s, unsigned char* ws, int max_bits);
 cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
                               unsigned char* ws);
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws);
+                             cudaStream_t s, unsigned char* ws, int max_nmod);
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint32_t* crt_c, const uint32_t* crt_P);
 
 }  // namespace hmat

@@ -179,10 +179,10 @@ __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int njobs, int
   it.l = l;
   const int64_t a_tile = (int64_t)kATileBytes;
   const int64_t b_tile = (int64_t)sj.bn * kTileK * 2;
-  it.a = ws + sj.off_encA + ((((int64_t)l * sj.nlf + sj.pl[p]) * sj.tiles_m + tm) * sj.nkb) * a_tile;
-  it.b = ws + sj.off_encB + ((((int64_t)l * sj.nrf + sj.pr[p]) * sj.tiles_n + tn) * sj.nkb) * b_tile;
+  it.a = ws + sj.off_encA + ((int64_t)l * sj.nlf + sj.pl[p]) * sj.encA_plane + ((int64_t)tm * sj.nkb) * a_tile;
+  it.b = ws + sj.off_encB + ((int64_t)l * sj.nrf + sj.pr[p]) * sj.encB_plane + ((int64_t)tn * sj.nkb) * b_tile;
   it.ncols = (int64_t)sj.tiles_n * sj.bn;
-  const int64_t plane = (int64_t)sj.tiles_m * kTileM * it.ncols;
+  const int64_t plane = sj.res_plane;
   it.out = reinterpret_cast<int8_t*>(ws + sj.off_res) + ((int64_t)l * sj.np + p) * plane +
            (int64_t)tm * kTileM * it.ncols + (int64_t)tn * sj.bn;
   return it;

@@ -113,16 +113,44 @@ static int pick_bn(int64_t n) {
   return 64;
 }
 
+static int ceil_log2(int64_t x) {
+  int b = 0;
+  while (((int64_t)1 << b) < x) ++b;
+  return b;
+}
+
+int tile_bin(int64_t x) { return std::min(kTileBins - 1, ceil_log2(std::max<int64_t>(x, 1))); }
+
+// Tile width for an m x n output: the tuned table entry for its (log2 m, log2 n)
+// bin when one is set, else the default size rule.
+static int choose_bn(const int8_t* table, int64_t m, int64_t n) {
+  if (table) {
+    const int v = table[tile_bin(m) * kTileBins + tile_bin(n)];   // 1, 2, 3 -> 64, 128, 256
+    if (v >= 1 && v <= 3) return 32 << v;
+  }
+  return pick_bn(n);
+}
+
 static inline int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 
+// plane skews: an odd multiple of 256 B (bulk copies need 16-byte alignment)
+static constexpr int64_t kPlaneSkewEnc = 3 * 256;
+static constexpr int64_t kPlaneSkewRes = 3 * 256;
+
+// encode blocks: tiles of 16 rows x 32 k over the padded operand
+static inline int64_t enc_blocks(int64_t rows_pad, int64_t nkb) { return (rows_pad / 16) * (nkb * kTileK / 32); }
+// CRT blocks: one per output row and kCrtThreads consecutive columns
+static inline int64_t crt_blocks(int64_t m, int64_t n) { return m * ((n + kCrtThreads - 1) / kCrtThreads); }
+
 // Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
-static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, SplitJob* sj, int64_t* offset) {
+static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const int8_t* table, SplitJob* sj,
+                              int64_t* offset) {
   SplitParams sp;
   hmat_status st = split_params(sh.k, tol, &sp);
   if (st != HMAT_STATUS_SUCCESS) return st;
   sj->nmod = sp.nmod;
   sj->bits = sp.bits;
-  sj->bn = pick_bn(sh.n);
+  sj->bn = choose_bn(table, sh.m, sh.n);
   sj->tiles_m = (int32_t)((sh.m + kTileM - 1) / kTileM);
   sj->tiles_n = (int32_t)((sh.n + sj->bn - 1) / sj->bn);
   sj->nkb = (int32_t)((sh.k + kTileK - 1) / kTileK);
@@ -135,27 +163,34 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
       sj->pr[p] = plan->pr[p];
     }
   }
+  // Plane strides get a skew so that the many planes a single encode / CRT
+  // thread touches do not sit at power-of-two distances (which maps them onto
+  // the same memory channels and cache sets).
+  sj->encA_plane = (int64_t)sj->tiles_m * sj->nkb * kTileM * kTileK * 2 + kPlaneSkewEnc;
+  sj->encB_plane = (int64_t)sj->tiles_n * sj->nkb * sj->bn * kTileK * 2 + kPlaneSkewEnc;
+  sj->res_plane = ((int64_t)sj->tiles_m * kTileM) * ((int64_t)sj->tiles_n * sj->bn) + kPlaneSkewRes;
   int64_t off = *offset;
   sj->off_sexp = off;
   off = align256(off + 4 * sh.m);
   sj->off_texp = off;
   off = align256(off + 4 * sh.n);
   sj->off_encA = off;
-  off = align256(off + (int64_t)sj->nmod * sj->nlf * sj->tiles_m * sj->nkb * kTileM * kTileK * 2);
+  off = align256(off + (int64_t)sj->nmod * sj->nlf * sj->encA_plane);
   sj->off_encB = off;
-  off = align256(off + (int64_t)sj->nmod * sj->nrf * sj->tiles_n * sj->nkb * sj->bn * kTileK * 2);
+  off = align256(off + (int64_t)sj->nmod * sj->nrf * sj->encB_plane);
   sj->off_res = off;
-  off = align256(off + (int64_t)sj->nmod * sj->np * ((int64_t)sj->tiles_m * kTileM) * ((int64_t)sj->tiles_n * sj->bn));
+  off = align256(off + (int64_t)sj->nmod * sj->np * sj->res_plane);
   *offset = off;
   return HMAT_STATUS_SUCCESS;
 }
 
-hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, size_t* bytes) {
+hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const int8_t* table,
+                                  size_t* bytes) {
   int64_t off = 0;
   for (const SplitShape& sh : shapes) {
     SplitJob sj;
     std::memset(&sj, 0, sizeof(sj));
-    hmat_status st = layout_job(sh, nullptr, tol, &sj, &off);
+    hmat_status st = layout_job(sh, nullptr, tol, table, &sj, &off);
     if (st != HMAT_STATUS_SUCCESS) return st;
   }
   *bytes = (size_t)off;
@@ -163,7 +198,7 @@ hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double 
 }
 
 hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
-                          SplitPrep* out) {
+                          const int8_t* table, SplitPrep* out) {
   SplitPrep sp;
   int64_t off = 0;
   for (const JobDesc& d : jobs) {
@@ -172,18 +207,20 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     std::memset(&sj, 0, sizeof(sj));
     sj.d = d;
     SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf};
-    hmat_status st = layout_job(sh, &P, tol, &sj, &off);
+    hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
     if (st != HMAT_STATUS_SUCCESS) return st;
     sj.exp_begin = sp.exp_units;
     sp.exp_units += (d.m + 31) / 32 + (d.n + 31) / 32;
     sj.encA_begin = sp.encA_units;
-    sp.encA_units += (int64_t)sj.nmod * sj.tiles_m * kTileM * sj.nkb * (kTileK / 8);
+    sp.encA_units += enc_blocks(sj.tiles_m * kTileM, sj.nkb);
     sj.encB_begin = sp.encB_units;
-    sp.encB_units += (int64_t)sj.nmod * sj.tiles_n * sj.bn * sj.nkb * (kTileK / 8);
+    sp.encB_units += enc_blocks(sj.tiles_n * sj.bn, sj.nkb);
     sj.item_begin = sp.items;
     sp.items += (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
     sj.crt_begin = sp.crt_units;
-    sp.crt_units += (int64_t)d.m * d.n;
+    sp.crt_units += crt_blocks(d.m, d.n);
+    sp.max_bits = std::max(sp.max_bits, sj.bits);
+    sp.max_nmod = std::max(sp.max_nmod, sj.nmod);
     sp.jobs.push_back(sj);
   }
   if ((size_t)off > ws_bytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
@@ -192,19 +229,22 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
   return HMAT_STATUS_SUCCESS;
 }
 
-hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, SplitJob* out, SplitUnits* units) {
+hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
+                                SplitUnits* units) {
   SplitJob sj;
   std::memset(&sj, 0, sizeof(sj));
   sj.d = d;
   SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf};
   int64_t off = 0;
-  hmat_status st = layout_job(sh, &P, tol, &sj, &off);
+  hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
   if (st != HMAT_STATUS_SUCCESS) return st;
   units->exp = (d.m + 31) / 32 + (d.n + 31) / 32;
-  units->encA = (int64_t)sj.nmod * sj.tiles_m * kTileM * sj.nkb * (kTileK / 8);
-  units->encB = (int64_t)sj.nmod * sj.tiles_n * sj.bn * sj.nkb * (kTileK / 8);
+  units->encA = enc_blocks(sj.tiles_m * kTileM, sj.nkb);
+  units->encB = enc_blocks(sj.tiles_n * sj.bn, sj.nkb);
   units->items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
-  units->crt = (int64_t)d.m * d.n;
+  units->crt = crt_blocks(d.m, d.n);
+  units->max_bits = sj.bits;
+  units->max_nmod = sj.nmod;
   units->ws_bytes = off;
   *out = sj;
   return HMAT_STATUS_SUCCESS;
@@ -221,8 +261,8 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
   if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
   {
     ProfScope ps(h, 2, stream);
-    e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws);
-    if (e == cudaSuccess) e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws);
+    e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws, sp.max_bits);
+    if (e == cudaSuccess) e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws, sp.max_bits);
   }
   if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
   {
@@ -233,7 +273,7 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
   if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
   {
     ProfScope ps(h, 4, stream);
-    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws);
+    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod);
   }
   return e == cudaSuccess ? HMAT_STATUS_SUCCESS : HMAT_STATUS_CUDA_ERROR;
 }

@@ -20,6 +20,7 @@ struct ModConst {
   float inv;    // 1/p (float)
   float c18;    // 2^18 mod p, centred
   float c36;    // 2^36 mod p, centred
+  float c23;    // 2^23 mod p, in [0, p)
   int inv4;     // 4^-1 mod p
   unsigned long long fm;  // floor(2^64 / p) + 1 (fast exact 32-bit mod)
 };
@@ -179,124 +180,163 @@ __global__ void __launch_bounds__(256) split_exponents_kernel(const SplitJob* __
 }
 
 // ------------------------------------------------------------------ 2. encode
-// One thread per (modulus, row, 8-wide k chunk) of one side: reads the eight
-// present components, scales to integers, forms every factor of the plan
-// modulo p and writes 16 bytes (8 BF16) per factor into the swizzled tile.
+// One block per tile of 32 rows x 32 k of one side (op(A) rows, or op(B)
+// columns); every modulus is handled by the same block.
+//   phase 1: the eight present components of the tile are read (coalesced
+//            along whichever index is contiguous in memory), scaled to
+//            integers round(x 2^s_r) and staged in shared memory;
+//   phase 2: thread (row, 4-wide k chunk) splits its 32 integers into exact
+//            float limbs once, then per modulus forms the component residues,
+//            the plan's factors (+-1 sums, Re+Im) mod p, and writes 4 BF16
+//            (8 bytes) per factor into the swizzled tile.  A warp covers 4
+//            rows x 32 k: each row's 64 bytes land in one aligned half of a
+//            128-byte swizzled row, so the stores fill whole sectors.
+constexpr int kEncRows = 16, kEncK = 32, kEncThreads = 128;
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   uint32_t r;
   asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
   return r;
 }
 
-__global__ void __launch_bounds__(256) split_encode_kernel(const SplitJob* __restrict__ jobs, int njobs,
-                                                           const KPlan* __restrict__ plans, int side,
-                                                           int64_t units, unsigned char* __restrict__ ws) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units) return;
-  const int g = find_split_job(jobs, njobs, u, side ? 2 : 1);
+// Centred residue (as float) of a scaled integer: X = hi 2^23 + lo for
+// |X| <= 2^47 (LIMBS == 2), else X = x2 2^36 + x1 2^18 + x0 (|X| <= 2^52);
+// every limb and partial sum stays below 2^24, so float arithmetic is exact.
+template <int LIMBS>
+__device__ __forceinline__ float residue_of(long long X, const ModConst& mc, float c23) {
+  if (LIMBS == 2) {
+    const float lo = (float)(int)(X & 0x7FFFFF);
+    const float hi = (float)(long long)(X >> 23);
+    return fmod_c(fmaf(fmod_c(hi, mc), c23, lo), mc);
+  } else {
+    return residue_i64(X, mc);
+  }
+}
+
+template <int LIMBS>
+__global__ void __launch_bounds__(kEncThreads) split_encode_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                                   const KPlan* __restrict__ plans, int side,
+                                                                   unsigned char* __restrict__ ws) {
+  __shared__ long long xs[8][kEncK][kEncRows + 1];
+  __shared__ int s_row[kEncRows];
+  const int64_t blk = blockIdx.x;
+  const int g = find_split_job(jobs, njobs, blk, side ? 2 : 1);
   const SplitJob& sj = jobs[g];
   const JobDesc& d = sj.d;
   const KPlan& P = plans[d.plan];
-  const int64_t local = u - (side ? sj.encB_begin : sj.encA_begin);
+  const int64_t local = blk - (side ? sj.encB_begin : sj.encA_begin);
   const int tile_rows = side ? sj.bn : kTileM;
   const int rows_pad = (side ? sj.tiles_n : sj.tiles_m) * tile_rows;
-  const int kch = sj.nkb * (kTileK / 8);
-  const bool contiguous = side ? (d.transB != 0) : (d.transA == 0);
-  int r, kc, l;
-  if (contiguous) {
-    kc = (int)(local % kch);
-    r = (int)((local / kch) % rows_pad);
-    l = (int)(local / ((int64_t)kch * rows_pad));
-  } else {
-    r = (int)(local % rows_pad);
-    kc = (int)((local / rows_pad) % kch);
-    l = (int)(local / ((int64_t)kch * rows_pad));
-  }
-  const ModConst& mc = c_mod[l];
+  const int ktiles = sj.nkb * (kTileK / kEncK);
+  const int r0 = (int)(local / ktiles) * kEncRows;
+  const int k0 = (int)(local % ktiles) * kEncK;
   const int nout = side ? d.n : d.m;
   const uint32_t flags = side ? d.fb : d.fa;
   const double* base = side ? d.B : d.A;
   const int64_t ld = side ? d.ldb : d.lda, cs = side ? d.sB : d.sA;
   const int8_t* sign = side ? d.signB : d.signA;
-  const int s = (r < nout) ? reinterpret_cast<const int32_t*>(ws + (side ? sj.off_texp : sj.off_sexp))[r] : 0;
-
-  // component residues for the 8 k values of this chunk
-  float rc[8][8];
-#pragma unroll
-  for (int c = 0; c < 8; ++c) {
-#pragma unroll
-    for (int q = 0; q < 8; ++q) rc[c][q] = 0.f;
-    if (!((flags >> c) & 1u) || r >= nout) continue;
-    const double* cb = base + (int64_t)c * cs;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int kk = kc * 8 + q;
-      if (kk < d.k) {
-        const int64_t off = contiguous ? (int64_t)r * ld + kk : (int64_t)kk * ld + r;
-        const unsigned long long bits = (unsigned long long)__double_as_longlong(__ldg(cb + off));
-        rc[c][q] = residue_i64(scaled_int(bits, s), mc);
-      }
-    }
+  const bool contiguous = side ? (d.transB != 0) : (d.transA == 0);
+  const int t = threadIdx.x;
+  if (t < kEncRows) {
+    const int r = r0 + t;
+    s_row[t] = (r < nout) ? reinterpret_cast<const int32_t*>(ws + (side ? sj.off_texp : sj.off_sexp))[r] : 0;
   }
+  __syncthreads();
+  // phase 1: stage scaled integers (reads coalesced along the contiguous index)
+  for (int idx = t; idx < 8 * kEncK * kEncRows; idx += kEncThreads) {
+    const int c = idx / (kEncK * kEncRows);
+    const int rem = idx % (kEncK * kEncRows);
+    int rr, kk;
+    if (contiguous) { rr = rem / kEncK; kk = rem % kEncK; }
+    else { kk = rem / kEncRows; rr = rem % kEncRows; }
+    long long X = 0;
+    const int r = r0 + rr, kg = k0 + kk;
+    if (((flags >> c) & 1u) && r < nout && kg < d.k) {
+      const int64_t off = contiguous ? (int64_t)r * ld + kg : (int64_t)kg * ld + r;
+      const unsigned long long bits = (unsigned long long)__double_as_longlong(__ldg(base + (int64_t)c * cs + off));
+      X = scaled_int(bits, s_row[rr]);
+    }
+    xs[c][kk][rr] = X;
+  }
+  __syncthreads();
 
-  // destination: tile (l, f, row tile, kb), row rr, 16-byte chunk kc % 8 (128B swizzle)
-  const int kb = kc / (kTileK / 8), c16 = kc % (kTileK / 8);
-  const int rt = r / tile_rows, rr = r % tile_rows;
-  const int ntile = side ? sj.tiles_n : sj.tiles_m;
+  // phase 2: thread (row, 4-wide k chunk); a warp covers 4 rows x 32 k
+  const int rr = t / (kEncK / 4), k4 = t % (kEncK / 4);
+  const int r = r0 + rr;
+  if (r >= rows_pad) return;
+  const int kg = k0 + k4 * 4;
+  const int kb = kg / kTileK, c16 = (kg % kTileK) / 8, half8 = (kg % 8) * 2;
+  const int rt = r / tile_rows, rin = r % tile_rows;
   const int nf = side ? sj.nrf : sj.nlf;
   const int64_t tile_bytes = (int64_t)tile_rows * kTileK * 2;
-  unsigned char* enc = ws + (side ? sj.off_encB : sj.off_encA);
-  const int64_t within = (int64_t)(rr >> 3) * 1024 + (rr & 7) * 128 + ((c16 ^ (rr & 7)) << 4);
-
+  const int64_t plane_bytes = side ? sj.encB_plane : sj.encA_plane;
+  unsigned char* enc = ws + (side ? sj.off_encB : sj.off_encA) + ((int64_t)rt * sj.nkb + kb) * tile_bytes +
+                       (int64_t)(rin >> 3) * 1024 + (rin & 7) * 128 + ((c16 ^ (rin & 7)) << 4) + half8;
   const int ng = side ? P.nrg : P.nlg;
-  for (int gi = 0; gi < ng; ++gi) {
-    const int8_t* cre = side ? P.rre[gi] : P.lre[gi];
-    const int8_t* cim = side ? P.rim[gi] : P.lim[gi];
-    const int8_t* slot = side ? P.rslot[gi] : P.lslot[gi];
-    float re[8], im[8];
+
+  for (int l = 0; l < sj.nmod; ++l) {
+    const ModConst& mc = c_mod[l];
+    const float c23 = mc.c23;
+    float rc[8][4];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) { re[q] = 0.f; im[q] = 0.f; }
+    for (int c = 0; c < 8; ++c) {
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int a = cre[e] * sign[e], b = cim[e] * sign[e + 4];
-#pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        if (a) re[q] += a > 0 ? rc[e][q] : -rc[e][q];
-        if (b) im[q] += b > 0 ? rc[e + 4][q] : -rc[e + 4][q];
-      }
+      for (int q = 0; q < 4; ++q)
+        rc[c][q] = ((flags >> c) & 1u) ? residue_of<LIMBS>(xs[c][k4 * 4 + q][rr], mc, c23) : 0.f;
     }
+    for (int gi = 0; gi < ng; ++gi) {
+      const int8_t* cre = side ? P.rre[gi] : P.lre[gi];
+      const int8_t* cim = side ? P.rim[gi] : P.lim[gi];
+      const int8_t* slot = side ? P.rslot[gi] : P.lslot[gi];
+      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int part = 0; part < 3; ++part) {
-      const int f = slot[part];
-      if (f < 0) continue;
-      float v[8];
+      for (int e = 0; e < 4; ++e) {
+        const int a = cre[e] * sign[e], b = cim[e] * sign[e + 4];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float x = part == 0 ? re[q] : (part == 1 ? im[q] : re[q] + im[q]);
-        v[q] = fmod_c(x, mc);
+        for (int q = 0; q < 4; ++q) {
+          if (a) re[q] += a > 0 ? rc[e][q] : -rc[e][q];
+          if (b) im[q] += b > 0 ? rc[e + 4][q] : -rc[e + 4][q];
+        }
       }
-      uint4 pk;
-      pk.x = pack_bf16x2(v[0], v[1]);
-      pk.y = pack_bf16x2(v[2], v[3]);
-      pk.z = pack_bf16x2(v[4], v[5]);
-      pk.w = pack_bf16x2(v[6], v[7]);
-      const int64_t tile = (((int64_t)l * nf + f) * ntile + rt) * sj.nkb + kb;
-      *reinterpret_cast<uint4*>(enc + tile * tile_bytes + within) = pk;
+#pragma unroll
+      for (int part = 0; part < 3; ++part) {
+        const int f = slot[part];
+        if (f < 0) continue;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = fmod_c(part == 0 ? re[q] : (part == 1 ? im[q] : re[q] + im[q]), mc);
+        const uint2 pk = make_uint2(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]));
+        *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pk;
+      }
     }
   }
 }
 
 // ------------------------------------------------------------------ 4. CRT + recombination + alpha/beta
-// One thread per output element.  Per modulus: the eight output residues
-// sum_p w4[e][p] T_p * 4^-1 (mod p); then S_e = sum_l r_{l,e} c_l (mod P) with
-// the CRT basis c_l, centred, converted to FP64 and scaled by 2^-(s_i + t_j).
+// One block per output row segment of kCrtThreads columns; one thread per
+// element.  The np residue rows of each modulus are prefetched into a
+// three-slot shared-memory ring with cp.async two moduli ahead.  Per modulus the np product residues are packed four to a word
+// and the eight output residues sum_p w4[e][p] T_p come from __dp4a against
+// the plan's weights (packed the same way, in shared memory); times 4^-1 mod p
+// gives the residue of the output.  S_e = sum_l r_{l,e} c_l accumulates in
+// 64-bit limbs (c_l the CRT basis), is reduced mod P, centred, converted to
+// FP64 with one rounding and scaled by 2^-(s_i + t_j); then the complex
+// alpha / beta update (Sec. III scaling and addition).
+template <int L>
 __device__ __forceinline__ double limbs_to_double(const uint32_t* x, int neg, int scale_exp) {
-  int h = kLimbs - 1;
-  while (h > 0 && x[h] == 0) --h;
-  if (h == 0 && x[0] == 0) return neg ? -0.0 : 0.0;
-  const uint32_t l2 = x[h], l1 = h >= 1 ? x[h - 1] : 0u, l0 = h >= 2 ? x[h - 2] : 0u;
-  uint32_t sticky = 0;
-  for (int i = 0; i < h - 2; ++i) sticky |= x[i];
+  int h = 0;
+#pragma unroll
+  for (int q = 0; q < L; ++q)
+    if (x[q]) h = q;
+  if (x[h] == 0) return neg ? -0.0 : 0.0;
+  uint32_t l2 = 0, l1 = 0, l0 = 0, sticky = 0;
+#pragma unroll
+  for (int q = 0; q < L; ++q) {
+    if (q == h) l2 = x[q];
+    else if (q == h - 1) l1 = x[q];
+    else if (q == h - 2) l0 = x[q];
+    else if (q < h - 2) sticky |= x[q];
+  }
   const int lz = __clz(l2);                       // normalise the 96-bit window [l2 l1 l0]
   unsigned long long hi = ((unsigned long long)l2 << 32) | l1;
   unsigned long long lo = (unsigned long long)l0 << 32;
@@ -304,135 +344,186 @@ __device__ __forceinline__ double limbs_to_double(const uint32_t* x, int neg, in
     hi = (hi << lz) | (lo >> (64 - lz));
     lo <<= lz;
   }
-  if (lo != 0 || sticky != 0) hi |= 1ull;         // sticky bit for correct rounding
-  double v = __ull2double_rn(hi);                  // value = hi * 2^(32*(h-2) + ... )
-  // window bottom bit weight: 2^(32*(h-2) - lz) relative to limb 0 (exact power-of-two scaling)
-  const int e2 = 32 * (h - 1) - lz + scale_exp;   // value = W 2^(32(h-2)), W ~ hi 2^(32-lz)
-  v = scalbn(v, e2);
-  return neg ? -v : v;
+  if (lo != 0 || sticky != 0) hi |= 1ull;         // sticky bit: one correct rounding below
+  const double v = __ull2double_rn(hi);
+  // value = W 2^(32(h-2)) with W ~ hi 2^(32 - lz)
+  const double r = scalbn(v, 32 * (h - 1) - lz + scale_exp);
+  return neg ? -r : r;
 }
 
-__global__ void __launch_bounds__(256) split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs,
-                                                        const KPlan* __restrict__ plans, int64_t units,
-                                                        unsigned char* __restrict__ ws) {
-  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (u >= units) return;
-  const int g = find_split_job(jobs, njobs, u, 4);
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
+
+template <int L>
+__global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                                const KPlan* __restrict__ plans,
+                                                                unsigned char* __restrict__ ws) {
+  constexpr int kStages = 3;
+  __shared__ uint32_t wpk[8][kMaxProducts / 4];
+  __shared__ __align__(16) uint8_t ring[kStages][kMaxProducts][kCrtThreads];
+  const int64_t blk = blockIdx.x;
+  const int g = find_split_job(jobs, njobs, blk, 4);
   const SplitJob& sj = jobs[g];
   const JobDesc& d = sj.d;
   const KPlan& P = plans[d.plan];
-  const int64_t local = u - sj.crt_begin;
-  const int i = (int)(local / d.n), j = (int)(local % d.n);
-  const int nm = sj.nmod, np = sj.np;
+  const int np = sj.np, nw = (np + 3) / 4, nm = sj.nmod;
+  const int tid = threadIdx.x;
+  if (tid < 8 * (kMaxProducts / 4)) {
+    const int e = tid / (kMaxProducts / 4), w = tid % (kMaxProducts / 4);
+    uint32_t word = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int p = 4 * w + b;
+      const int v = p < np ? (int)P.w4[e][p] : 0;
+      word |= ((uint32_t)(v & 0xFF)) << (8 * b);
+    }
+    wpk[e][w] = word;
+  }
+  // this block: row i, columns jb*128 .. jb*128+127 of the output
+  const int64_t local = blk - sj.crt_begin;
+  const int colblocks = (d.n + kCrtThreads - 1) / kCrtThreads;
+  const int i = (int)(local / colblocks);
+  const int jb = (int)(local % colblocks);
+  const int j = jb * kCrtThreads + tid;
   const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
-  const int64_t plane = (int64_t)sj.tiles_m * kTileM * ncols;
-  const int8_t* res = reinterpret_cast<const int8_t*>(ws + sj.off_res) + (int64_t)i * ncols + j;
+  const int64_t plane = sj.res_plane;
+  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtThreads;
+  const int64_t cavail = (ncols - (int64_t)jb * kCrtThreads) / 16;
+  const int cmax = cavail < kCrtThreads / 16 ? (int)cavail : kCrtThreads / 16;
 
-  unsigned long long acc[8][kLimbs];
+  // prefetch modulus l's np residue rows (128 bytes each) into ring slot l % 3
+  auto issue = [&](int l) {
+    if (l < nm) {
+      uint8_t(*slot)[kCrtThreads] = ring[l % kStages];
+      for (int idx = tid; idx < np * (kCrtThreads / 16); idx += kCrtThreads) {
+        const int p = idx / (kCrtThreads / 16), c = idx % (kCrtThreads / 16);
+        if (c < cmax) cp_async16(&slot[p][c * 16], rowbase + ((int64_t)l * np + p) * plane + c * 16);
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+
+  unsigned long long acc[8][L];
 #pragma unroll
   for (int e = 0; e < 8; ++e)
 #pragma unroll
-    for (int q = 0; q < kLimbs; ++q) acc[e][q] = 0ull;
+    for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
 
   for (int l = 0; l < nm; ++l) {
+    issue(l + 2);
+    cp_async_wait2();            // modulus l has landed
+    __syncthreads();
     const ModConst& mc = c_mod[l];
-    int o[8];
+    const uint8_t(*slot)[kCrtThreads] = ring[l % kStages];
+    uint32_t tw[kMaxProducts / 4];
 #pragma unroll
-    for (int e = 0; e < 8; ++e) o[e] = 0;
-    for (int p = 0; p < np; ++p) {
-      const int t = res[((int64_t)l * np + p) * plane];
+    for (int w = 0; w < kMaxProducts / 4; ++w) {
+      uint32_t word = 0;
+      if (w < nw) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) o[e] += (int)P.w4[e][p] * t;
+        for (int b = 0; b < 4; ++b) {
+          const int p = 4 * w + b;
+          const uint32_t v = p < np ? (uint32_t)slot[p][tid] : 0u;
+          word |= v << (8 * b);
+        }
+      }
+      tw[w] = word;
     }
+    const float inv4 = (float)mc.inv4;
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
-      // |o| <= 24 * 8 * 127; times 4^-1 mod p stays below 2^24 (exact in float)
-      int r = (int)fmod_c((float)(cmod_i32(o[e], mc) * mc.inv4), mc);
-      if (r < 0) r += mc.p;
+      int o = 0;
 #pragma unroll
-      for (int q = 0; q < kLimbs; ++q) acc[e][q] += (unsigned long long)(uint32_t)r * c_crt[nm][l][q];
+      for (int w = 0; w < kMaxProducts / 4; ++w)
+        if (w < nw) o = __dp4a((int)wpk[e][w], (int)tw[w], o);
+      // |o| <= 24 * 8 * 127 < 2^15: exact in float; r = o * 4^-1 mod p
+      float r = fmod_c(fmod_c((float)o, mc) * inv4, mc);
+      if (r < 0.f) r += mc.pf;
+      const uint32_t ru = (uint32_t)r;
+#pragma unroll
+      for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru * c_crt[nm][l][q];
     }
+    __syncthreads();             // slot l % 3 is refilled by issue(l + 3)
   }
+  if (j >= d.n) return;
 
   const int s_i = reinterpret_cast<const int32_t*>(ws + sj.off_sexp)[i];
   const int t_j = reinterpret_cast<const int32_t*>(ws + sj.off_texp)[j];
   double q8[8];
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
-    // carry-normalise to 32-bit limbs
-    uint32_t x[kLimbs];
+    uint32_t x[L];
     unsigned long long carry = 0;
 #pragma unroll
-    for (int q = 0; q < kLimbs; ++q) {
-      const unsigned long long t = acc[e][q] + carry;
-      x[q] = (uint32_t)t;
-      carry = t >> 32;
+    for (int q = 0; q < L; ++q) {
+      const unsigned long long tq = acc[e][q] + carry;
+      x[q] = (uint32_t)tq;
+      carry = tq >> 32;
     }
-    // quotient estimate q = floor(S / P) from the top three limbs (S < nmod * 255 * P)
+    // quotient estimate q = floor(S / P) from the leading limbs (S < nmod * 255 * P)
     const int pb = c_Pbase[nm];
     float sf = 0.f;
 #pragma unroll
-    for (int q = kLimbs - 1; q >= 0; --q)
+    for (int q = L - 1; q >= 0; --q)
       if (q >= pb) sf = sf * 4294967296.f + (float)x[q];
     int qq = (int)floorf(sf / c_Pf[nm]);
     if (qq < 0) qq = 0;
-    // x -= qq * P
     long long borrow = 0;
-    {
-      unsigned long long mulc = 0;
+    unsigned long long mulc = 0;
 #pragma unroll
-      for (int q = 0; q < kLimbs; ++q) {
-        const unsigned long long prod = (unsigned long long)c_P[nm][q] * (uint32_t)qq + mulc;
-        mulc = prod >> 32;
-        const long long diff = (long long)x[q] - (long long)(uint32_t)prod + borrow;
-        x[q] = (uint32_t)diff;
-        borrow = diff >> 32;     // 0 or -1
-      }
-      borrow += 0;   // (mulc is 0 when qq*P fits, as it does for qq <= floor(S/P)+1)
+    for (int q = 0; q < L; ++q) {            // x -= qq * P
+      const unsigned long long prod = (unsigned long long)c_P[nm][q] * (uint32_t)qq + mulc;
+      mulc = prod >> 32;
+      const long long diff = (long long)x[q] - (long long)(uint32_t)prod + borrow;
+      x[q] = (uint32_t)diff;
+      borrow = diff >> 32;
     }
-    // fix an over-estimate (x went negative) or an under-estimate (x >= P)
-    if (borrow < 0) {
+    if (borrow < 0) {                        // over-estimate by one: add P back
       unsigned long long c = 0;
 #pragma unroll
-      for (int q = 0; q < kLimbs; ++q) {
-        const unsigned long long t = (unsigned long long)x[q] + c_P[nm][q] + c;
-        x[q] = (uint32_t)t;
-        c = t >> 32;
+      for (int q = 0; q < L; ++q) {
+        const unsigned long long tq = (unsigned long long)x[q] + c_P[nm][q] + c;
+        x[q] = (uint32_t)tq;
+        c = tq >> 32;
       }
-    } else {
+    } else {                                 // under-estimate by one: subtract P
       bool ge = true;
 #pragma unroll
-      for (int q = kLimbs - 1; q >= 0; --q) {
+      for (int q = L - 1; q >= 0; --q) {
         if (x[q] != c_P[nm][q]) { ge = x[q] > c_P[nm][q]; break; }
       }
       if (ge) {
         long long b = 0;
 #pragma unroll
-        for (int q = 0; q < kLimbs; ++q) {
+        for (int q = 0; q < L; ++q) {
           const long long diff = (long long)x[q] - (long long)c_P[nm][q] + b;
           x[q] = (uint32_t)diff;
           b = diff >> 32;
         }
       }
     }
-    // centre: x > P/2 means the negative value x - P
-    bool gt = false;
+    bool gt = false;                         // centre: x > P/2 means x - P
 #pragma unroll
-    for (int q = kLimbs - 1; q >= 0; --q) {
+    for (int q = L - 1; q >= 0; --q) {
       if (x[q] != c_Ph[nm][q]) { gt = x[q] > c_Ph[nm][q]; break; }
     }
     int neg = 0;
     if (gt) {
       long long b = 0;
 #pragma unroll
-      for (int q = 0; q < kLimbs; ++q) {   // x = P - x
+      for (int q = 0; q < L; ++q) {
         const long long diff = (long long)c_P[nm][q] - (long long)x[q] + b;
         x[q] = (uint32_t)diff;
         b = diff >> 32;
       }
       neg = 1;
     }
-    q8[e] = limbs_to_double(x, neg, -(s_i + t_j));
+    q8[e] = limbs_to_double<L>(x, neg, -(s_i + t_j));
   }
 
   double* cbase = d.C + (int64_t)i * d.ldc + j;
@@ -473,6 +564,7 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
     };
     m.c18 = centred(1ll << 18);
     m.c36 = centred(1ll << 36);
+    m.c23 = (float)((1ll << 23) % p);
     int inv4 = 0;
     for (int x = 1; x < p; ++x)
       if ((4 * x) % p == 1) { inv4 = x; break; }
@@ -518,18 +610,19 @@ cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t un
 }
 
 cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int side, int64_t units,
-                                cudaStream_t s, unsigned char* ws) {
+                                cudaStream_t s, unsigned char* ws, int max_bits) {
   if (units <= 0) return cudaSuccess;
-  const int64_t blocks = (units + 255) / 256;
-  split_encode_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, d_plans, side, units, ws);
+  if (max_bits <= 47) split_encode_kernel<2><<<(unsigned)units, kEncThreads, 0, s>>>(d_jobs, njobs, d_plans, side, ws);
+  else split_encode_kernel<3><<<(unsigned)units, kEncThreads, 0, s>>>(d_jobs, njobs, d_plans, side, ws);
   return cudaGetLastError();
 }
 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws) {
+                             cudaStream_t s, unsigned char* ws, int max_nmod) {
   if (units <= 0) return cudaSuccess;
-  const int64_t blocks = (units + 255) / 256;
-  split_crt_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs, d_plans, units, ws);
+  // 4 limbs hold sum_l r_l c_l while nmod * 255 * P < 2^128 (nmod <= 14)
+  if (max_nmod <= 14) split_crt_kernel<4><<<(unsigned)units, kCrtThreads, 0, s>>>(d_jobs, njobs, d_plans, ws);
+  else split_crt_kernel<kLimbs><<<(unsigned)units, kCrtThreads, 0, s>>>(d_jobs, njobs, d_plans, ws);
   return cudaGetLastError();
 }
 

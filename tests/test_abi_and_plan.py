@@ -130,3 +130,12 @@ def test_split_limits():
         hm.split_info(200000, 1e-12)           # beyond the int32 drained accumulators
     with pytest.raises(hm.HmatError):
         hm.split_info(8192, 1e-30)             # beyond the modulus table
+
+
+def test_tile_table_codes_are_validated():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("handle creation is covered on the GPU")
+    # host-only: the setter rejects codes outside 0..3 before touching the device
+    L = hm.lib()
+    assert L.hmat_set_tile_table(None, None) == 7     # no handle

@@ -193,3 +193,54 @@ def test_argument_errors(handle):
     st = L.hmat_bq_gemm(None, 0, 0, 0xFF, 0xFF, 4, 4, 4, 1.0, 0.0, A.data_ptr(), 4, 16, A.data_ptr(), 4, 16,
                         0.0, 0.0, C.data_ptr(), 4, 16, 0, 0.0, None, 0, None)
     assert st == 7                                        # no handle
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_grouped_batch_config_512(handle, mode):
+    """The batching configuration at full size: 512 products, m,n,k log-uniform in [32,1024].
+
+    16 sampled problems are compared with the oracle; every product is compared
+    between the two modes (independent arithmetic: FP64 DFMA vs residue GEMMs)."""
+    dev = torch.device("cuda")
+    shapes = bi.batch_shapes(104, 512)
+    mats, descs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A = bi.uniform(10_000 + i, m, k, device=dev)
+        B = bi.uniform(20_000 + i, k, n, device=dev)
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        mats.append((A, B, C))
+        descs.append(hm.make_desc(A, B, C))
+    hm.hmat_bq_gemm_grouped(handle, descs, mode=mode, tol=TOL, use_graph=True, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    small = [i for i, (m, n, k) in enumerate(shapes) if m * n * k <= (1 << 25)]
+    for i in rng.choice(small, size=16, replace=False):
+        A, B, C = mats[i]
+        want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy())
+        assert rel(C.cpu().numpy(), want) <= (1e-14 if mode == "fp64" else TOL)
+    other = "split" if mode == "fp64" else "fp64"
+    outs = [C.clone() for _, _, C in mats]
+    hm.hmat_bq_gemm_grouped(handle, descs, mode=other, tol=TOL, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    for (A, B, C), first in zip(mats, outs):
+        e = float(torch.linalg.norm(C - first) / torch.linalg.norm(first))
+        assert e <= TOL, e
+
+
+@pytest.mark.parametrize("code", [1, 2, 3])
+def test_tile_table_widths_give_identical_results(handle, code):
+    """Every tuned tile width (64/128/256 columns) reproduces the oracle bit for bit."""
+    m, n, k = 150, 300, 130
+    A = bi.small_int(110, m, k)
+    B = bi.small_int(111, k, n)
+    t = np.zeros((16, 16), dtype=np.int8)
+    t[:, :] = code
+    handle.set_tile_table(t)
+    try:
+        got = run(handle, A, B, mode="split")
+    finally:
+        handle.set_tile_table(None)
+    np.testing.assert_array_equal(got, oracle.bq_gemm(A.numpy(), B.numpy()))
+    bad = np.full((16, 16), 7, dtype=np.int8)
+    with pytest.raises(hm.HmatError):
+        handle.set_tile_table(bad)
