@@ -225,8 +225,10 @@ hmat_status hmat_plan_info(int32_t opA, int32_t opB, uint32_t flagsA,
 hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
                             int32_t *moduli, int32_t *bits);
 
-/* Read and clear the device error word (0 = none; otherwise a bit mask of
- * which bounded wait gave up).  Synchronises the device. */
+/* Read and clear the device error word (0 = none; otherwise a bit mask:
+ * 0x1 producer, 0x2 MMA issuer, 0x4 epilogue wait of the residue GEMM gave
+ * up; 0x10 split mode met an Inf/NaN input; 0x20 the self-test wait gave up).
+ * Synchronises the device. */
 hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
 
 /* Tile-width table for split mode (written by the autotuner,
@@ -236,6 +238,15 @@ hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
  * built-in rule.  Affects later calls and hmat_workspace_size on this handle.
  * Errors: NOT_INITIALIZED, INVALID_VALUE (a code outside 0..3). */
 hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
+
+/* Failure-detection self-test: launch one thread that waits on a device
+ * barrier nothing will ever complete, with the same bounded wait the kernels
+ * use and a limit of limit_cycles clock cycles (1 .. 2^33).  The wait gives up,
+ * sets bit 5 (0x20) of the device error word and the kernel returns normally;
+ * the context stays usable.  hmat_get_device_error then reports 0x20.  Used by
+ * the tests to show that a stuck wait ends with an error status, not a hang.
+ * Errors: NOT_INITIALIZED, INVALID_VALUE, CUDA_ERROR. */
+hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, void *stream);
 
 /* Kernel profiling: when enabled, every library kernel launch on the handle
  * is bracketed by CUDA events on its launch stream; hmat_get_profile returns,

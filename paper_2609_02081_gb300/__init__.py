@@ -73,6 +73,7 @@ SIGNATURES = {
     "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
     "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
+    "hmat_debug_wait_selftest": (ctypes.c_int, [_ptr, _i64, _ptr]),
     "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
     "hmat_get_profile": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "hmat_reset_profile": (ctypes.c_int, [_ptr]),

@@ -14,6 +14,7 @@ enum : uint32_t {
   kErrWaitEpilogue = 1u << 2,
   kErrWaitTmem = 1u << 3,
   kErrNonFinite = 1u << 4,   // split mode met an Inf/NaN input
+  kErrWaitSelfTest = 1u << 5,  // hmat_debug_wait_selftest gave up (expected)
 };
 
 // Device address of the library's error word (defined in hmat_capi.cu); kernels

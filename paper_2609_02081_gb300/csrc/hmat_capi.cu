@@ -60,6 +60,7 @@ static cudaError_t noalloc_setup(int device, NoAllocAddrs* out) {
 
 size_t fp64_smem_bytes();
 cudaError_t fp64_configure();
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s);
 cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* d_plans, int64_t total_tiles,
                                  int grid, cudaStream_t stream);
 int fp64_tile_m();
@@ -633,6 +634,12 @@ hmat_status hmat_set_tile_table(hmat_handle h, const int8_t* table) {
   std::memcpy(h->split.tile_table, table, sizeof(h->split.tile_table));
   h->split.has_table = true;
   return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_debug_wait_selftest(hmat_handle h, int64_t limit_cycles, void* stream) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (limit_cycles <= 0 || limit_cycles > ((int64_t)1 << 33)) return HMAT_STATUS_INVALID_VALUE;
+  return cuda_status(launch_wait_selftest(limit_cycles, static_cast<cudaStream_t>(stream)));
 }
 
 hmat_status hmat_set_profiling(hmat_handle h, int32_t enable) {

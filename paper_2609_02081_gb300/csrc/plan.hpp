@@ -56,6 +56,10 @@ struct KPlan {
   int8_t rre[8][4], rim[8][4], rslot[8][3];
   int8_t pl[kMaxProducts], pr[kMaxProducts];
   int8_t w4[8][kMaxProducts];
+  // 1 when that side's groups are exactly the eight complex factors of
+  // Eq. bilinearH on all eight components (left: a1, a4, a2, a3, then the
+  // Hadamard rows; right: b1, b3, b4, b2, then the Hadamard rows), in that order
+  int32_t bilinear_left = 0, bilinear_right = 0;
 };
 
 namespace detail {
@@ -298,6 +302,19 @@ inline bool build_plan(unsigned fa, unsigned fb, KPlan* out) {
   p.nrf = (int32_t)ru.size();
   if (!layout_side(lu, p.lre, p.lim, p.lslot, &p.nlg)) return false;
   if (!layout_side(ru, p.rre, p.rim, p.rslot, &p.nrg)) return false;
+  // recognise the full bilinear factor groups (enables a butterfly path in the encoder)
+  CComb X[8], Y[8];
+  int w4t[8][4];
+  bilinear_tables(X, Y, w4t);
+  auto matches = [](int ng, int8_t re[8][4], int8_t im[8][4], const CComb* C) {
+    if (ng != 8) return 0;
+    for (int g = 0; g < 8; ++g)
+      for (int e = 0; e < 4; ++e)
+        if (re[g][e] != C[g].x[e] || im[g][e] != C[g].x[e]) return 0;
+    return 1;
+  };
+  p.bilinear_left = matches(p.nlg, p.lre, p.lim, X);
+  p.bilinear_right = matches(p.nrg, p.rre, p.rim, Y);
   *out = p;
   return true;
 }

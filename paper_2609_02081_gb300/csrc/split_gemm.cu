@@ -68,9 +68,10 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: true when the phase with `parity` completed; false on abort/timeout.
+// Bounded wait: true when the phase with `parity` completed; false on abort or
+// after `limit` clock cycles (then the abort flag and the error bit are set).
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint32_t* err,
-                                          uint32_t err_bit) {
+                                          uint32_t err_bit, long long limit = kWaitCycles) {
   long long t0 = 0;
   for (uint32_t it = 0;; ++it) {
     if (mbar_try(bar, parity)) return true;
@@ -78,7 +79,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       if (*abort_flag) return false;
       const long long now = clock64();
       if (t0 == 0) t0 = now;
-      else if (now - t0 > kWaitCycles) {
+      else if (now - t0 > limit) {
         *abort_flag = 1;
         atomicOr(err, err_bit);
         return false;
@@ -390,6 +391,25 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+}
+
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at; after `limit` cycles the wait gives up, sets kErrWaitSelfTest in
+// the device error word and the kernel returns normally.
+__global__ void wait_selftest_kernel(long long limit, uint32_t* err) {
+  __shared__ uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    (void)mbar_wait(smem_u32(&bar), 0u, &abort_flag, err, kErrWaitSelfTest, limit);
+  }
+}
+
+cudaError_t launch_wait_selftest(long long limit_cycles, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(limit_cycles, device_error_ptr());
+  return cudaGetLastError();
 }
 
 size_t split_gemm_smem_bytes() { return sizeof(GemmSmem) + 1024; }

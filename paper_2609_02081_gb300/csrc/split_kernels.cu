@@ -33,9 +33,12 @@ __constant__ float c_Pf[kMaxModuli + 1];                          // P / 2^(32 P
 __constant__ int c_Pbase[kMaxModuli + 1];                         // limb index one below P's top limb
 
 // ------------------------------------------------------------------ small exact modular helpers
-// Centred residue of an integer-valued float |v| < 2^24: v - p*rint(v/p), |result| <= (p+1)/2.
+// Centred residue of an integer-valued float |v| < 2^24: v - p*round(v/p),
+// |result| <= (p+1)/2.  round() by the 1.5 * 2^23 shift: for |t| < 2^22 the
+// sum t + 1.5*2^23 rounds t to an integer in round-to-nearest; v/p < 2^17.
 __device__ __forceinline__ float fmod_c(float v, const ModConst& mc) {
-  const float q = rintf(v * mc.inv);
+  const float shifted = fmaf(v, mc.inv, 12582912.0f);
+  const float q = shifted - 12582912.0f;
   return fmaf(-q, mc.pf, v);
 }
 
@@ -199,26 +202,25 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return r;
 }
 
-// Centred residue (as float) of a scaled integer: X = hi 2^23 + lo for
-// |X| <= 2^47 (LIMBS == 2), else X = x2 2^36 + x1 2^18 + x0 (|X| <= 2^52);
-// every limb and partial sum stays below 2^24, so float arithmetic is exact.
+// Centred residue (as float) of a scaled integer given by its float limbs:
+// X = hi 2^23 + lo for |X| <= 2^47 (LIMBS == 2), else X = x2 2^36 + x1 2^18 + x0
+// (|X| <= 2^52); every limb and partial sum stays below 2^24 (exact floats).
 template <int LIMBS>
-__device__ __forceinline__ float residue_of(long long X, const ModConst& mc, float c23) {
-  if (LIMBS == 2) {
-    const float lo = (float)(int)(X & 0x7FFFFF);
-    const float hi = (float)(long long)(X >> 23);
-    return fmod_c(fmaf(fmod_c(hi, mc), c23, lo), mc);
-  } else {
-    return residue_i64(X, mc);
-  }
+__device__ __forceinline__ float residue_of(const float* x, const ModConst& mc) {
+  if (LIMBS == 2) return fmod_c(fmaf(fmod_c(x[1], mc), mc.c23, x[0]), mc);
+  return fmod_c(fmaf(fmod_c(x[2], mc), mc.c36, fmaf(fmod_c(x[1], mc), mc.c18, fmod_c(x[0], mc))), mc);
 }
 
 template <int LIMBS>
-__global__ void __launch_bounds__(kEncThreads) split_encode_kernel(const SplitJob* __restrict__ jobs, int njobs,
+__global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const SplitJob* __restrict__ jobs, int njobs,
                                                                    const KPlan* __restrict__ plans, int side,
                                                                    unsigned char* __restrict__ ws) {
-  __shared__ long long xs[8][kEncK][kEncRows + 1];
+  // exact float limbs of the scaled integers: (lo, hi) with X = hi 2^23 + lo
+  // (LIMBS == 2), or (x0, x1, x2) with X = x2 2^36 + x1 2^18 + x0 (LIMBS == 3)
+  __shared__ float xs[8][kEncK][kEncRows + 1][LIMBS];
   __shared__ int s_row[kEncRows];
+  __shared__ float s_coef[8][8];     // group g: signed +-1 / 0 weight of component c (op signs folded in)
+  __shared__ int s_slot[8][3];       // factor slots of group g: Re, Im, Re+Im (-1: none)
   const int64_t blk = blockIdx.x;
   const int g = find_split_job(jobs, njobs, blk, side ? 2 : 1);
   const SplitJob& sj = jobs[g];
@@ -241,6 +243,19 @@ __global__ void __launch_bounds__(kEncThreads) split_encode_kernel(const SplitJo
     const int r = r0 + t;
     s_row[t] = (r < nout) ? reinterpret_cast<const int32_t*>(ws + (side ? sj.off_texp : sj.off_sexp))[r] : 0;
   }
+  const int ng = side ? P.nrg : P.nlg;
+  if (t < 64) {
+    const int gi = t / 8, c = t % 8;
+    float w = 0.f;
+    if (gi < ng) {
+      const int8_t* cf = c < 4 ? (side ? P.rre[gi] : P.lre[gi]) : (side ? P.rim[gi] : P.lim[gi]);
+      w = (float)(cf[c & 3] * sign[c]);
+    }
+    s_coef[gi][c] = w;
+  } else if (t < 64 + 24) {
+    const int gi = (t - 64) / 3, part = (t - 64) % 3;
+    s_slot[gi][part] = gi < ng ? (side ? P.rslot[gi][part] : P.lslot[gi][part]) : -1;
+  }
   __syncthreads();
   // phase 1: stage scaled integers (reads coalesced along the contiguous index)
   for (int idx = t; idx < 8 * kEncK * kEncRows; idx += kEncThreads) {
@@ -256,7 +271,14 @@ __global__ void __launch_bounds__(kEncThreads) split_encode_kernel(const SplitJo
       const unsigned long long bits = (unsigned long long)__double_as_longlong(__ldg(base + (int64_t)c * cs + off));
       X = scaled_int(bits, s_row[rr]);
     }
-    xs[c][kk][rr] = X;
+    if (LIMBS == 2) {
+      xs[c][kk][rr][0] = (float)(int)(X & 0x7FFFFF);
+      xs[c][kk][rr][LIMBS - 1] = (float)(long long)(X >> 23);
+    } else {
+      xs[c][kk][rr][0] = (float)(int)(X & 0x3FFFF);
+      xs[c][kk][rr][1] = (float)(int)((X >> 18) & 0x3FFFF);
+      xs[c][kk][rr][LIMBS - 1] = (float)(int)(X >> 36);
+    }
   }
   __syncthreads();
 
@@ -272,40 +294,88 @@ __global__ void __launch_bounds__(kEncThreads) split_encode_kernel(const SplitJo
   const int64_t plane_bytes = side ? sj.encB_plane : sj.encA_plane;
   unsigned char* enc = ws + (side ? sj.off_encB : sj.off_encA) + ((int64_t)rt * sj.nkb + kb) * tile_bytes +
                        (int64_t)(rin >> 3) * 1024 + (rin & 7) * 128 + ((c16 ^ (rin & 7)) << 4) + half8;
-  const int ng = side ? P.nrg : P.nlg;
+
+  const bool butterfly = side ? (P.bilinear_right != 0) : (P.bilinear_left != 0);
+  if (butterfly) {
+    // the eight complex factors of Eq. bilinearH: four single coefficients and the
+    // four Hadamard rows (two butterfly stages); each emits Re, Im and Re+Im
+    float sg[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) sg[c] = (float)sign[c];
+    // single-coefficient groups: left a1, a4, a2, a3; right b1, b3, b4, b2
+    const int pick0 = 0, pick1 = side ? 2 : 3, pick2 = side ? 3 : 1, pick3 = side ? 1 : 2;
+    auto emit = [&](int gi, const float (&re)[4], const float (&im)[4], int l, const ModConst& mc) {
+#pragma unroll
+      for (int part = 0; part < 3; ++part) {
+        const int f = s_slot[gi][part];
+        if (f < 0) continue;
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = fmod_c(part == 0 ? re[q] : (part == 1 ? im[q] : re[q] + im[q]), mc);
+        const uint2 pkd = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
+                                     __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
+        *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pkd;
+      }
+    };
+    for (int l = 0; l < sj.nmod; ++l) {
+      const ModConst& mc = c_mod[l];
+      float xr[4][4], xi[4][4];      // [component][k]
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          xr[e][q] = sg[e] * residue_of<LIMBS>(xs[e][k4 * 4 + q][rr], mc);
+          xi[e][q] = sg[e + 4] * residue_of<LIMBS>(xs[e + 4][k4 * 4 + q][rr], mc);
+        }
+      const int pk[4] = {pick0, pick1, pick2, pick3};
+#pragma unroll
+      for (int g = 0; g < 4; ++g) emit(g, xr[pk[g]], xi[pk[g]], l, mc);
+      // Hadamard rows by two butterfly stages, in place
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float sr01 = xr[0][q] + xr[1][q], dr01 = xr[0][q] - xr[1][q];
+        const float sr23 = xr[2][q] + xr[3][q], dr23 = xr[2][q] - xr[3][q];
+        xr[0][q] = sr01 + sr23; xr[1][q] = sr01 - sr23; xr[2][q] = dr01 + dr23; xr[3][q] = dr01 - dr23;
+        const float si01 = xi[0][q] + xi[1][q], di01 = xi[0][q] - xi[1][q];
+        const float si23 = xi[2][q] + xi[3][q], di23 = xi[2][q] - xi[3][q];
+        xi[0][q] = si01 + si23; xi[1][q] = si01 - si23; xi[2][q] = di01 + di23; xi[3][q] = di01 - di23;
+      }
+#pragma unroll
+      for (int g = 0; g < 4; ++g) emit(4 + g, xr[g], xi[g], l, mc);
+    }
+    return;
+  }
 
   for (int l = 0; l < sj.nmod; ++l) {
     const ModConst& mc = c_mod[l];
-    const float c23 = mc.c23;
     float rc[8][4];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
 #pragma unroll
       for (int q = 0; q < 4; ++q)
-        rc[c][q] = ((flags >> c) & 1u) ? residue_of<LIMBS>(xs[c][k4 * 4 + q][rr], mc, c23) : 0.f;
+        rc[c][q] = ((flags >> c) & 1u) ? residue_of<LIMBS>(xs[c][k4 * 4 + q][rr], mc) : 0.f;
     }
     for (int gi = 0; gi < ng; ++gi) {
-      const int8_t* cre = side ? P.rre[gi] : P.lre[gi];
-      const int8_t* cim = side ? P.rim[gi] : P.lim[gi];
-      const int8_t* slot = side ? P.rslot[gi] : P.lslot[gi];
       float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int a = cre[e] * sign[e], b = cim[e] * sign[e + 4];
+        const float a = s_coef[gi][e], b = s_coef[gi][e + 4];   // +-1 or 0: exact products
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          if (a) re[q] += a > 0 ? rc[e][q] : -rc[e][q];
-          if (b) im[q] += b > 0 ? rc[e + 4][q] : -rc[e + 4][q];
+          re[q] = fmaf(a, rc[e][q], re[q]);
+          im[q] = fmaf(b, rc[e + 4][q], im[q]);
         }
       }
 #pragma unroll
       for (int part = 0; part < 3; ++part) {
-        const int f = slot[part];
+        const int f = s_slot[gi][part];
         if (f < 0) continue;
         float v[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) v[q] = fmod_c(part == 0 ? re[q] : (part == 1 ? im[q] : re[q] + im[q]), mc);
-        const uint2 pk = make_uint2(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]));
+        // |v| <= 128 is exact in BF16, whose bits are the upper half of the float's
+        const uint2 pk = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
+                                    __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
         *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pk;
       }
     }
@@ -441,10 +511,12 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
 #pragma unroll
       for (int w = 0; w < kMaxProducts / 4; ++w)
         if (w < nw) o = __dp4a((int)wpk[e][w], (int)tw[w], o);
-      // |o| <= 24 * 8 * 127 < 2^15: exact in float; r = o * 4^-1 mod p
-      float r = fmod_c(fmod_c((float)o, mc) * inv4, mc);
+      // |o| <= 24 * 8 * 127 < 2^15 and 4^-1 < 2^8: o * 4^-1 is an exact float below 2^23.
+      // int <-> float through the 1.5 * 2^23 bias (exact for |x| < 2^22, no conversion unit)
+      const float of = __int_as_float(o + 0x4B400000) - 12582912.0f;
+      float r = fmod_c(of * inv4, mc);
       if (r < 0.f) r += mc.pf;
-      const uint32_t ru = (uint32_t)r;
+      const uint32_t ru = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
 #pragma unroll
       for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru * c_crt[nm][l][q];
     }

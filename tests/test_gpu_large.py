@@ -1,0 +1,89 @@
+"""Full-size configurations, checked on sampled output elements against the oracle.
+
+The oracle computes C[rows, cols] directly from A's rows and B's columns (the
+plain definition restricted to those elements), so only a small sample has to
+leave the GPU.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import bq_inputs as bi
+import oracle
+import paper_2609_02081_gb300 as hm
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    with hm.Handle() as h:
+        yield h
+        assert h.device_error() == 0
+
+
+def sampled_check(A, B, C, opA, opB, rows, cols):
+    """Relative Frobenius error of C[:, rows, cols] against the oracle."""
+    tA = opA in ("T", "H")
+    tB = opB in ("T", "H")
+    r = torch.as_tensor(rows, device=A.device)
+    c = torch.as_tensor(cols, device=B.device)
+    Asub = (A[:, :, r] if tA else A[:, r, :]).cpu().numpy()
+    Bsub = (B[:, c, :] if tB else B[:, :, c]).cpu().numpy()
+    want = oracle.bq_gemm(Asub, Bsub, opA, opB)
+    got = C[:, r, :][:, :, c].cpu().numpy()
+    return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+
+CASES_4096 = [("BQ x BQ, op N,N", bi.BQ, bi.BQ, "N", "N"),
+              ("TRS x TRA, op N,N", bi.TRS, bi.TRA, "N", "N"),
+              ("BQ x BQ, op(A) = H", bi.BQ, bi.BQ, "H", "N")]
+
+
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+@pytest.mark.parametrize("name,fa,fb,opA,opB", CASES_4096)
+def test_config_n4096_fock_like(handle, mode, name, fa, fb, opA, opB):
+    """m = n = k = 4096, N(0,1) exp(-|i-j|/200) entries; 96 x 96 sampled output block."""
+    dev = torch.device("cuda")
+    n = 4096
+    A = bi.fock_like(201, n, n, flags=fa, device=dev)
+    B = bi.fock_like(202, n, n, flags=fb, device=dev)
+    C = torch.full((8, n, n), float("nan"), dtype=torch.float64, device=dev)
+    hm.hmat_bq_gemm(handle, A, B, C, opA, opB, fa, fb, mode=mode, tol=TOL)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(3)
+    rows = np.sort(rng.choice(n, 96, replace=False))
+    cols = np.sort(rng.choice(n, 96, replace=False))
+    err = sampled_check(A, B, C, opA, opB, rows, cols)
+    assert err <= (1e-14 if mode == "fp64" else TOL), err
+    assert torch.isfinite(C).all()
+
+
+@pytest.mark.skipif(os.environ.get("HMAT_RUN_LARGE") != "1",
+                    reason="n = 24576 FP64 takes ~13 minutes on GB300 (set HMAT_RUN_LARGE=1)")
+def test_config_n24576_fp64(handle):
+    """m = n = k = 24576 FP64 (the complex isomorph would exceed 2^31 elements),
+    Fock-like inputs, ~116 GB resident; 64 x 64 sampled output block."""
+    dev = torch.device("cuda")
+    n = 24576
+    A = bi.fock_like(205, n, n, device=dev)
+    B = bi.fock_like(206, n, n, device=dev)
+    C = torch.empty((8, n, n), dtype=torch.float64, device=dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    hm.hmat_bq_gemm(handle, A, B, C, mode="fp64")
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rng = np.random.default_rng(5)
+    rows = np.sort(rng.choice(n, 64, replace=False))
+    cols = np.sort(rng.choice(n, 64, replace=False))
+    err = sampled_check(A, B, C, "N", "N", rows, cols)
+    print(f"n=24576 fp64: {ms:.0f} ms, {64 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} TFLOP/s 64-equiv, "
+          f"{24 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} executed, sampled error {err:.3e}")
+    assert err <= 1e-14

@@ -244,3 +244,17 @@ def test_tile_table_widths_give_identical_results(handle, code):
     bad = np.full((16, 16), 7, dtype=np.int8)
     with pytest.raises(hm.HmatError):
         handle.set_tile_table(bad)
+
+
+def test_bounded_wait_gives_up_with_an_error_status(handle):
+    """A device wait that can never complete ends after its cycle limit with an
+    error bit (no hang, no fault), and the context keeps working afterwards."""
+    assert handle.device_error() == 0
+    st = hm.lib().hmat_debug_wait_selftest(handle.value, 2_000_000, torch.cuda.current_stream().cuda_stream)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert handle.device_error() == 0x20
+    assert handle.device_error() == 0          # read-and-clear
+    A = bi.small_int(120, 20, 30)
+    B = bi.small_int(121, 30, 10)
+    np.testing.assert_array_equal(run(handle, A, B, mode="split"), oracle.bq_gemm(A.numpy(), B.numpy()))
