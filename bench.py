@@ -369,6 +369,13 @@ def grouped(args, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    # per-stage kernel times (one extra eager step with event brackets)
+    h.set_profiling(True)
+    h.reset_profile()
+    hm.hmat_bq_gemm_grouped(h, descs, args.mode, args.tol, workspace=ws, stream=stream, use_graph=False)
+    torch.cuda.synchronize()
+    stages = {k: {"launches": v[0], "ms": v[1]} for k, v in ((k, h.profile(k)) for k in hm.KERNEL_IDS) if v[0]}
+    h.set_profiling(False)
     flops64 = sum(64 * 2.0 * m * n * k for m, n, k in shapes)
     value = world * flops64 / (ms * 1e-3) / 1e12
     if rank == 0:
@@ -388,7 +395,7 @@ def grouped(args, rank, world, local):
                                        "full biquaternions", "mode": args.mode, "graph": args.graph,
                            "tol": args.tol, "total_flops_64equiv": flops64,
                            "tile_table": args.tile_table, "workspace_bytes": ws_bytes},
-                "max_rel_fro_err_16_sampled": max(errs), "clocks": clk}
+                "max_rel_fro_err_16_sampled": max(errs), "clocks": clk, "stages_one_step": stages}
         print(json.dumps(line), flush=True)
     barrier(world)
     h.close()

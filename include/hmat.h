@@ -116,6 +116,10 @@ int32_t hmat_version(void);
 /* Text for a status code (static storage, never NULL). */
 const char *hmat_status_string(hmat_status s);
 
+/* Name and text of the CUDA error behind the calling thread's last
+ * HMAT_STATUS_CUDA_ERROR ("" if none yet); thread-local storage. */
+const char *hmat_last_cuda_error(void);
+
 /* Create a handle bound to the current CUDA device.  Allocates host-side
  * state only (pinned staging for grouped descriptors).  Errors:
  * INVALID_VALUE (NULL out pointer), CUDA_ERROR. */

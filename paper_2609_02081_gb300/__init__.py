@@ -54,6 +54,7 @@ _i32, _u32, _i64, _dbl, _ptr, _sz = (ctypes.c_int32, ctypes.c_uint32, ctypes.c_i
 SIGNATURES = {
     "hmat_version": (_i32, []),
     "hmat_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "hmat_last_cuda_error": (ctypes.c_char_p, []),
     "hmat_create": (ctypes.c_int, [ctypes.POINTER(_ptr)]),
     "hmat_destroy": (ctypes.c_int, [_ptr]),
     "hmat_workspace_size": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc), _i32, _dbl,
@@ -106,6 +107,8 @@ def lib(build_if_missing: bool = True):
 
 def _check(status: int, what: str):
     if status != 0:
+        if status == 5:
+            what = f"{what} [{lib().hmat_last_cuda_error().decode()}]"
         raise HmatError(status, what)
 
 

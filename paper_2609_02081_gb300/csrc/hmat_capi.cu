@@ -120,8 +120,12 @@ struct hmat_context {
 
 namespace {
 
+thread_local char g_last_cuda_error[256] = "";
+
 hmat_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return HMAT_STATUS_SUCCESS;
+  std::snprintf(g_last_cuda_error, sizeof(g_last_cuda_error), "%s: %s", cudaGetErrorName(e),
+                cudaGetErrorString(e));
   (void)cudaGetLastError();
   return HMAT_STATUS_CUDA_ERROR;
 }
@@ -256,6 +260,7 @@ ProfScope::~ProfScope() {
 }
 
 int handle_sm_count(hmat_context* h) { return h->sm_count; }
+hmat_status split_cuda_error(cudaError_t e) { return cuda_status(e); }
 SplitState& handle_split(hmat_context* h) { return h->split; }
 
 }  // namespace hmat
@@ -422,6 +427,8 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
 extern "C" {
 
 int32_t hmat_version(void) { return 100; }
+
+const char* hmat_last_cuda_error(void) { return g_last_cuda_error; }
 
 const char* hmat_status_string(hmat_status s) {
   switch (s) {

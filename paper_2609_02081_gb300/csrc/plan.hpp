@@ -60,6 +60,9 @@ struct KPlan {
   // Eq. bilinearH on all eight components (left: a1, a4, a2, a3, then the
   // Hadamard rows; right: b1, b3, b4, b2, then the Hadamard rows), in that order
   int32_t bilinear_left = 0, bilinear_right = 0;
+  // 1 when the products are the 24 of Eq. bilinearH with Gauss, in the order
+  // (P1: T1, T2, T3), (P2: ...), ..., (P8: ...), with the paper's weights
+  int32_t bilinear_full = 0;
 };
 
 namespace detail {
@@ -315,6 +318,23 @@ inline bool build_plan(unsigned fa, unsigned fb, KPlan* out) {
   };
   p.bilinear_left = matches(p.nlg, p.lre, p.lim, X);
   p.bilinear_right = matches(p.nrg, p.rre, p.rim, Y);
+  if (p.np == 24 && p.bilinear_left && p.bilinear_right) {
+    // expected weights: Gauss (T1 -> Re +1, Im -1; T2 -> Re -1, Im -1; T3 -> Im +1)
+    // times the weight of P_r in Q_e (Eq. bilinearH, times 4)
+    bool ok = true;
+    for (int r = 0; r < 8 && ok; ++r) {
+      const int gre[3] = {+1, -1, 0}, gim[3] = {-1, -1, +1};
+      for (int t = 0; t < 3 && ok; ++t) {
+        const int q = 3 * r + t;
+        for (int e = 0; e < 4; ++e) {
+          ok = ok && (p.w4[e][q] == w4t[r][e] * gre[t]) && (p.w4[e + 4][q] == w4t[r][e] * gim[t]);
+        }
+        // factors: group r, parts Re / Im / Re+Im on both sides
+        ok = ok && (p.pl[q] == p.lslot[r][t]) && (p.pr[q] == p.rslot[r][t]);
+      }
+    }
+    p.bilinear_full = ok ? 1 : 0;
+  }
   *out = p;
   return true;
 }

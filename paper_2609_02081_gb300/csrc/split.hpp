@@ -137,6 +137,8 @@ class ProfScope {
 };
 
 int handle_sm_count(hmat_context* h);
+// Record a CUDA error for hmat_last_cuda_error() and return HMAT_STATUS_CUDA_ERROR.
+hmat_status split_cuda_error(cudaError_t e);
 SplitState& handle_split(hmat_context* h);
 
 

@@ -189,21 +189,19 @@ __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int njobs, int
   return it;
 }
 
-// Centred residue of a signed 32-bit value modulo p (exact, any magnitude).
-__device__ __forceinline__ int cmod32(int x, int p, unsigned long long fm) {
-  auto fmod_u = [&](uint32_t v) { return (uint32_t)__umul64hi(fm * (unsigned long long)v, (unsigned long long)p); };
-  const uint32_t lo = (uint32_t)x & 0xFFFFu;
-  const int hi = x >> 16;
-  const uint32_t rhi = fmod_u((uint32_t)(hi + 256 * p));
-  const uint32_t r = fmod_u(rhi * fmod_u(65536u) + fmod_u(lo));
-  return (int)r > ((p - 1) >> 1) ? (int)r - p : (int)r;
+// v - p * round(v / p) for an integer-valued float |v| <= 2^24 (exact; the
+// rounding uses the 1.5 * 2^23 shift, valid while |v / p| < 2^22).
+// The result lies in [-(p+1)/2, (p+1)/2].
+__device__ __forceinline__ float fmod_centred(float v, float pf, float inv) {
+  const float q = fmaf(v, inv, 12582912.0f) - 12582912.0f;
+  return fmaf(-q, pf, v);
 }
 
 }  // namespace
 
 struct GemmModConst {
   int p;
-  unsigned long long fm;
+  float pf, inv;
 };
 __constant__ GemmModConst c_gmod[kModTable];
 
@@ -331,9 +329,12 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
       const int cols = it.bn >> 1;        // columns handled by this thread: 32, 64 or 128
       const int col0 = half * cols;
       const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
-      int acc[kBnMax / 2];
+      // running sum of chunk residues (each |r| <= (p+1)/2, at most 127 chunks:
+      // exact in float)
+      const float pf = c_gmod[it.l].pf, pinv = c_gmod[it.l].inv;
+      float acc[kBnMax / 2];
 #pragma unroll
-      for (int i = 0; i < kBnMax / 2; ++i) acc[i] = 0;
+      for (int i = 0; i < kBnMax / 2; ++i) acc[i] = 0.f;
       for (int c = 0; c < nchunks; ++c) {
         const uint32_t buf = chunk_ctr & 1u, aph = (chunk_ctr >> 1) & 1u;
         // one lane waits, the warp follows (tcgen05.ld is warp-collective)
@@ -351,7 +352,7 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
             TMEM_LD32(taddr + (uint32_t)(g * 32), r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[g * 32 + i] += __float2int_rn(__uint_as_float(r[i]));
+            for (int i = 0; i < 32; ++i) acc[g * 32 + i] += fmod_centred(__uint_as_float(r[i]), pf, pinv);
           }
         }
         tc_fence_before();
@@ -360,10 +361,9 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         ++chunk_ctr;
       }
       if (!ok) break;
-      // reduce mod p and store this row's residues (16-byte stores)
-      const int p = c_gmod[it.l].p;
-      const unsigned long long fm = c_gmod[it.l].fm;
+      // reduce mod p to [-127, 127] and store this row's residues (16-byte stores)
       int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
+      const float half = 0.5f * (pf - 1.f);
 #pragma unroll
       for (int g = 0; g < kBnMax / 2 / 16; ++g) {
         if (g * 16 < cols) {
@@ -373,8 +373,11 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
             uint32_t packed = 0;
 #pragma unroll
             for (int bidx = 0; bidx < 4; ++bidx) {
-              const int rr = cmod32(acc[g * 16 + v * 4 + bidx], p, fm);
-              packed |= ((uint32_t)(rr & 0xFF)) << (8 * bidx);
+              float rr = fmod_centred(acc[g * 16 + v * 4 + bidx], pf, pinv);
+              rr = rr > half ? rr - pf : (rr < -half ? rr + pf : rr);
+              // float -> int through the 1.5 * 2^23 bias (exact for small integers)
+              const int ri = __float_as_int(rr + 12582912.0f) - 0x4B400000;
+              packed |= ((uint32_t)(ri & 0xFF)) << (8 * bidx);
             }
             w[v] = packed;
           }
@@ -419,7 +422,8 @@ cudaError_t split_gemm_configure(const int* moduli, int n) {
   for (int l = 0; l < kModTable; ++l) {
     const int p = l < n ? moduli[l] : 255;
     g[l].p = p;
-    g[l].fm = ~0ull / (unsigned long long)p + 1ull;
+    g[l].pf = (float)p;
+    g[l].inv = 1.0f / (float)p;
   }
   cudaError_t e = cudaMemcpyToSymbol(c_gmod, g, sizeof(g));
   if (e != cudaSuccess) return e;

@@ -258,24 +258,24 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
     ProfScope ps(h, 1, stream);
     e = launch_split_exponents(d_jobs, njobs, sp.exp_units, 0, stream, ws);
   }
-  if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 2, stream);
     e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws, sp.max_bits);
     if (e == cudaSuccess) e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws, sp.max_bits);
   }
-  if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 3, stream);
     const int grid = (int)std::min<int64_t>(sp.items, handle_sm_count(h));
     e = launch_split_gemm(d_jobs, njobs, sp.items, grid, stream, ws);
   }
-  if (e != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 4, stream);
     e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod);
   }
-  return e == cudaSuccess ? HMAT_STATUS_SUCCESS : HMAT_STATUS_CUDA_ERROR;
+  return e == cudaSuccess ? HMAT_STATUS_SUCCESS : split_cuda_error(e);
 }
 
 // Upload the job table through the handle's staging buffer and launch.

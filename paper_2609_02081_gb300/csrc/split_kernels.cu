@@ -484,12 +484,53 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
 #pragma unroll
     for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
 
+  const bool structured = P.bilinear_full != 0;
   for (int l = 0; l < nm; ++l) {
     issue(l + 2);
     cp_async_wait2();            // modulus l has landed
     __syncthreads();
     const ModConst& mc = c_mod[l];
     const uint8_t(*slot)[kCrtThreads] = ring[l % kStages];
+    if (structured) {
+      // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
+      // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
+      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); all exact floats
+      float pre[8], pim[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        float t[3];
+#pragma unroll
+        for (int u = 0; u < 3; ++u)   // int8 -> float through the 1.5 * 2^23 bias
+          t[u] = __int_as_float(0x4B400000 + (int)(int8_t)slot[3 * r + u][tid]) - 12582912.0f;
+        pre[r] = t[0] - t[1];
+        pim[r] = t[2] - t[0] - t[1];
+      }
+      float q4[8];
+      {
+        const float a = pre[4] + pre[5], b = pre[4] - pre[5], c = pre[6] + pre[7], dd = pre[6] - pre[7];
+        q4[0] = fmaf(8.f, pre[0], -(a + c));
+        q4[1] = fmaf(-8.f, pre[1], a - c);
+        q4[2] = fmaf(-8.f, pre[2], b + dd);
+        q4[3] = fmaf(-8.f, pre[3], b - dd);
+        const float ai = pim[4] + pim[5], bi = pim[4] - pim[5], ci = pim[6] + pim[7], di = pim[6] - pim[7];
+        q4[4] = fmaf(8.f, pim[0], -(ai + ci));
+        q4[5] = fmaf(-8.f, pim[1], ai - ci);
+        q4[6] = fmaf(-8.f, pim[2], bi + di);
+        q4[7] = fmaf(-8.f, pim[3], bi - di);
+      }
+      const float inv4 = (float)mc.inv4;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        // |4Q| <= 8*254 + 4*254 and 4^-1 < 2^8: the product is an exact float below 2^22
+        float r = fmod_c(q4[e] * inv4, mc);
+        if (r < 0.f) r += mc.pf;
+        const uint32_t ru = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
+#pragma unroll
+        for (int qq = 0; qq < L; ++qq) acc[e][qq] += (unsigned long long)ru * c_crt[nm][l][qq];
+      }
+      __syncthreads();           // slot l % 3 is refilled by issue(l + 3)
+      continue;
+    }
     uint32_t tw[kMaxProducts / 4];
 #pragma unroll
     for (int w = 0; w < kMaxProducts / 4; ++w) {
