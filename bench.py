@@ -46,6 +46,9 @@ def parse():
                     help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
+    ap.add_argument("--algo", choices=["bilinear", "standard", "isomorph"], default="bilinear",
+                    help="product algorithm: the bilinear scheme, component-wise (HMAT-standard) "
+                         "or the complex isomorph (CMAT)")
     return ap.parse_args()
 
 
@@ -53,7 +56,7 @@ def workload_config(args):
     return {"workload": f"bq_gemm m=n=k={args.n} Fock-like N(0,1)*exp(-|i-j|/200) with per-row scales "
                         f"10^U(-6,0), full biquaternions x full biquaternions, op N,N, C=AB",
             "m": args.n, "n": args.n, "k": args.n, "mode": args.mode, "tol": args.tol,
-            "flags": "BQxBQ", "seed": args.seed,
+            "flags": "BQxBQ", "seed": args.seed, "algo": getattr(args, "algo", "bilinear"),
             "l2": "inputs larger than L2 (8 x n^2 x 8 B per operand), no flush"}
 
 
@@ -224,6 +227,7 @@ def ours(args, rank, world, local):
     B = bi.fock_like(args.seed + 1, n, n, row_scale=True, device=dev)
     C = torch.empty((8, n, n), dtype=torch.float64, device=dev)
     h = hm.Handle()
+    h.set_algorithm(args.algo)
     d = hm.make_desc(A, B, C)
     ws_bytes = hm.hmat_workspace_size(h, [d], args.mode, args.tol)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
@@ -259,8 +263,14 @@ def ours(args, rank, world, local):
 
     # accuracy on sampled rows (rank 0)
     info = {}
-    P, _, _, _, _ = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ)
-    mods, bits = hm.split_info(n, args.tol)
+    # the real products one step executes: plan products x their size relative to n^3
+    if args.algo == "isomorph":
+        P = hm.plan_info("N", "N", hm.HMAT_COMPLEX, hm.HMAT_COMPLEX)[0]
+        size, kin = 8, 2 * n          # one complex product of 2n x 2n x 2n
+    else:
+        P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ, algo=args.algo)[0]
+        size, kin = 1, n
+    mods, bits = hm.split_info(kin, args.tol)
     if rank == 0:
         rng = np.random.default_rng(args.seed + 7)
         rows = np.sort(rng.choice(n, size=args.sample_rows, replace=False))
@@ -284,7 +294,7 @@ def ours(args, rank, world, local):
             fms = e0.elapsed_time(e1)
             got64 = C[:, torch.as_tensor(rows, device=dev), :].cpu().numpy()
             info["fp64_plain"] = {"ms": fms, "tflops_64equiv": flops64 / (fms * 1e-3) / 1e12,
-                                  "tflops_executed": P * 2.0 * n ** 3 / (fms * 1e-3) / 1e12,
+                                  "tflops_executed": P * size * 2.0 * n ** 3 / (fms * 1e-3) / 1e12,
                                   "rel_fro_err_sampled": float(np.linalg.norm(got64 - want) / np.linalg.norm(want)),
                                   "speedup_split_vs_fp64": fms / ms}
 
@@ -303,23 +313,38 @@ def ours(args, rank, world, local):
         e1.record(stream)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / args.e2e_steps
+        # breakdown of one end-to-end step: copies in, product, copy out
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        A.copy_(Ah, non_blocking=True)
+        B.copy_(Bh, non_blocking=True)
+        ev[1].record(stream)
+        step()
+        ev[2].record(stream)
+        Ch.copy_(C, non_blocking=True)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
         info["e2e"] = {"value": flops64 / (ems * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "ms_per_step": ems}
+                       "d2h_bytes_per_step": d2h, "ms_per_step": ems,
+                       "breakdown_ms": {"h2d": ev[0].elapsed_time(ev[1]), "product": ev[1].elapsed_time(ev[2]),
+                                        "d2h": ev[2].elapsed_time(ev[3])}}
 
     if rank == 0:
         peaks, src = measured_peaks()
         gl, gms = kernels["split_residue_gemm"] if args.mode == "split" else kernels["fp64_bilinear"]
+        wl_key = f"n={n} split tol={args.tol}" + ("" if args.algo == "bilinear" else f" algo={args.algo}")
         if args.mode == "split":
-            alg = len(mods) * P * 2.0 * n * n * n           # BF16 tensor flops of one GEMM launch
+            # BF16 tensor flops of the GEMM launches of one step, per launch
+            alg = len(mods) * P * size * 2.0 * n * n * n * args.steps / max(gl, 1)
             avg = gms / max(gl, 1)
             ach = alg / (avg * 1e-3) / 1e12
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
             roof = {"bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": recorded_traffic("split_gemm.cu", f"n={n} split tol={args.tol}"),
+                    "traffic": recorded_traffic("split_gemm.cu", wl_key),
                     "kernel": "split_residue_gemm_kernel", "peak_source": f"bf16 sustained ({src})",
                     "algorithmic_flops_per_launch": alg, "avg_launch_ms": avg}
         else:
-            alg = P * 2.0 * n * n * n
+            alg = P * size * 2.0 * n * n * n * args.steps / max(gl, 1)   # a plan over 24 products takes passes
             avg = gms / max(gl, 1)
             ach = alg / (avg * 1e-3) / 1e12
             peak = 1.204   # measured DFMA throughput (152 SMs x 2 FP64 FMA/clk)
@@ -337,7 +362,7 @@ def ours(args, rank, world, local):
                 "rel_fro_err_sampled": info.get("rel_fro_err_sampled"),
                 "err_ok": (info.get("rel_fro_err_sampled") is not None and info["rel_fro_err_sampled"] <= 1e-12),
                 "fp64_plain": info.get("fp64_plain"), "stages": stages,
-                "executed_tflops": value * (len(mods) * P if args.mode == "split" else P) / 64.0}
+                "executed_tflops": value * size * (len(mods) * P if args.mode == "split" else P) / 64.0}
         print(json.dumps(line), flush=True)
     barrier(world)
     h.close()

@@ -96,6 +96,22 @@ typedef enum {
     HMAT_MODE_SPLIT = 1
 } hmat_mode;
 
+/* Algorithm for later products on a handle (hmat_set_algorithm).
+ *   BILINEAR  the paper's bilinear scheme (Sec. III B, Eq. bilinearH with
+ *             Gauss): 24 real products for full biquaternions; for mixed
+ *             subalgebras the cheaper of it and component-wise terms with
+ *             Gauss's rule.  The default.
+ *   STANDARD  the component-wise algorithm the paper calls HMAT-standard: one
+ *             real product per pair of present components (64 for full
+ *             biquaternions, 16 for real quaternions).
+ *   ISOMORPH  the complex route the paper calls CMAT: op(A), op(B) mapped to
+ *             their complex 2m x 2k / 2k x 2n images (Sec. III M+/M- blocks),
+ *             one complex product (Gauss: 3 real products of the doubled
+ *             size), mapped back with Eq. mapping-formulas.  Needs workspace
+ *             for the images in both modes (hmat_workspace_size).
+ * STANDARD and ISOMORPH exist for comparison with BILINEAR on the same GPU. */
+typedef enum { HMAT_ALGO_BILINEAR = 0, HMAT_ALGO_STANDARD = 1, HMAT_ALGO_ISOMORPH = 2 } hmat_algo;
+
 typedef struct hmat_context *hmat_handle;
 
 /* One product C <- alpha op(A) op(B) + beta C for the grouped call. */
@@ -208,18 +224,26 @@ size_t hmat_split_noalloc_capacity(void);
 /* Index of the descriptor that made the last grouped call fail, or -1. */
 int32_t hmat_last_bad_index(hmat_handle handle);
 
-/* The product plan used for (opA, opB, flagsA, flagsB) — host only, for
- * tests and tools.  On return *n_products = P (<= 24) and, for p < P,
+/* Select the algorithm (hmat_algo) of later hmat_bq_gemm and
+ * hmat_bq_gemm_grouped calls on this handle; hmat_workspace_size follows the
+ * same setting.  hmat_bq_gemm_split_noalloc always uses BILINEAR.
+ * Errors: NOT_INITIALIZED, INVALID_VALUE. */
+hmat_status hmat_set_algorithm(hmat_handle handle, int32_t algo);
+
+/* The product plan of algorithm algo (BILINEAR or STANDARD) for (opA, opB,
+ * flagsA, flagsB) — host only, for tests and tools.  On return
+ * *n_products = P (<= 64) and, for p < P,
  *   U[p*8 + c]  in {-1,0,1}: coefficient of STORED component c of A in the
  *               left factor of real product p (op signs folded in);
  *   V[p*8 + d]  likewise for B;
- *   W[e*24 + p] coefficient of product p in output component e (exact
+ *   W[e*64 + p] coefficient of product p in output component e (exact
  *               dyadic rationals: 0, +-1/4, +-1/2, +-1, +-2, ...),
  * so that output_e = sum_p W[e,p] (sum_c U[p,c] A_c)(sum_d V[p,d] B_d).
  * strategy (may be NULL): 0 = the paper's bilinear scheme (Eq. bilinearH +
- * Gauss), 1 = component-wise terms with Gauss (chosen when fewer products).
+ * Gauss), 1 = component-wise terms with Gauss (chosen when fewer products),
+ * 2 = the standard component-wise algorithm.
  * U, V, W may be NULL to query only the count. */
-hmat_status hmat_plan_info(int32_t opA, int32_t opB, uint32_t flagsA,
+hmat_status hmat_plan_info(int32_t algo, int32_t opA, int32_t opB, uint32_t flagsA,
                            uint32_t flagsB, int32_t *n_products, int8_t *U,
                            int8_t *V, double *W, int32_t *strategy);
 
@@ -257,7 +281,8 @@ hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, v
  * per kernel id, the number of launches and the summed event time (ms) since
  * the last reset (it synchronises on the recorded events).  Kernel ids:
  * 0 fp64 bilinear, 1 split exponents, 2 split encode, 3 split residue GEMM,
- * 4 split CRT/recombine, 5 beta-scale. */
+ * 4 split CRT/recombine, 5 beta-scale, 6 isomorph map-in, 7 isomorph
+ * map-out. */
 hmat_status hmat_set_profiling(hmat_handle handle, int32_t enable);
 hmat_status hmat_get_profile(hmat_handle handle, int32_t kernel_id,
                              int64_t *launches, double *total_ms);

@@ -24,9 +24,11 @@ HMAT_OP_N, HMAT_OP_T, HMAT_OP_C, HMAT_OP_H, HMAT_OP_QC = 0, 1, 2, 3, 4
 OPS = {"N": HMAT_OP_N, "T": HMAT_OP_T, "C": HMAT_OP_C, "H": HMAT_OP_H, "QC": HMAT_OP_QC}
 HMAT_REAL, HMAT_COMPLEX, HMAT_TRS, HMAT_TRA, HMAT_BQ = 0x01, 0x11, 0x0F, 0xF0, 0xFF
 HMAT_MODE_FP64, HMAT_MODE_SPLIT = 0, 1
+HMAT_ALGO_BILINEAR, HMAT_ALGO_STANDARD, HMAT_ALGO_ISOMORPH = 0, 1, 2
+ALGOS = {"bilinear": HMAT_ALGO_BILINEAR, "standard": HMAT_ALGO_STANDARD, "isomorph": HMAT_ALGO_ISOMORPH}
 MODES = {"fp64": HMAT_MODE_FP64, "split": HMAT_MODE_SPLIT}
 KERNEL_IDS = {"fp64_bilinear": 0, "split_exponents": 1, "split_encode": 2, "split_residue_gemm": 3,
-              "split_crt": 4, "beta_scale": 5}
+              "split_crt": 4, "beta_scale": 5, "iso_map_in": 6, "iso_map_out": 7}
 STATUS = {0: "SUCCESS", 1: "INVALID_VALUE", 2: "UNSUPPORTED", 3: "MISALIGNED", 4: "WORKSPACE_TOO_SMALL",
           5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "NOT_INITIALIZED", 8: "TOLERANCE_UNREACHABLE", 9: "INTERNAL"}
 
@@ -69,8 +71,9 @@ SIGNATURES = {
                                                   _dbl, _ptr]),
     "hmat_split_noalloc_capacity": (_sz, []),
     "hmat_last_bad_index": (_i32, [_ptr]),
-    "hmat_plan_info": (ctypes.c_int, [_i32, _i32, _u32, _u32, ctypes.POINTER(_i32), ctypes.c_void_p,
+    "hmat_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _u32, _u32, ctypes.POINTER(_i32), ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_i32)]),
+    "hmat_set_algorithm": (ctypes.c_int, [_ptr, _i32]),
     "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
     "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
@@ -113,15 +116,16 @@ def _check(status: int, what: str):
 
 
 # ----------------------------------------------------------------------------- host-only queries
-def plan_info(opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ):
+def plan_info(opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, algo="bilinear"):
     """(n_products, U[P,8], V[P,8], W[8,P], strategy) of the product plan (hmat_plan_info)."""
     L = lib()
     n = _i32()
     st = _i32()
-    U = np.zeros((24, 8), dtype=np.int8)
-    V = np.zeros((24, 8), dtype=np.int8)
-    W = np.zeros((8, 24), dtype=np.float64)
-    _check(L.hmat_plan_info(_op(opA), _op(opB), flagsA, flagsB, ctypes.byref(n), U.ctypes.data, V.ctypes.data,
+    U = np.zeros((64, 8), dtype=np.int8)
+    V = np.zeros((64, 8), dtype=np.int8)
+    W = np.zeros((8, 64), dtype=np.float64)
+    a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    _check(L.hmat_plan_info(a, _op(opA), _op(opB), flagsA, flagsB, ctypes.byref(n), U.ctypes.data, V.ctypes.data,
                             W.ctypes.data, ctypes.byref(st)), "hmat_plan_info")
     P = n.value
     return P, U[:P].copy(), V[:P].copy(), W[:, :P].copy(), st.value
@@ -188,6 +192,11 @@ class Handle:
 
     def reset_profile(self):
         _check(lib().hmat_reset_profile(self._h), "hmat_reset_profile")
+
+    def set_algorithm(self, algo):
+        """'bilinear' (default), 'standard' (component-wise, HMAT-standard) or 'isomorph' (CMAT)."""
+        a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+        _check(lib().hmat_set_algorithm(self._h, a), "hmat_set_algorithm")
 
     def set_tile_table(self, table):
         """Install a 16 x 16 tile-width code table (None: built-in rule); see autotune.py."""
@@ -273,7 +282,7 @@ def hmat_bq_gemm(handle: Handle, A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flag
     d = make_desc(A, B, C, opA, opB, flagsA, flagsB, alpha, beta)
     md = _mode(mode)
     ws = workspace
-    if ws is None and md == HMAT_MODE_SPLIT:
+    if ws is None:
         ws, _ = _workspace(hmat_workspace_size(handle, [d], md, tol), C.device)
     ws_ptr = ws.data_ptr() if ws is not None else None
     ws_bytes = ws.numel() if ws is not None else 0
@@ -290,7 +299,7 @@ def hmat_bq_gemm_grouped(handle: Handle, descs, mode="fp64", tol=0.0, workspace=
     md = _mode(mode)
     arr = (hmat_gemm_desc * len(descs))(*descs)
     ws = workspace
-    if ws is None and md == HMAT_MODE_SPLIT:
+    if ws is None:
         import torch
         ws, _ = _workspace(hmat_workspace_size(handle, descs, md, tol), device or torch.device("cuda"))
     ws_ptr = ws.data_ptr() if ws is not None else None

@@ -37,6 +37,26 @@ struct JobDesc {
   int64_t tile_begin;    // first global tile of this job (FP64 kernel)
 };
 
+// Complex-isomorph route (isomorph.cu): image of op(X) as two planes (real,
+// imaginary) of 2 rows x 2 cols doubles, and the inverse map with alpha / beta.
+struct IsoMapIn {
+  const double* X;           // biquaternion source (8 components)
+  int64_t ld, cs;            // leading dimension, component stride
+  int32_t rows, cols;        // op(X) is rows x cols
+  int32_t trans;             // op transposes
+  uint32_t flags;            // present components
+  int8_t sign[8];            // op signs
+  double* out;               // 2 planes of (2 rows) x (2 cols)
+};
+struct IsoMapOut {
+  const double* Xc;          // the complex product: real plane of (2m) x (2n) at Xc,
+  int64_t im_off;            // imaginary plane at Xc + im_off
+  int32_t m, n;
+  double alpha_re, alpha_im, beta_re, beta_im;
+  double* C;
+  int64_t ldc, sC;
+};
+
 // Locate the job owning global tile t (jobs sorted by tile_begin).
 __device__ __forceinline__ int find_job(const JobDesc* jobs, int njobs, int64_t t) {
   int lo = 0, hi = njobs - 1;

@@ -26,13 +26,16 @@
 namespace hmat {
 
 constexpr int F_BM = 32, F_BN = 32, F_BK = 8, F_THREADS = 256;
+// products per pass: 24 accumulators per output point fill the register file;
+// plans with more products run as several passes (host side)
+constexpr int F_MAXP = 24;
 
 struct Fp64Smem {
   double araw[2][8][F_BK][F_BM];    // staged op(A) components (double buffer)
   double braw[2][8][F_BK][F_BN];    // staged op(B) components
-  double xs[kMaxProducts][F_BK][F_BM];  // left factors
-  double ys[kMaxProducts][F_BK][F_BN];  // right factors
-  double wd[8][kMaxProducts];           // recombination weights w4 / 4 of the loaded plan
+  double xs[kMaxFactors][F_BK][F_BM];   // left factors
+  double ys[kMaxFactors][F_BK][F_BN];   // right factors
+  double wd[8][F_MAXP];                 // recombination weights w4 / 4 of the loaded plan
   KPlan plan;
   int plan_id;
 };
@@ -155,15 +158,15 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
       __syncthreads();
       if (t == 0) { s.plan = plans[jb.plan]; s.plan_id = jb.plan; }
       __syncthreads();
-      for (int w = t; w < 8 * kMaxProducts; w += F_THREADS)
-        s.wd[w / kMaxProducts][w % kMaxProducts] = 0.25 * (double)s.plan.w4[w / kMaxProducts][w % kMaxProducts];
+      for (int w = t; w < 8 * F_MAXP; w += F_THREADS)
+        s.wd[w / F_MAXP][w % F_MAXP] = 0.25 * (double)s.plan.w4[w / F_MAXP][w % F_MAXP];
       __syncthreads();
     }
     const int np = s.plan.np;
 
-    double acc[kMaxProducts][4];
+    double acc[F_MAXP][4];
 #pragma unroll
-    for (int q = 0; q < kMaxProducts; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
+    for (int q = 0; q < F_MAXP; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
 
     const int nkb = (jb.k + F_BK - 1) / F_BK;
     if (nkb > 0) stage_raw(s, 0, jb, i0, j0, 0);
@@ -178,7 +181,7 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
 #pragma unroll 2
       for (int kk = 0; kk < F_BK; ++kk) {
 #pragma unroll
-        for (int q = 0; q < kMaxProducts; ++q) {
+        for (int q = 0; q < F_MAXP; ++q) {
           if (q < np) {
             const double2 x = *reinterpret_cast<const double2*>(&s.xs[s.plan.pl[q]][kk][2 * ty]);
             const double2 y = *reinterpret_cast<const double2*>(&s.ys[s.plan.pr[q]][kk][2 * tx]);
@@ -204,7 +207,7 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
       for (int e = 0; e < 8; ++e) {
         double o = 0.0;
 #pragma unroll
-        for (int pp = 0; pp < kMaxProducts; ++pp) {
+        for (int pp = 0; pp < F_MAXP; ++pp) {
           if (pp < np) {
             if (s.plan.w4[e][pp] != 0) o = fma(acc[pp][pt], s.wd[e][pp], o);
           }
@@ -250,6 +253,7 @@ cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* 
 }
 
 int fp64_tile_m() { return F_BM; }
+int fp64_max_products() { return F_MAXP; }
 int fp64_tile_n() { return F_BN; }
 
 }  // namespace hmat

@@ -65,10 +65,13 @@ cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* 
                                  int grid, cudaStream_t stream);
 int fp64_tile_m();
 int fp64_tile_n();
+int fp64_max_products();
+cudaError_t launch_iso_map_in(const IsoMapIn& p, cudaStream_t s);
+cudaError_t launch_iso_map_out(const IsoMapOut& p, cudaStream_t s);
 
 constexpr int kPlanSlots = 256;
 constexpr int kStageSlots = 8;
-constexpr int kKernelIds = 6;
+constexpr int kKernelIds = 8;
 constexpr size_t kGraphCache = 8;
 
 }  // namespace hmat
@@ -106,15 +109,17 @@ struct hmat_context {
   struct GraphEntry {
     std::vector<unsigned char> key;
     cudaGraphExec_t exec = nullptr;
-    JobDesc* d_fp64 = nullptr;
+    std::vector<JobDesc*> d_fp64;   // one job table per FP64 launch group
     SplitJob* d_split = nullptr;
     void release() {
       if (exec) cudaGraphExecDestroy(exec);
-      if (d_fp64) cudaFree(d_fp64);
+      for (JobDesc* d : d_fp64)
+        if (d) cudaFree(d);
       if (d_split) cudaFree(d_split);
-      exec = nullptr; d_fp64 = nullptr; d_split = nullptr;
+      exec = nullptr; d_fp64.clear(); d_split = nullptr;
     }
   };
+  int32_t algo = HMAT_ALGO_BILINEAR;
   std::vector<GraphEntry> graphs;
 };
 
@@ -185,22 +190,60 @@ hmat_status validate(const hmat_gemm_desc& d, JobDesc* out) {
   return HMAT_STATUS_SUCCESS;
 }
 
-// Plan slot for (fa, fb); uploads a new plan on `stream` the first time.
-hmat_status plan_slot(hmat_context* h, uint32_t fa, uint32_t fb, cudaStream_t stream, int* slot) {
-  const uint32_t key = (fa << 8) | fb;
-  for (int i = 0; i < h->n_plans; ++i)
-    if (h->plan_key[i] == key) { *slot = i; return HMAT_STATUS_SUCCESS; }
-  if (h->n_plans >= kPlanSlots) return HMAT_STATUS_UNSUPPORTED;
-  KPlan p;
-  if (!build_plan(fa, fb, &p)) return HMAT_STATUS_INTERNAL;
-  const int i = h->n_plans;
-  h->h_plans[i] = p;
+// Upload plan i (host copy already filled) on `stream`.
+hmat_status upload_plan(hmat_context* h, int i, uint32_t key, cudaStream_t stream) {
   cudaError_t e = cudaMemcpyAsync(h->d_plans + i, h->h_plans + i, sizeof(KPlan), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->plan_key[i] = key;
   h->n_plans = i + 1;
-  *slot = i;
   return HMAT_STATUS_SUCCESS;
+}
+
+// Key of a plan: algorithm, FP64 pass (0 = the whole plan) and the two flag bytes.
+uint32_t plan_key_of(int algo, int pass, uint32_t fa, uint32_t fb) {
+  return ((uint32_t)algo << 24) | ((uint32_t)pass << 16) | (fa << 8) | fb;
+}
+
+// Plan slot for (fa, fb) under algorithm algo; uploads a new plan on `stream` the first time.
+hmat_status plan_slot(hmat_context* h, uint32_t fa, uint32_t fb, int algo, cudaStream_t stream, int* slot) {
+  const uint32_t key = plan_key_of(algo, 0, fa, fb);
+  for (int i = 0; i < h->n_plans; ++i)
+    if (h->plan_key[i] == key) { *slot = i; return HMAT_STATUS_SUCCESS; }
+  if (h->n_plans >= kPlanSlots) return HMAT_STATUS_UNSUPPORTED;
+  KPlan p;
+  if (!build_plan(fa, fb, &p, algo)) return HMAT_STATUS_INTERNAL;
+  const int i = h->n_plans;
+  h->h_plans[i] = p;
+  hmat_status st = upload_plan(h, i, key, stream);
+  if (st == HMAT_STATUS_SUCCESS) *slot = i;
+  return st;
+}
+
+// Slot of pass `pass` (1-based) of a plan with more products than one FP64
+// pass holds: the same factor groups, products [(pass-1) P, pass P).
+hmat_status pass_slot(hmat_context* h, int full, int pass, cudaStream_t stream, int* slot) {
+  const uint32_t base = h->plan_key[full];
+  const uint32_t key = (base & ~(0xFFu << 16)) | ((uint32_t)pass << 16);
+  for (int i = 0; i < h->n_plans; ++i)
+    if (h->plan_key[i] == key) { *slot = i; return HMAT_STATUS_SUCCESS; }
+  if (h->n_plans >= kPlanSlots) return HMAT_STATUS_UNSUPPORTED;
+  const KPlan& P = h->h_plans[full];
+  const int per = fp64_max_products();
+  const int q0 = (pass - 1) * per, q1 = std::min(P.np, q0 + per);
+  KPlan s = P;
+  s.np = q1 - q0;
+  for (int q = 0; q < kMaxProducts; ++q) {
+    const bool in = q < s.np;
+    s.pl[q] = in ? P.pl[q0 + q] : 0;
+    s.pr[q] = in ? P.pr[q0 + q] : 0;
+    for (int e = 0; e < 8; ++e) s.w4[e][q] = in ? P.w4[e][q0 + q] : 0;
+  }
+  s.bilinear_full = 0;
+  const int i = h->n_plans;
+  h->h_plans[i] = s;
+  hmat_status st = upload_plan(h, i, key, stream);
+  if (st == HMAT_STATUS_SUCCESS) *slot = i;
+  return st;
 }
 
 // Copy jobs to the device through the staging ring; returns the device pointer.
@@ -270,55 +313,156 @@ namespace {
 
 const int8_t* split_table(hmat_context* h) { return h->split.has_table ? h->split.tile_table : nullptr; }
 
-// A validated call: FP64 jobs (with tile prefixes) and split jobs (with layouts).
-struct Prepared {
-  std::vector<JobDesc> f;
-  int64_t f_tiles = 0;
-  SplitPrep sp;
-  bool has_split = false;
+// A validated call: FP64 launch groups (a plan with more products than one
+// pass holds adds later groups that accumulate into C), split jobs (with
+// layouts) and, for the isomorph algorithm, the mapping launches around them.
+struct IsoJob {
+  IsoMapIn ina, inb;
+  IsoMapOut out;
 };
 
+struct Prepared {
+  std::vector<std::vector<JobDesc>> f;
+  std::vector<int64_t> f_tiles;
+  SplitPrep sp;
+  bool has_split = false;
+  int64_t split_offset = 0;            // split workspace starts here (after isomorph buffers)
+  std::vector<IsoJob> iso;
+  int64_t ws_needed = 0;
+};
+
+int64_t align_up256(int64_t x) { return (x + 255) & ~(int64_t)255; }
+
+// Workspace bytes of the isomorph buffers of one product: images of op(A) and
+// op(B) (real and imaginary planes, 8 m k + 8 k n doubles) and the complex
+// product.  The product kernels write all eight output components (zeros
+// where the plan has none), so the product buffer holds eight full planes of
+// 2m x 2n (32 m n doubles): component c starts at plane c, and the real and
+// imaginary parts are planes 0 and 4.
+int64_t iso_bytes(int64_t m, int64_t n, int64_t k) {
+  return align_up256(64 * m * k) + align_up256(64 * k * n) + align_up256(256 * m * n);
+}
+
+void add_fp64_job(Prepared* out, const JobDesc& j, int group) {
+  if ((int)out->f.size() <= group) out->f.resize(group + 1);
+  out->f[group].push_back(j);
+}
+
 hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                    size_t ws_bytes, cudaStream_t stream, Prepared* out) {
+                    void* workspace, size_t ws_bytes, cudaStream_t stream, Prepared* out) {
   if (count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
   if (tol < 0 || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) return HMAT_STATUS_INVALID_VALUE;
+  const int algo = h->algo;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  int64_t iso_off = 0;
   std::vector<JobDesc> split_jobs;
   for (int32_t i = 0; i < count; ++i) {
     JobDesc j;
     hmat_status st = validate(descs[i], &j);
     if (st != HMAT_STATUS_SUCCESS) { h->last_bad = i; return st; }
     if (j.m == 0 || j.n == 0) continue;
+    if (algo == HMAT_ALGO_ISOMORPH && j.k > 0) {
+      // CMAT route: images of op(A), op(B) -> one complex product -> inverse map
+      const int64_t need = iso_bytes(j.m, j.n, j.k);
+      if ((size_t)(iso_off + need) > ws_bytes || !ws) { h->last_bad = i; return HMAT_STATUS_WORKSPACE_TOO_SMALL; }
+      double* Xa = reinterpret_cast<double*>(ws + iso_off);
+      double* Xb = reinterpret_cast<double*>(ws + iso_off + align_up256(64 * (int64_t)j.m * j.k));
+      double* Xc = reinterpret_cast<double*>(ws + iso_off + align_up256(64 * (int64_t)j.m * j.k) +
+                                             align_up256(64 * (int64_t)j.k * j.n));
+      iso_off += need;
+      IsoJob ij;
+      ij.ina = IsoMapIn{j.A, j.lda, j.sA, j.m, j.k, j.transA, j.fa, {0}, Xa};
+      ij.inb = IsoMapIn{j.B, j.ldb, j.sB, j.k, j.n, j.transB, j.fb, {0}, Xb};
+      std::memcpy(ij.ina.sign, j.signA, 8);
+      std::memcpy(ij.inb.sign, j.signB, 8);
+      ij.out = IsoMapOut{Xc, 16 * (int64_t)j.m * j.n, j.m, j.n, j.alpha_re, j.alpha_im, j.beta_re, j.beta_im,
+                         j.C, j.ldc, j.sC};
+      out->iso.push_back(ij);
+      JobDesc in = j;
+      in.A = Xa; in.lda = 2 * (int64_t)j.k; in.sA = (int64_t)j.m * j.k;
+      in.B = Xb; in.ldb = 2 * (int64_t)j.n; in.sB = (int64_t)j.k * j.n;
+      in.C = Xc; in.ldc = 2 * (int64_t)j.n; in.sC = 4 * (int64_t)j.m * j.n;
+      in.m = 2 * j.m; in.n = 2 * j.n; in.k = 2 * j.k;
+      in.transA = 0; in.transB = 0;
+      in.fa = HMAT_COMPLEX; in.fb = HMAT_COMPLEX;
+      for (int c = 0; c < 8; ++c) { in.signA[c] = 1; in.signB[c] = 1; }
+      in.alpha_re = 1.0; in.alpha_im = 0.0; in.beta_re = 0.0; in.beta_im = 0.0;
+      j = in;
+    }
     int slot = 0;
-    st = plan_slot(h, j.fa, j.fb, stream, &slot);
+    const int palgo = (algo == HMAT_ALGO_STANDARD) ? kAlgoStandard : kAlgoBilinear;
+    st = plan_slot(h, j.fa, j.fb, palgo, stream, &slot);
     if (st != HMAT_STATUS_SUCCESS) { h->last_bad = i; return st; }
     j.plan = slot;
     // k == 0 or an all-absent operand: the product vanishes; the FP64 kernel applies beta.
-    const bool trivial = (j.k == 0) || h->h_plans[slot].np == 0;
-    if (mode == HMAT_MODE_SPLIT && !trivial) split_jobs.push_back(j);
-    else out->f.push_back(j);
+    const int np = h->h_plans[slot].np;
+    const bool trivial = (j.k == 0) || np == 0;
+    if (mode == HMAT_MODE_SPLIT && !trivial) {
+      split_jobs.push_back(j);
+    } else if (np <= fp64_max_products()) {
+      add_fp64_job(out, j, 0);
+    } else {
+      const int passes = (np + fp64_max_products() - 1) / fp64_max_products();
+      for (int ps = 1; ps <= passes; ++ps) {
+        JobDesc jp = j;
+        st = pass_slot(h, slot, ps, stream, &jp.plan);
+        if (st != HMAT_STATUS_SUCCESS) { h->last_bad = i; return st; }
+        if (ps > 1) { jp.beta_re = 1.0; jp.beta_im = 0.0; }   // later passes add into C
+        add_fp64_job(out, jp, ps - 1);
+      }
+    }
   }
   const int tm = fp64_tile_m(), tn = fp64_tile_n();
-  for (auto& j : out->f) {
-    j.tiles_m = (j.m + tm - 1) / tm;
-    j.tiles_n = (j.n + tn - 1) / tn;
-    j.tile_begin = out->f_tiles;
-    out->f_tiles += (int64_t)j.tiles_m * j.tiles_n;
+  for (auto& group : out->f) {
+    int64_t tiles = 0;
+    for (auto& j : group) {
+      j.tiles_m = (j.m + tm - 1) / tm;
+      j.tiles_n = (j.n + tn - 1) / tn;
+      j.tile_begin = tiles;
+      tiles += (int64_t)j.tiles_m * j.tiles_n;
+    }
+    out->f_tiles.push_back(tiles);
   }
+  out->split_offset = align_up256(iso_off);
+  out->ws_needed = out->split_offset;
   if (!split_jobs.empty()) {
-    hmat_status st = split_prepare(split_jobs, h->h_plans, tol, ws_bytes, split_table(h), &out->sp);
+    const size_t avail = ws_bytes > (size_t)out->split_offset ? ws_bytes - (size_t)out->split_offset : 0;
+    hmat_status st = split_prepare(split_jobs, h->h_plans, tol, avail, split_table(h), &out->sp);
     if (st != HMAT_STATUS_SUCCESS) return st;
     out->has_split = true;
+    out->ws_needed += out->sp.ws_needed;
   }
   return HMAT_STATUS_SUCCESS;
 }
 
-hmat_status launch_fp64(hmat_context* h, const Prepared& pr, const JobDesc* d_jobs, cudaStream_t stream) {
-  const int grid = (int)std::min<int64_t>(pr.f_tiles, h->sm_count);
+hmat_status launch_fp64_group(hmat_context* h, const Prepared& pr, int g, const JobDesc* d_jobs,
+                              cudaStream_t stream) {
+  const int grid = (int)std::min<int64_t>(pr.f_tiles[g], h->sm_count);
   ProfScope ps(h, 0, stream);
-  return cuda_status(launch_fp64_bilinear(d_jobs, (int)pr.f.size(), h->d_plans, pr.f_tiles, grid, stream));
+  return cuda_status(launch_fp64_bilinear(d_jobs, (int)pr.f[g].size(), h->d_plans, pr.f_tiles[g], grid, stream));
+}
+
+hmat_status launch_iso_in(hmat_context* h, const Prepared& pr, cudaStream_t stream) {
+  for (const IsoJob& ij : pr.iso) {
+    for (const IsoMapIn* p : {&ij.ina, &ij.inb}) {
+      ProfScope ps(h, 6, stream);
+      cudaError_t e = launch_iso_map_in(*p, stream);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+  }
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status launch_iso_out(hmat_context* h, const Prepared& pr, cudaStream_t stream) {
+  for (const IsoJob& ij : pr.iso) {
+    ProfScope ps(h, 7, stream);
+    cudaError_t e = launch_iso_map_out(ij.out, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return HMAT_STATUS_SUCCESS;
 }
 
 hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
@@ -327,24 +471,28 @@ hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
   std::lock_guard<std::mutex> lock(h->mu);
   h->last_bad = -1;
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
   Prepared pr;
-  hmat_status st = prepare(h, count, descs, mode, tol, ws_bytes, stream, &pr);
+  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  st = launch_iso_in(h, pr, stream);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (pr.has_split) {
-    if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
-    st = run_split(h, pr.sp, h->d_plans, workspace, stream);
+    st = run_split(h, pr.sp, h->d_plans, static_cast<unsigned char*>(workspace) + pr.split_offset, stream);
     if (st != HMAT_STATUS_SUCCESS) return st;
   }
-  if (pr.f_tiles > 0) {
+  for (size_t g = 0; g < pr.f.size(); ++g) {
+    if (pr.f_tiles[g] == 0) continue;
     JobDesc* d_jobs = nullptr;
     int slot = 0;
-    st = upload_jobs(h, pr.f, stream, &d_jobs, &slot);
+    st = upload_jobs(h, pr.f[g], stream, &d_jobs, &slot);
     if (st != HMAT_STATUS_SUCCESS) return st;
-    st = launch_fp64(h, pr, d_jobs, stream);
+    st = launch_fp64_group(h, pr, (int)g, d_jobs, stream);
     if (st != HMAT_STATUS_SUCCESS) return st;
-    return finish_slot(h, slot, stream);
+    st = finish_slot(h, slot, stream);
+    if (st != HMAT_STATUS_SUCCESS) return st;
   }
-  return HMAT_STATUS_SUCCESS;
+  return launch_iso_out(h, pr, stream);
 }
 
 // Grouped call replayed from a CUDA graph keyed by the exact call arguments.
@@ -356,32 +504,40 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
     return run(h, count, descs, mode, tol, workspace, ws_bytes, stream_ptr);
   std::lock_guard<std::mutex> lock(h->mu);
   h->last_bad = -1;
-  // key: descriptors + mode + tol + workspace
-  std::vector<unsigned char> key(sizeof(int32_t) * 2 + sizeof(double) + sizeof(void*) + sizeof(size_t) +
+  // key: descriptors + mode + tol + workspace + algorithm + tile table
+  const size_t tbl = sizeof(h->split.tile_table);
+  std::vector<unsigned char> key(sizeof(int32_t) * 3 + sizeof(double) + sizeof(void*) + sizeof(size_t) + 1 + tbl +
                                  (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc));
   {
     unsigned char* k = key.data();
     std::memcpy(k, &count, 4); k += 4;
     std::memcpy(k, &mode, 4); k += 4;
+    std::memcpy(k, &h->algo, 4); k += 4;
     std::memcpy(k, &tol, 8); k += 8;
     std::memcpy(k, &workspace, sizeof(void*)); k += sizeof(void*);
     std::memcpy(k, &ws_bytes, sizeof(size_t)); k += sizeof(size_t);
+    *k++ = h->split.has_table ? 1 : 0;
+    std::memcpy(k, h->split.tile_table, tbl); k += tbl;
     if (count > 0 && descs) std::memcpy(k, descs, (size_t)count * sizeof(hmat_gemm_desc));
   }
   for (auto& g : h->graphs) {
     if (g.key == key) return cuda_status(cudaGraphLaunch(g.exec, stream));
   }
+  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
   Prepared pr;
-  hmat_status st = prepare(h, count, descs, mode, tol, ws_bytes, stream, &pr);
+  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr);
   if (st != HMAT_STATUS_SUCCESS) return st;
-  if (pr.has_split && (reinterpret_cast<uintptr_t>(workspace) & 255u)) return HMAT_STATUS_MISALIGNED;
   hmat_context::GraphEntry ge;
   ge.key = key;
   cudaError_t e = cudaSuccess;
-  if (pr.f_tiles > 0) {
-    e = cudaMalloc(&ge.d_fp64, pr.f.size() * sizeof(JobDesc));
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(ge.d_fp64, pr.f.data(), pr.f.size() * sizeof(JobDesc), cudaMemcpyHostToDevice, stream);
+  for (size_t g = 0; e == cudaSuccess && g < pr.f.size(); ++g) {
+    JobDesc* d = nullptr;
+    if (!pr.f[g].empty()) {
+      e = cudaMalloc(&d, pr.f[g].size() * sizeof(JobDesc));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d, pr.f[g].data(), pr.f[g].size() * sizeof(JobDesc), cudaMemcpyHostToDevice, stream);
+    }
+    ge.d_fp64.push_back(d);
   }
   if (e == cudaSuccess && pr.has_split) {
     e = cudaMalloc(&ge.d_split, pr.sp.jobs.size() * sizeof(SplitJob));
@@ -399,9 +555,13 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
   cudaGraph_t graph = nullptr;
   e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    if (pr.has_split)
-      st = split_launch(h, pr.sp, ge.d_split, h->d_plans, static_cast<unsigned char*>(workspace), stream);
-    if (st == HMAT_STATUS_SUCCESS && pr.f_tiles > 0) st = launch_fp64(h, pr, ge.d_fp64, stream);
+    st = launch_iso_in(h, pr, stream);
+    if (st == HMAT_STATUS_SUCCESS && pr.has_split)
+      st = split_launch(h, pr.sp, ge.d_split, h->d_plans, static_cast<unsigned char*>(workspace) + pr.split_offset,
+                        stream);
+    for (size_t g = 0; st == HMAT_STATUS_SUCCESS && g < pr.f.size(); ++g)
+      if (pr.f_tiles[g] > 0) st = launch_fp64_group(h, pr, (int)g, ge.d_fp64[g], stream);
+    if (st == HMAT_STATUS_SUCCESS) st = launch_iso_out(h, pr, stream);
     const cudaError_t e2 = cudaStreamEndCapture(stream, &graph);
     if (e == cudaSuccess) e = e2;
   }
@@ -492,18 +652,34 @@ hmat_status hmat_workspace_size(hmat_handle h, int32_t count, const hmat_gemm_de
   if (!bytes || count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
   *bytes = 0;
-  if (mode == HMAT_MODE_FP64) return HMAT_STATUS_SUCCESS;
+  const int algo = h->algo;
+  int64_t iso = 0;
   std::vector<SplitShape> shapes;
   for (int32_t i = 0; i < count; ++i) {
     const hmat_gemm_desc& d = descs[i];
     if (d.m < 0 || d.n < 0 || d.k < 0 || d.flagsA > 0xFFu || d.flagsB > 0xFFu) return HMAT_STATUS_INVALID_VALUE;
     if (d.m == 0 || d.n == 0 || d.k == 0) continue;
+    int64_t m = d.m, n = d.n, k = d.k;
+    unsigned fa = d.flagsA, fb = d.flagsB;
+    if (algo == HMAT_ALGO_ISOMORPH) {
+      iso += iso_bytes(m, n, k);
+      m *= 2; n *= 2; k *= 2;
+      fa = HMAT_COMPLEX; fb = HMAT_COMPLEX;
+    }
+    if (mode == HMAT_MODE_FP64) continue;
     KPlan p;
-    if (!build_plan(d.flagsA, d.flagsB, &p)) return HMAT_STATUS_INTERNAL;
+    if (!build_plan(fa, fb, &p, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
+      return HMAT_STATUS_INTERNAL;
     if (p.np == 0) continue;
-    shapes.push_back({d.m, d.n, d.k, p.np, p.nlf, p.nrf});
+    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf});
   }
-  return split_workspace_bytes(shapes, tol, split_table(h), bytes);
+  size_t split = 0;
+  if (!shapes.empty()) {
+    hmat_status st = split_workspace_bytes(shapes, tol, split_table(h), &split);
+    if (st != HMAT_STATUS_SUCCESS) return st;
+  }
+  *bytes = (size_t)align_up256(iso) + split;
+  return HMAT_STATUS_SUCCESS;
 }
 
 hmat_status hmat_bq_gemm(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
@@ -551,7 +727,7 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (j.m == 0 || j.n == 0) return HMAT_STATUS_SUCCESS;
   int slot = 0;
-  st = plan_slot(h, j.fa, j.fb, stream, &slot);
+  st = plan_slot(h, j.fa, j.fb, kAlgoBilinear, stream, &slot);
   if (st != HMAT_STATUS_SUCCESS) return st;
   j.plan = slot;
   // the fixed scratch serves the split pipeline only: an empty product (k == 0
@@ -580,12 +756,14 @@ size_t hmat_split_noalloc_capacity(void) { return kNoAllocScratchBytes; }
 
 int32_t hmat_last_bad_index(hmat_handle h) { return h ? h->last_bad : -1; }
 
-hmat_status hmat_plan_info(int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int32_t* n_products,
-                           int8_t* U, int8_t* V, double* W, int32_t* strategy) {
+hmat_status hmat_plan_info(int32_t algo, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+                           int32_t* n_products, int8_t* U, int8_t* V, double* W, int32_t* strategy) {
   if (!n_products || opA < 0 || opA > 4 || opB < 0 || opB > 4 || flagsA > 0xFFu || flagsB > 0xFFu)
     return HMAT_STATUS_INVALID_VALUE;
+  if (algo != HMAT_ALGO_BILINEAR && algo != HMAT_ALGO_STANDARD) return HMAT_STATUS_INVALID_VALUE;
   KPlan p;
-  if (!build_plan(flagsA, flagsB, &p)) return HMAT_STATUS_INTERNAL;
+  if (!build_plan(flagsA, flagsB, &p, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
+    return HMAT_STATUS_INTERNAL;
   *n_products = p.np;
   if (strategy) *strategy = p.strategy;
   for (int q = 0; q < p.np; ++q) {
@@ -626,6 +804,15 @@ hmat_status hmat_get_device_error(hmat_handle h, uint32_t* code) {
     e = cudaMemcpyToSymbol(g_hmat_device_error, &zero, sizeof(uint32_t));
   }
   return cuda_status(e);
+}
+
+hmat_status hmat_set_algorithm(hmat_handle h, int32_t algo) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (algo != HMAT_ALGO_BILINEAR && algo != HMAT_ALGO_STANDARD && algo != HMAT_ALGO_ISOMORPH)
+    return HMAT_STATUS_INVALID_VALUE;
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->algo = algo;
+  return HMAT_STATUS_SUCCESS;
 }
 
 hmat_status hmat_set_tile_table(hmat_handle h, const int8_t* table) {

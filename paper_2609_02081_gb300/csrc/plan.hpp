@@ -25,7 +25,8 @@
 
 namespace hmat {
 
-constexpr int kMaxProducts = 24;
+constexpr int kMaxProducts = 64;   // plan capacity (the component-wise algorithm needs 64)
+constexpr int kMaxFactors = 24;    // factor slots per side (8 groups x Re, Im, Re+Im)
 
 // Real-valued linear combination of the 8 components of op(X): sign per component.
 struct Comb8 {
@@ -48,10 +49,10 @@ struct Comb8 {
 // and Re+Im (the Gauss factor).  Product p multiplies left slot pl[p] by right
 // slot pr[p]; its result enters output component e with weight w4[e][p] / 4.
 struct KPlan {
-  int32_t np = 0;            // real products (<= 24)
-  int32_t strategy = 0;      // 0 bilinear (Eq. bilinearH + Gauss), 1 component-wise + Gauss
+  int32_t np = 0;            // real products (<= kMaxProducts)
+  int32_t strategy = 0;      // 0 bilinear (Eq. bilinearH + Gauss), 1 component-wise + Gauss, 2 standard
   int32_t nlg = 0, nrg = 0;  // groups per side (<= 8)
-  int32_t nlf = 0, nrf = 0;  // factor slots per side (<= 24)
+  int32_t nlf = 0, nrf = 0;  // factor slots per side (<= kMaxFactors)
   int8_t lre[8][4], lim[8][4], lslot[8][3];  // slot of Re, Im, Re+Im (-1: not needed)
   int8_t rre[8][4], rim[8][4], rslot[8][3];
   int8_t pl[kMaxProducts], pr[kMaxProducts];
@@ -275,19 +276,79 @@ inline bool layout_side(const std::vector<Factor>& uniq, int8_t re[8][4], int8_t
 
 }  // namespace detail
 
+namespace detail {
+// The component-wise ("standard") algorithm: one real product per pair of
+// present components (A_c, B_d) that meets in some output component — 64 for
+// full biquaternions, 16 for real quaternions (Sec. III B).  Signs and target
+// components come from the same expansion of Eq. bilinearH.
+inline std::vector<Product> standard_products(unsigned fa, unsigned fb) {
+  CComb X[8], Y[8];
+  int w4[8][4];
+  bilinear_tables(X, Y, w4);
+  std::vector<Product> ps;
+  for (int f = 0; f < 4; ++f)
+    for (int g = 0; g < 4; ++g) {
+      int h[4];
+      bool any = false;
+      for (int e = 0; e < 4; ++e) {
+        int s = 0;
+        for (int r = 0; r < 8; ++r) s += w4[r][e] * X[r].x[f] * Y[r].x[g];
+        h[e] = s;                      // 4 * (+-1 or 0)
+        any |= (s != 0);
+      }
+      if (!any) continue;
+      CComb uf{}, ug{};
+      uf.x[f] = 1;
+      ug.x[g] = 1;
+      // a_f b_g = (Af Bg - Af' Bg') + i (Af Bg' + Af' Bg)   (' = imaginary part)
+      const int parts[4][2] = {{PART_RE, PART_RE}, {PART_IM, PART_IM}, {PART_RE, PART_IM}, {PART_IM, PART_RE}};
+      const int cre[4] = {+1, -1, 0, 0}, cim[4] = {0, 0, +1, +1};
+      for (int t = 0; t < 4; ++t) {
+        const int la = parts[t][0], rb = parts[t][1];
+        const bool lp = la == PART_RE ? ((fa >> f) & 1u) : ((fa >> (f + 4)) & 1u);
+        const bool rp = rb == PART_RE ? ((fb >> g) & 1u) : ((fb >> (g + 4)) & 1u);
+        if (!lp || !rp) continue;
+        Product p;
+        p.l = make_factor(uf, fa, la);
+        p.r = make_factor(ug, fb, rb);
+        for (int e = 0; e < 4; ++e) {
+          p.w4[e] = h[e] * cre[t];
+          p.w4[e + 4] = h[e] * cim[t];
+        }
+        ps.push_back(p);
+      }
+    }
+  return merge(ps);
+}
+}  // namespace detail
+
+// Algorithms: 0 = the paper's bilinear scheme (or, when cheaper for mixed
+// subalgebras, component-wise terms with Gauss's rule); 1 = the component-wise
+// ("standard") algorithm with four real products per complex term.
+enum { kAlgoBilinear = 0, kAlgoStandard = 1 };
+
 // Build the kernel plan for component activity flags fa (of A) and fb (of B).
-inline bool build_plan(unsigned fa, unsigned fb, KPlan* out) {
+inline bool build_plan(unsigned fa, unsigned fb, KPlan* out, int algo = kAlgoBilinear) {
   using namespace detail;
   fa &= 0xFFu;
   fb &= 0xFFu;
-  std::vector<Product> bl = bilinear_products(fa, fb);
-  std::vector<Product> dr = direct_products(fa, fb);
-  const bool use_direct = dr.size() < bl.size();
-  const std::vector<Product>& ps = use_direct ? dr : bl;
+  std::vector<Product> chosen;
+  int strategy;
+  if (algo == kAlgoStandard) {
+    chosen = standard_products(fa, fb);
+    strategy = 2;
+  } else {
+    std::vector<Product> bl = bilinear_products(fa, fb);
+    std::vector<Product> dr = direct_products(fa, fb);
+    const bool use_direct = dr.size() < bl.size();
+    chosen = use_direct ? dr : bl;
+    strategy = use_direct ? 1 : 0;
+  }
+  const std::vector<Product>& ps = chosen;
   if (ps.size() > (size_t)kMaxProducts) return false;
   KPlan p;
   std::memset(&p, 0, sizeof(p));
-  p.strategy = use_direct ? 1 : 0;
+  p.strategy = strategy;
   p.np = (int32_t)ps.size();
   std::vector<Factor> lu, ru;
   auto index_of = [](std::vector<Factor>& v, const Factor& f) {

@@ -139,3 +139,28 @@ def test_tile_table_codes_are_validated():
     # host-only: the setter rejects codes outside 0..3 before touching the device
     L = hm.lib()
     assert L.hmat_set_tile_table(None, None) == 7     # no handle
+
+
+@pytest.mark.parametrize("fa,fb", list(itertools.product(FLAGS, FLAGS)))
+def test_standard_plan_reproduces_structure_tensor(fa, fb):
+    """The component-wise (HMAT-standard) plan: same structure tensor, one real product per component pair."""
+    for opA, opB in [("N", "N"), ("H", "T")]:
+        P, U, V, W, strategy = hm.plan_info(opA, opB, fa, fb, algo="standard")
+        assert strategy == 2
+        T = structure_tensor(opA, opB)
+        got = np.einsum("ep,pc,pd->ecd", W, U.astype(float), V.astype(float))
+        mask = np.zeros((8, 8, 8), bool)
+        for c in range(8):
+            for d in range(8):
+                mask[:, c, d] = bool((fa >> c) & 1) and bool((fb >> d) & 1)
+        np.testing.assert_array_equal(got[mask], T[mask])
+        assert np.all(np.count_nonzero(U, axis=1) == 1) and np.all(np.count_nonzero(V, axis=1) == 1)
+
+
+def test_standard_counts():
+    """Sec. III B: 64 real products for full biquaternions, 16 for real quaternions."""
+    assert hm.plan_info("N", "N", bi.BQ, bi.BQ, algo="standard")[0] == 64
+    assert hm.plan_info("N", "N", bi.TRS, bi.TRS, algo="standard")[0] == 16
+    assert hm.plan_info("N", "N", bi.TRA, bi.TRA, algo="standard")[0] == 16
+    assert hm.plan_info("N", "N", bi.REAL, bi.REAL, algo="standard")[0] == 1
+    assert hm.plan_info("N", "N", bi.COMPLEX, bi.COMPLEX, algo="standard")[0] == 4

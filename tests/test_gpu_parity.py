@@ -258,3 +258,47 @@ def test_bounded_wait_gives_up_with_an_error_status(handle):
     A = bi.small_int(120, 20, 30)
     B = bi.small_int(121, 30, 10)
     np.testing.assert_array_equal(run(handle, A, B, mode="split"), oracle.bq_gemm(A.numpy(), B.numpy()))
+
+
+@pytest.mark.parametrize("algo", ["standard", "isomorph"])
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("opA,opB,fa,fb", [("N", "N", bi.BQ, bi.BQ), ("H", "T", bi.BQ, bi.BQ),
+                                           ("C", "QC", bi.TRS, bi.TRA), ("T", "N", bi.COMPLEX, bi.BQ)])
+def test_comparison_algorithms_exact(handle, algo, mode, opA, opB, fa, fb):
+    """HMAT-standard and CMAT (complex isomorph) routes reproduce the oracle bit for bit."""
+    m, n, k = 45, 70, 130
+    A = bi.small_int(130, *stored(opA, m, k), flags=fa)
+    B = bi.small_int(131, *stored(opB, k, n), flags=fb)
+    C0 = bi.small_int(132, m, n)
+    want = oracle.bq_gemm(A.numpy(), B.numpy(), opA, opB, alpha=1 - 2j, beta=3 + 1j, C=C0.numpy())
+    handle.set_algorithm(algo)
+    try:
+        got = run(handle, A, B, opA, opB, fa, fb, alpha=1 - 2j, beta=3 + 1j, C0=C0, mode=mode)
+    finally:
+        handle.set_algorithm("bilinear")
+    np.testing.assert_array_equal(got, want)
+
+
+@pytest.mark.parametrize("algo", ["standard", "isomorph"])
+@pytest.mark.parametrize("mode", MODES)
+def test_comparison_algorithms_random_and_grouped(handle, algo, mode):
+    dev = torch.device("cuda")
+    shapes = [(64, 96, 200), (130, 40, 33)]
+    mats, descs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A = bi.uniform(140 + i, m, k, device=dev)
+        B = bi.uniform(150 + i, k, n, device=dev)
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        mats.append((A, B, C))
+        descs.append(hm.make_desc(A, B, C))
+    handle.set_algorithm(algo)
+    try:
+        for use_graph in (False, True):
+            hm.hmat_bq_gemm_grouped(handle, descs, mode=mode, tol=TOL, use_graph=use_graph,
+                                    stream=torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            for A, B, C in mats:
+                want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy())
+                assert rel(C.cpu().numpy(), want) <= (1e-14 if mode == "fp64" else TOL)
+    finally:
+        handle.set_algorithm("bilinear")
