@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 METRIC = "biquaternion GEMM TFLOP/s (64-GEMM-equiv.) vs plain FP64 at n=8192, err≤1e-12"
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
@@ -46,17 +46,33 @@ def parse():
                     help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
+    ap.add_argument("--flags", choices=["BQxBQ", "TRSxTRA", "TRSxTRS", "CxBQ"], default="BQxBQ",
+                    help="subalgebra flags of A x B (single workload)")
+    ap.add_argument("--opA", choices=["N", "T", "C", "H", "QC"], default="N", help="op(A) (single workload)")
+    ap.add_argument("--no-row-scale", action="store_true",
+                    help="banded Fock-like inputs without the per-row scales 10^U(-6,0)")
     ap.add_argument("--algo", choices=["bilinear", "standard", "isomorph"], default="bilinear",
                     help="product algorithm: the bilinear scheme, component-wise (HMAT-standard) "
                          "or the complex isomorph (CMAT)")
-    return ap.parse_args()
+    return ap.parse_args(argv)
+
+
+FLAG_PAIRS = {"BQxBQ": (0xFF, 0xFF), "TRSxTRA": (0x0F, 0xF0), "TRSxTRS": (0x0F, 0x0F), "CxBQ": (0x11, 0xFF)}
+FLAG_WORDS = {"BQxBQ": "full biquaternions x full biquaternions",
+              "TRSxTRA": "real quaternions (TRS) x i*real quaternions (TRA)",
+              "TRSxTRS": "real quaternions x real quaternions", "CxBQ": "complex x full biquaternions"}
 
 
 def workload_config(args):
-    return {"workload": f"bq_gemm m=n=k={args.n} Fock-like N(0,1)*exp(-|i-j|/200) with per-row scales "
-                        f"10^U(-6,0), full biquaternions x full biquaternions, op N,N, C=AB",
+    flags = getattr(args, "flags", "BQxBQ")
+    opA = getattr(args, "opA", "N")
+    scaled = not getattr(args, "no_row_scale", False)
+    scale_txt = " with per-row scales 10^U(-6,0)" if scaled else ""
+    return {"workload": f"bq_gemm m=n=k={args.n} Fock-like N(0,1)*exp(-|i-j|/200){scale_txt}, "
+                        f"{FLAG_WORDS[flags]}, op {opA},N, C=op(A)B",
             "m": args.n, "n": args.n, "k": args.n, "mode": args.mode, "tol": args.tol,
-            "flags": "BQxBQ", "seed": args.seed, "algo": getattr(args, "algo", "bilinear"),
+            "flags": flags, "opA": opA, "row_scale": scaled, "seed": args.seed,
+            "algo": getattr(args, "algo", "bilinear"),
             "l2": "inputs larger than L2 (8 x n^2 x 8 B per operand), no flush"}
 
 
@@ -169,13 +185,16 @@ def measured_peaks():
 
 
 # ----------------------------------------------------------------------------- oracle sample
-def oracle_rows(A_cpu, B_cpu, rows):
-    """Selected output rows of A B from the CPU oracle; returns (rows x, seconds, threads)."""
+def oracle_rows(A_cpu, B_cpu, rows, opA="N"):
+    """Selected output rows of op(A) B from the CPU oracle; returns (rows x, seconds, threads)."""
     import numpy as np
     import oracle
-    Asub = np.ascontiguousarray(A_cpu[:, rows, :])
+    if opA in ("T", "H"):                     # rows of op(A) are columns of the stored A
+        Asub = np.ascontiguousarray(A_cpu[:, :, rows])
+    else:
+        Asub = np.ascontiguousarray(A_cpu[:, rows, :])
     t0 = time.perf_counter()
-    out = oracle.bq_gemm(Asub, B_cpu, "N", "N")
+    out = oracle.bq_gemm(Asub, B_cpu, opA, "N")
     return out, time.perf_counter() - t0, oracle.max_threads()
 
 
@@ -188,15 +207,17 @@ def reference_arm(args, rank, world):
     import bq_inputs as bi
     import oracle
     n = args.n
-    A = bi.fock_like(args.seed, n, n, row_scale=True).numpy()
-    B = bi.fock_like(args.seed + 1, n, n, row_scale=True).numpy()
+    fa, fb = FLAG_PAIRS[args.flags]
+    scaled = not args.no_row_scale
+    A = bi.fock_like(args.seed, n, n, flags=fa, row_scale=scaled).numpy()
+    B = bi.fock_like(args.seed + 1, n, n, flags=fb, row_scale=scaled).numpy()
     threads = oracle.max_threads()
     rows_per_step = max(1, min(threads, 16))
     times = []
     rng = np.random.default_rng(args.seed)
     for step in range(args.warmup + args.steps):
         rows = np.sort(rng.choice(n, size=rows_per_step, replace=False))
-        _, dt, _ = oracle_rows(A, B, rows)
+        _, dt, _ = oracle_rows(A, B, rows, args.opA)
         if step >= args.warmup:
             times.append(dt)
     t = statistics.mean(times)
@@ -223,18 +244,20 @@ def ours(args, rank, world, local):
     dev = torch.device("cuda", local if torch.cuda.device_count() > local else 0)
     torch.cuda.set_device(dev)
     n = args.n
-    A = bi.fock_like(args.seed, n, n, row_scale=True, device=dev)
-    B = bi.fock_like(args.seed + 1, n, n, row_scale=True, device=dev)
+    fa, fb = FLAG_PAIRS[args.flags]
+    scaled = not args.no_row_scale
+    A = bi.fock_like(args.seed, n, n, flags=fa, row_scale=scaled, device=dev)
+    B = bi.fock_like(args.seed + 1, n, n, flags=fb, row_scale=scaled, device=dev)
     C = torch.empty((8, n, n), dtype=torch.float64, device=dev)
     h = hm.Handle()
     h.set_algorithm(args.algo)
-    d = hm.make_desc(A, B, C)
+    d = hm.make_desc(A, B, C, args.opA, "N", fa, fb)
     ws_bytes = hm.hmat_workspace_size(h, [d], args.mode, args.tol)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(mode=args.mode):
-        hm.hmat_bq_gemm(h, A, B, C, mode=mode, tol=args.tol, workspace=ws, stream=stream)
+        hm.hmat_bq_gemm(h, A, B, C, args.opA, "N", fa, fb, mode=mode, tol=args.tol, workspace=ws, stream=stream)
 
     for _ in range(args.warmup):
         step()
@@ -263,12 +286,13 @@ def ours(args, rank, world, local):
 
     # accuracy on sampled rows (rank 0)
     info = {}
+    naive = bin(fa).count("1") * bin(fb).count("1")      # component-wise real products
     # the real products one step executes: plan products x their size relative to n^3
     if args.algo == "isomorph":
         P = hm.plan_info("N", "N", hm.HMAT_COMPLEX, hm.HMAT_COMPLEX)[0]
         size, kin = 8, 2 * n          # one complex product of 2n x 2n x 2n
     else:
-        P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ, algo=args.algo)[0]
+        P = hm.plan_info(args.opA, "N", fa, fb, algo=args.algo)[0]
         size, kin = 1, n
     mods, bits = hm.split_info(kin, args.tol)
     if rank == 0:
@@ -276,7 +300,7 @@ def ours(args, rank, world, local):
         rows = np.sort(rng.choice(n, size=args.sample_rows, replace=False))
         A_cpu = A.cpu().numpy()
         B_cpu = B.cpu().numpy()
-        want, t_or, threads = oracle_rows(A_cpu, B_cpu, rows)
+        want, t_or, threads = oracle_rows(A_cpu, B_cpu, rows, args.opA)
         got = C[:, torch.as_tensor(rows, device=dev), :].cpu().numpy()
         err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
         info["rel_fro_err_sampled"] = err
@@ -362,7 +386,9 @@ def ours(args, rank, world, local):
                 "rel_fro_err_sampled": info.get("rel_fro_err_sampled"),
                 "err_ok": (info.get("rel_fro_err_sampled") is not None and info["rel_fro_err_sampled"] <= 1e-12),
                 "fp64_plain": info.get("fp64_plain"), "stages": stages,
-                "executed_tflops": value * size * (len(mods) * P if args.mode == "split" else P) / 64.0}
+                "executed_tflops": value * size * (len(mods) * P if args.mode == "split" else P) / 64.0,
+                "naive_equiv_tflops": value * naive / 64.0,
+                "naive_equiv_note": f"counted as {naive} component-wise real GEMMs of n^3"}
         print(json.dumps(line), flush=True)
     barrier(world)
     h.close()

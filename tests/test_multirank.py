@@ -11,7 +11,6 @@ import multiprocessing as mp
 import os
 import socket
 import sys
-import types
 from contextlib import redirect_stdout
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -30,9 +29,8 @@ def _worker(rank, world, port, q):
                       MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), OMP_NUM_THREADS="1")
     sys.path.insert(0, ROOT)
     import bench
-    args = types.SimpleNamespace(gpus=world, steps=1, warmup=1, impl="reference", n=24, mode="split", tol=1e-12,
-                                 sample_rows=2, no_fp64_compare=True, e2e_steps=1, seed=103, workload="single",
-                                 graph=False, tile_table=None)
+    args = bench.parse(["--gpus", str(world), "--steps", "1", "--warmup", "1", "--impl", "reference", "--n", "24",
+                        "--sample-rows", "2", "--no-fp64-compare", "--e2e-steps", "1"])
     r, w, _ = bench.dist_init(args)
     assert (r, w) == (rank, world)
     worst = bench.max_over_ranks(10.0 * (rank + 1), w)
