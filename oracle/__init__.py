@@ -15,6 +15,10 @@ Contents
 * ``isomorph.py``: the independent cross-check on the isomorphic complex
   2m x 2n representation (Sec. II A Eq. TRG-in-C, Sec. III M+/M- blocks and
   Eq. mapping-formulas), multiplied with numpy.
+* ``ops.py``: the element-wise operations of Sec. III (complex scaling,
+  addition, trace), the Hermiticity deviation, and the Hadamard block
+  reduction of Sec. III C (Eq. hadamard_general_transform), in numpy; pinned
+  in tests/test_oracle_ops_pins.py.
 
 Parity pins: every function here is pinned in tests/test_oracle_pins.py to
 values the paper and the mathematics fix (quaternion relations, the Pauli
