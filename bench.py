@@ -42,8 +42,9 @@ def parse(argv=None):
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=103)
-    ap.add_argument("--workload", choices=["single", "grouped"], default="single",
-                    help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]")
+    ap.add_argument("--workload", choices=["single", "grouped", "ops"], default="single",
+                    help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]; "
+                         "ops: the element-wise and mapping operations at n x n")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
     ap.add_argument("--flags", choices=["BQxBQ", "TRSxTRA", "TRSxTRS", "CxBQ"], default="BQxBQ",
@@ -469,11 +470,82 @@ def grouped(args, rank, world, local):
     h.close()
 
 
+def ops_arm(args, rank, world, local):
+    """The HBM-bound element-wise / mapping kernels on n x n full biquaternions:
+    achieved GB/s (algorithmic bytes / CUDA-event time) against the measured copy bandwidth."""
+    import torch
+    import bq_inputs as bi
+    import paper_2609_02081_gb300 as hm
+
+    dev = torch.device("cuda", local if torch.cuda.device_count() > local else 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    A = bi.fock_like(args.seed, n, n, device=dev)
+    B = bi.fock_like(args.seed + 1, n, n, device=dev)
+    Hj = bi.apply_flags(A.clone(), 0xCC)
+    C = torch.empty_like(A)
+    Z = torch.empty((2 * n, 2 * n), dtype=torch.complex128, device=dev)
+    Zh = torch.empty((n, n), dtype=torch.complex128, device=dev)
+    res = torch.empty(2, dtype=torch.float64, device=dev)
+    h = hm.Handle()
+    stream = torch.cuda.current_stream(dev)
+    e = n * n
+    # name -> (call, algorithmic bytes per launch)
+    cases = {
+        "add": (lambda: hm.hmat_bq_add(h, A, B, C, 1.0, 1.0, stream=stream), 3 * 64 * e),
+        "add_complex_scalars": (lambda: hm.hmat_bq_add(h, A, B, C, 1 - 1j, 0.5, stream=stream), 3 * 64 * e),
+        "add_opH": (lambda: hm.hmat_bq_add(h, A, B, C, 1.0, 1.0, "H", "N", stream=stream), 3 * 64 * e),
+        "scale_real": (lambda: hm.hmat_bq_scale(h, A, C, 2.5, stream=stream), 2 * 64 * e),
+        "scale_complex": (lambda: hm.hmat_bq_scale(h, A, C, 2 - 1j, stream=stream), 2 * 64 * e),
+        "to_complex": (lambda: hm.hmat_bq_to_complex(h, A, Z, stream=stream), 2 * 64 * e),
+        "to_complex_opT": (lambda: hm.hmat_bq_to_complex(h, A, Z, op="T", stream=stream), 2 * 64 * e),
+        "from_complex": (lambda: hm.hmat_complex_to_bq(h, Z, C, stream=stream), 2 * 64 * e),
+        "hermiticity": (lambda: hm.hmat_bq_hermiticity(h, A, out=res, stream=stream), 64 * e),
+        "hadamard": (lambda: hm.hmat_bq_hadamard_block(h, Hj, 1j, 0xCC, Z=Zh, stream=stream), (32 + 16) * e),
+    }
+    peaks, src = measured_peaks()
+    peak = peaks["hbm_gbs"]
+    out = {}
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    for name, (call, nbytes) in cases.items():
+        for _ in range(args.warmup):
+            call()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            call()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        out[name] = {"ms": ms, "GB_per_s": gbs, "frac": gbs / peak, "bytes": nbytes}
+    clk = clocks.stop()
+    if rank == 0:
+        top = out["add"]
+        line = {"metric": "element-wise biquaternion ops, achieved HBM GB/s", "value": top["GB_per_s"],
+                "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": top["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"n={n} full biquaternions, Fock-like N(0,1)*exp(-|i-j|/200) (seed "
+                                       f"{args.seed}); value = the paper's sum C = A + B",
+                           "l2": "operands 8 x n^2 x 8 B, larger than L2, no flush"},
+                "roofline": {"bound": "hbm", "achieved": top["GB_per_s"], "peak": peak, "unit": "GB/s",
+                             "frac": top["GB_per_s"] / peak, "traffic": None, "kernel": "axpby_kernel",
+                             "peak_source": f"hbm copy ({src})"},
+                "ops": out, "clocks": clk, "gpu_launches": args.steps * len(cases)}
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     try:
-        if args.workload == "grouped" and args.impl == "ours":
+        if args.workload == "ops" and args.impl == "ours":
+            ops_arm(args, rank, world, local)
+        elif args.workload == "grouped" and args.impl == "ours":
             grouped(args, rank, world, local)
         elif args.impl == "reference":
             reference_arm(args, rank, world)

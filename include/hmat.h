@@ -276,13 +276,94 @@ hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
  * Errors: NOT_INITIALIZED, INVALID_VALUE, CUDA_ERROR. */
 hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Element-wise operations (Sec. III: complex scaling, addition, trace) and the
+ * data movement of the diagonalisation path (Sec. III complex image and
+ * Eq. mapping-formulas; Sec. III C Hadamard transformation).  All are
+ * HBM-bound single-kernel launches on `stream`; none needs workspace.
+ * Operands follow the conventions of hmat_bq_gemm: op(X) is m x n, the stored
+ * X is m x n (n x m when op transposes), component c at X + c * strideX, row
+ * stride ldx; components whose flag bit is clear are read as zero and never
+ * touched.  Outputs are written for all eight components.  Result pointers
+ * (`result`, `offdiag`) are device memory.  Errors: NOT_INITIALIZED,
+ * INVALID_VALUE (bad op / flags / sizes / leading dimensions, null pointers,
+ * another device current), MISALIGNED (doubles not 8-byte aligned, complex
+ * buffers not 16-byte aligned), UNSUPPORTED (more than 2^31 tiles of 32 x 32),
+ * CUDA_ERROR.
+ * ------------------------------------------------------------------------- */
+
+/* C <- alpha op(A) + beta op(B) for complex alpha, beta: the addition formula
+ * of Sec. III applied to operands scaled by the alpha q formula of Sec. III
+ * (alpha = beta = 1 is the paper's plain sum).  B may be NULL (or flagsB 0):
+ * C <- alpha op(A).  C may be A or B when that operand's op does not
+ * transpose (in place); C == A with a transposing opA is INVALID_VALUE, and
+ * other overlaps are undefined.  Every entry is the correctly rounded result
+ * of the formula's steps in order: (alpha_R a_e - alpha_I a_{e+4}) +
+ * (beta_R b_e - beta_I b_{e+4}) for component e <= 4, and likewise for the
+ * imaginary components. */
+hmat_status hmat_bq_add(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+                        int64_t m, int64_t n,
+                        double alpha_re, double alpha_im, const double *A, int64_t lda, int64_t strideA,
+                        double beta_re, double beta_im, const double *B, int64_t ldb, int64_t strideB,
+                        double *C, int64_t ldc, int64_t strideC, void *stream);
+
+/* Y <- alpha op(X) (Sec. III, the alpha q formula); hmat_bq_add without B. */
+hmat_status hmat_bq_scale(hmat_handle handle, int32_t op, uint32_t flags, int64_t m, int64_t n,
+                          double alpha_re, double alpha_im, const double *X, int64_t ldx, int64_t strideX,
+                          double *Y, int64_t ldy, int64_t strideY, void *stream);
+
+/* result[0] + i result[1] <- Tr[op(X)] = 2 (Tr M1 + i Tr M5) for n x n X
+ * (Sec. III trace formula).  One block sums the diagonal in a fixed order, so
+ * repeated calls give identical bits. */
+hmat_status hmat_bq_trace(hmat_handle handle, int32_t op, uint32_t flags, int64_t n, const double *X,
+                          int64_t ldx, int64_t strideX, double *result, void *stream);
+
+/* Z <- the complex 2m x 2n image of op(X): [[E+G, F+H], [-F*+H*, E*-G*]]
+ * with E = M1 + i M2, F = M3 + i M4, G = -M6 + i M5, H = -M8 + i M7 (Sec. III,
+ * M+ and M- blocks).  Z is interleaved complex (re, im) doubles, row-major,
+ * ldz >= 2n complex elements per row, 16-byte aligned; the input of a
+ * complex Hermitian eigensolver when X is Hermitian. */
+hmat_status hmat_bq_to_complex(hmat_handle handle, int32_t op, uint32_t flags, int64_t m, int64_t n,
+                               const double *X, int64_t ldx, int64_t strideX, double *Z, int64_t ldz,
+                               void *stream);
+
+/* Y <- the m x n biquaternion of a 2m x 2n complex matrix [[A, B], [C, D]]
+ * (interleaved, ldz >= 2n): E = (A + D*)/2, F = (B - C*)/2, G = (A - D*)/2,
+ * H = (B + C*)/2 (Eq. mapping-formulas), stored as [E_R, E_I, F_R, F_I, G_I,
+ * -G_R, H_I, -H_R].  For a Z that is not an image, Y is the biquaternion whose
+ * image is the nearest one (the M+ / M- parts of Z). */
+hmat_status hmat_complex_to_bq(hmat_handle handle, int64_t m, int64_t n, const double *Z, int64_t ldz,
+                               double *Y, int64_t ldy, int64_t strideY, void *stream);
+
+/* *result <- max over components and entries of |X - X^dagger| (the
+ * Hermitian-conjugation signs of Sec. III); 0 exactly when the complex image
+ * is Hermitian, NaN if any compared entry is NaN.  n x n X. */
+hmat_status hmat_bq_hermiticity(hmat_handle handle, uint32_t flags, int64_t n, const double *X, int64_t ldx,
+                                int64_t strideX, double *result, void *stream);
+
+/* Hadamard block reduction (Sec. III C).  X (n x n) must have E and G absent
+ * (flags & 0x33 == 0; otherwise UNSUPPORTED), so its image is block
+ * anti-diagonal [[0, A], [B, 0]] with A = F + H, B = -F* + H*.  For a unit
+ * alpha (|alpha|^2 = 1 within 1e-12, else INVALID_VALUE):
+ *   Z (n x n interleaved complex) <- (alpha A + alpha* B) / 2, the upper-left
+ *     block of U_alpha^dagger M U_alpha (Eq. hadamard_general_transform);
+ *   *offdiag (device double, may be NULL) <- max |alpha A - alpha* B| / 2,
+ *     the largest entry of its lower-left block.
+ * offdiag = 0 means M is unitarily equivalent to diag(Z, -Z): pure j
+ * (F_R + i H_I) with alpha = +-i, pure k (F_I - i H_R) with alpha = +-1
+ * (Eq. reduced-hadamard-pure). */
+hmat_status hmat_bq_hadamard_block(hmat_handle handle, uint32_t flags, int64_t n, double alpha_re,
+                                   double alpha_im, const double *X, int64_t ldx, int64_t strideX, double *Z,
+                                   int64_t ldz, double *offdiag, void *stream);
+
 /* Kernel profiling: when enabled, every library kernel launch on the handle
  * is bracketed by CUDA events on its launch stream; hmat_get_profile returns,
  * per kernel id, the number of launches and the summed event time (ms) since
  * the last reset (it synchronises on the recorded events).  Kernel ids:
  * 0 fp64 bilinear, 1 split exponents, 2 split encode, 3 split residue GEMM,
  * 4 split CRT/recombine, 5 beta-scale, 6 isomorph map-in, 7 isomorph
- * map-out. */
+ * map-out, 8 add / scale, 9 to-complex, 10 from-complex, 11 trace,
+ * 12 Hermiticity, 13 Hadamard block. */
 hmat_status hmat_set_profiling(hmat_handle handle, int32_t enable);
 hmat_status hmat_get_profile(hmat_handle handle, int32_t kernel_id,
                              int64_t *launches, double *total_ms);

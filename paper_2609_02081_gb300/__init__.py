@@ -28,7 +28,8 @@ HMAT_ALGO_BILINEAR, HMAT_ALGO_STANDARD, HMAT_ALGO_ISOMORPH = 0, 1, 2
 ALGOS = {"bilinear": HMAT_ALGO_BILINEAR, "standard": HMAT_ALGO_STANDARD, "isomorph": HMAT_ALGO_ISOMORPH}
 MODES = {"fp64": HMAT_MODE_FP64, "split": HMAT_MODE_SPLIT}
 KERNEL_IDS = {"fp64_bilinear": 0, "split_exponents": 1, "split_encode": 2, "split_residue_gemm": 3,
-              "split_crt": 4, "beta_scale": 5, "iso_map_in": 6, "iso_map_out": 7}
+              "split_crt": 4, "beta_scale": 5, "iso_map_in": 6, "iso_map_out": 7, "add": 8, "to_complex": 9,
+              "from_complex": 10, "trace": 11, "hermiticity": 12, "hadamard": 13}
 STATUS = {0: "SUCCESS", 1: "INVALID_VALUE", 2: "UNSUPPORTED", 3: "MISALIGNED", 4: "WORKSPACE_TOO_SMALL",
           5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "NOT_INITIALIZED", 8: "TOLERANCE_UNREACHABLE", 9: "INTERNAL"}
 
@@ -81,6 +82,16 @@ SIGNATURES = {
     "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
     "hmat_get_profile": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "hmat_reset_profile": (ctypes.c_int, [_ptr]),
+    "hmat_bq_add": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
+                                   _dbl, _dbl, _ptr, _i64, _i64, _ptr, _i64, _i64, _ptr]),
+    "hmat_bq_scale": (ctypes.c_int, [_ptr, _i32, _u32, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64, _ptr, _i64, _i64,
+                                     _ptr]),
+    "hmat_bq_trace": (ctypes.c_int, [_ptr, _i32, _u32, _i64, _ptr, _i64, _i64, _ptr, _ptr]),
+    "hmat_bq_to_complex": (ctypes.c_int, [_ptr, _i32, _u32, _i64, _i64, _ptr, _i64, _i64, _ptr, _i64, _ptr]),
+    "hmat_complex_to_bq": (ctypes.c_int, [_ptr, _i64, _i64, _ptr, _i64, _ptr, _i64, _i64, _ptr]),
+    "hmat_bq_hermiticity": (ctypes.c_int, [_ptr, _u32, _i64, _ptr, _i64, _i64, _ptr, _ptr]),
+    "hmat_bq_hadamard_block": (ctypes.c_int, [_ptr, _u32, _i64, _dbl, _dbl, _ptr, _i64, _i64, _ptr, _i64, _ptr,
+                                              _ptr]),
 }
 
 _lock = threading.Lock()
@@ -345,7 +356,121 @@ def bq_gemm_host(handle: Handle, A_host, B_host, C_host, opA="N", opB="N", flags
     return C_host, h2d, C_host.numel() * 8
 
 
+# ----------------------------------------------------------------------------- element-wise and mapping operations
+def _op_shape(X, op):
+    """(rows, cols) of op(X) for a stored 8 x r x c tensor."""
+    return (X.shape[2], X.shape[1]) if _op(op) in (HMAT_OP_T, HMAT_OP_H) else (X.shape[1], X.shape[2])
+
+
+def _cplx_args(Z, rows, cols, name):
+    """(ptr, ld in complex elements) of a rows x cols complex128 CUDA tensor (row-major)."""
+    import torch
+    if not isinstance(Z, torch.Tensor) or Z.dtype != torch.complex128 or not Z.is_cuda:
+        raise TypeError(f"{name} must be a complex128 CUDA tensor")
+    if Z.dim() != 2 or Z.shape[0] != rows or Z.shape[1] != cols:
+        raise ValueError(f"{name} must have shape ({rows}, {cols}), got {tuple(Z.shape)}")
+    if cols > 1 and Z.stride(1) != 1:
+        raise ValueError(f"{name} must be row-major")
+    return Z.data_ptr(), max(Z.stride(0), cols, 1)
+
+
+def hmat_bq_add(handle: Handle, A, B, C, alpha=1.0, beta=1.0, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ,
+                stream=None):
+    """C <- alpha op(A) + beta op(B) (hmat_bq_add); B may be None.  Returns C."""
+    m, n = _op_shape(A, opA)
+    ta, tb = _op(opA) in (HMAT_OP_T, HMAT_OP_H), _op(opB) in (HMAT_OP_T, HMAT_OP_H)
+    a_ptr, lda, sa = _mat_args(A, *((n, m) if ta else (m, n)), "A")
+    b_ptr, ldb, sb = _mat_args(B, *((n, m) if tb else (m, n)), "B")
+    c_ptr, ldc, sc = _mat_args(C, m, n, "C")
+    alpha, beta = complex(alpha), complex(beta)
+    _check(lib().hmat_bq_add(handle.value, _op(opA), _op(opB), int(flagsA), int(flagsB) if B is not None else 0,
+                             m, n, alpha.real, alpha.imag, a_ptr, lda, sa, beta.real, beta.imag, b_ptr, ldb, sb,
+                             c_ptr, ldc, sc, _stream_ptr(stream)), "hmat_bq_add")
+    return C
+
+
+def hmat_bq_scale(handle: Handle, X, Y, alpha, op="N", flags=HMAT_BQ, stream=None):
+    """Y <- alpha op(X) (hmat_bq_scale).  Returns Y."""
+    m, n = _op_shape(X, op)
+    tr = _op(op) in (HMAT_OP_T, HMAT_OP_H)
+    x_ptr, ldx, sx = _mat_args(X, *((n, m) if tr else (m, n)), "X")
+    y_ptr, ldy, sy = _mat_args(Y, m, n, "Y")
+    alpha = complex(alpha)
+    _check(lib().hmat_bq_scale(handle.value, _op(op), int(flags), m, n, alpha.real, alpha.imag, x_ptr, ldx, sx,
+                               y_ptr, ldy, sy, _stream_ptr(stream)), "hmat_bq_scale")
+    return Y
+
+
+def hmat_bq_trace(handle: Handle, X, op="N", flags=HMAT_BQ, out=None, stream=None):
+    """Tr[op(X)] into a 2-element float64 CUDA tensor (re, im) (hmat_bq_trace); returns it."""
+    import torch
+    n = X.shape[1]
+    x_ptr, ldx, sx = _mat_args(X, n, n, "X")
+    if out is None:
+        out = torch.empty(2, dtype=torch.float64, device=X.device)
+    _check(lib().hmat_bq_trace(handle.value, _op(op), int(flags), n, x_ptr, ldx, sx, out.data_ptr(),
+                               _stream_ptr(stream)), "hmat_bq_trace")
+    return out
+
+
+def hmat_bq_to_complex(handle: Handle, X, Z=None, op="N", flags=HMAT_BQ, stream=None):
+    """The complex 2m x 2n image of op(X) as a complex128 CUDA tensor (hmat_bq_to_complex)."""
+    import torch
+    m, n = _op_shape(X, op)
+    tr = _op(op) in (HMAT_OP_T, HMAT_OP_H)
+    x_ptr, ldx, sx = _mat_args(X, *((n, m) if tr else (m, n)), "X")
+    if Z is None:
+        Z = torch.empty((2 * m, 2 * n), dtype=torch.complex128, device=X.device)
+    z_ptr, ldz = _cplx_args(Z, 2 * m, 2 * n, "Z")
+    _check(lib().hmat_bq_to_complex(handle.value, _op(op), int(flags), m, n, x_ptr, ldx, sx, z_ptr, ldz,
+                                    _stream_ptr(stream)), "hmat_bq_to_complex")
+    return Z
+
+
+def hmat_complex_to_bq(handle: Handle, Z, Y=None, stream=None):
+    """The m x n biquaternion of a 2m x 2n complex128 tensor (hmat_complex_to_bq)."""
+    import torch
+    m, n = Z.shape[0] // 2, Z.shape[1] // 2
+    z_ptr, ldz = _cplx_args(Z, 2 * m, 2 * n, "Z")
+    if Y is None:
+        Y = torch.empty((8, m, n), dtype=torch.float64, device=Z.device)
+    y_ptr, ldy, sy = _mat_args(Y, m, n, "Y")
+    _check(lib().hmat_complex_to_bq(handle.value, m, n, z_ptr, ldz, y_ptr, ldy, sy, _stream_ptr(stream)),
+           "hmat_complex_to_bq")
+    return Y
+
+
+def hmat_bq_hermiticity(handle: Handle, X, flags=HMAT_BQ, out=None, stream=None):
+    """max |X - X^dagger| into a 1-element float64 CUDA tensor (hmat_bq_hermiticity); returns it."""
+    import torch
+    n = X.shape[1]
+    x_ptr, ldx, sx = _mat_args(X, n, n, "X")
+    if out is None:
+        out = torch.empty(1, dtype=torch.float64, device=X.device)
+    _check(lib().hmat_bq_hermiticity(handle.value, int(flags), n, x_ptr, ldx, sx, out.data_ptr(),
+                                     _stream_ptr(stream)), "hmat_bq_hermiticity")
+    return out
+
+
+def hmat_bq_hadamard_block(handle: Handle, X, alpha, flags=0xCC, Z=None, offdiag=True, stream=None):
+    """(Z, offdiag) of the Hadamard block reduction (hmat_bq_hadamard_block): Z the n x n complex128
+    block, offdiag a 1-element float64 CUDA tensor (or None when offdiag=False)."""
+    import torch
+    n = X.shape[1]
+    x_ptr, ldx, sx = _mat_args(X, n, n, "X")
+    if Z is None:
+        Z = torch.empty((n, n), dtype=torch.complex128, device=X.device)
+    z_ptr, ldz = _cplx_args(Z, n, n, "Z")
+    off = torch.empty(1, dtype=torch.float64, device=X.device) if offdiag else None
+    a = complex(alpha)
+    _check(lib().hmat_bq_hadamard_block(handle.value, int(flags), n, a.real, a.imag, x_ptr, ldx, sx, z_ptr, ldz,
+                                        off.data_ptr() if off is not None else None, _stream_ptr(stream)),
+           "hmat_bq_hadamard_block")
+    return Z, off
+
+
 __all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gemm_grouped", "hmat_workspace_size",
-           "hmat_bq_gemm_split_noalloc",
+           "hmat_bq_gemm_split_noalloc", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
+           "hmat_complex_to_bq", "hmat_bq_hermiticity", "hmat_bq_hadamard_block",
            "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",
            "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]

@@ -141,3 +141,11 @@ def test_hadamard_general_transform_closed_form(alpha):
     np.testing.assert_allclose(blk, (a * A + a.conjugate() * B) / 2, rtol=0, atol=1e-13)
     assert abs(off - np.max(np.abs(a * A - a.conjugate() * B)) / 2) < 1e-13
     assert off > 0.1
+
+
+@pytest.mark.parametrize("op", OPS)
+def test_op_signs_match_the_image(op):
+    """The sign patterns of Sec. III (transposition, complex and Hermitian
+    conjugation, quaternion conjugation) are the matrix operations on the image."""
+    X = bi.small_int(213, 5, 7).numpy()
+    np.testing.assert_array_equal(iso.to_isomorph(oracle.apply_op(op, X)), iso.iso_op(op, iso.to_isomorph(X)))
