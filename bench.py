@@ -161,10 +161,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def recorded_traffic(kernel_file, workload_key):
+def recorded_traffic(kernel_file, workload_key, record="split_residue_gemm_traffic.json"):
     """DRAM bytes per launch from a committed ncu capture, if the kernel source is unchanged."""
     import hashlib
-    prof = os.path.join(ROOT, "profiles", "split_residue_gemm_traffic.json")
+    prof = os.path.join(ROOT, "profiles", record)
     src = os.path.join(ROOT, "paper_2609_02081_gb300", "csrc", kernel_file)
     if not (os.path.exists(prof) and os.path.exists(src)):
         return None
@@ -532,7 +532,10 @@ def ops_arm(args, rank, world, local):
                                        f"{args.seed}); value = the paper's sum C = A + B",
                            "l2": "operands 8 x n^2 x 8 B, larger than L2, no flush"},
                 "roofline": {"bound": "hbm", "achieved": top["GB_per_s"], "peak": peak, "unit": "GB/s",
-                             "frac": top["GB_per_s"] / peak, "traffic": None, "kernel": "axpby_kernel",
+                             "frac": top["GB_per_s"] / peak,
+                             "traffic": recorded_traffic("elementwise.cu", f"ops n={n} add",
+                                                         "elementwise_ops_traffic.json"),
+                             "kernel": "axpby_rows_kernel<2>",
                              "peak_source": f"hbm copy ({src})"},
                 "ops": out, "clocks": clk, "gpu_launches": args.steps * len(cases)}
         print(json.dumps(line), flush=True)
