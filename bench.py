@@ -42,9 +42,11 @@ def parse(argv=None):
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--seed", type=int, default=103)
-    ap.add_argument("--workload", choices=["single", "grouped", "ops"], default="single",
+    ap.add_argument("--workload", choices=["single", "grouped", "ops", "streamed"], default="single",
                     help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]; "
-                         "ops: the element-wise and mapping operations at n x n")
+                         "ops: the element-wise and mapping operations at n x n; streamed: the product with "
+                         "A, B, C in pinned host memory through a device budget (--budget-gb)")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="streamed: device budget in GB")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
     ap.add_argument("--flags", choices=["BQxBQ", "TRSxTRA", "TRSxTRS", "CxBQ"], default="BQxBQ",
@@ -542,12 +544,97 @@ def ops_arm(args, rank, world, local):
     h.close()
 
 
+def streamed_arm(args, rank, world, local):
+    """Split-mode product with every operand in pinned host memory, computed block by block within a device
+    budget; the timed region covers all copies in and out."""
+    import numpy as np
+    import torch
+    import bq_inputs as bi
+    import paper_2609_02081_gb300 as hm
+
+    dev = torch.device("cuda", local if torch.cuda.device_count() > local else 0)
+    torch.cuda.set_device(dev)
+    n = args.n
+    A = bi.fock_like(args.seed, n, n, row_scale=True, device=dev).cpu().pin_memory()
+    B = bi.fock_like(args.seed + 1, n, n, row_scale=True, device=dev).cpu().pin_memory()
+    torch.cuda.empty_cache()
+    C = torch.empty((8, n, n), dtype=torch.float64).pin_memory()
+    budget = int(args.budget_gb * (1 << 30))
+    mb, nb, kb, nbytes = hm.streamed_plan(n, n, n, mode=args.mode, tol=args.tol, budget=budget)
+    h = hm.Handle()
+    ws = torch.empty(budget, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        hm.hmat_bq_gemm_streamed(h, A, B, C, mode=args.mode, tol=args.tol, workspace=ws, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    h.set_profiling(True)
+    h.reset_profile()
+    clocks = ClockSampler(dev.index)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world)
+    kernels = {k: h.profile(k) for k in hm.KERNEL_IDS}
+    h.set_profiling(False)
+    flops64 = 64 * 2.0 * n ** 3
+    value = world * flops64 / (ms * 1e-3) / 1e12
+    if rank == 0:
+        rng = np.random.default_rng(args.seed + 7)
+        rows = np.sort(rng.choice(n, size=args.sample_rows, replace=False))
+        want, t_or, threads = oracle_rows(A.numpy(), B.numpy(), rows)
+        got = C.numpy()[:, rows, :]
+        err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
+        blocks_i, blocks_j = -(-n // mb), -(-n // nb)
+        h2d = 8 * 8 * n * n * (1 + blocks_i)          # A once per block row, B once per block
+        d2h = 8 * 8 * n * n
+        mods, bits = hm.split_info(kb, args.tol)
+        P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ)[0]
+        gl, gms = kernels["split_residue_gemm"]
+        alg = len(mods) * P * 2.0 * mb * nb * kb     # per launch (full blocks)
+        avg = gms / max(gl, 1)
+        peaks, src = measured_peaks()
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        line = {"metric": "biquaternion GEMM TFLOP/s (64-GEMM-equiv.), operands in host memory, streamed",
+                "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16" if args.mode == "split" else "f64", "data": "synthetic",
+                "config": {"workload": f"bq_gemm m=n=k={n} Fock-like row-scaled, A, B, C in pinned host memory, "
+                                       f"device budget {args.budget_gb:g} GB, blocks {mb} x {nb} x {kb}",
+                           "mode": args.mode, "tol": args.tol, "blocks": [mb, nb, kb], "device_bytes": nbytes},
+                "roofline": {"bound": "tensor", "achieved": alg / (avg * 1e-3) / 1e12, "peak": peak,
+                             "unit": "TFLOP/s", "frac": alg / (avg * 1e-3) / 1e12 / peak, "traffic": None,
+                             "kernel": "split_residue_gemm_kernel", "peak_source": f"bf16 sustained ({src})"},
+                "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "rel_fro_err_sampled": err, "err_ok": err <= 1e-12,
+                "cpu_baseline": {"value": 64 * 2.0 * len(rows) * n * n / t_or / 1e12, "unit": "TFLOP/s",
+                                 "cores": threads, "kind": "oracle",
+                                 "sample": f"{len(rows)} of {n} output rows, {t_or:.1f} s"},
+                "stages": {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items() if v[0] > 0},
+                "gpu_launches": sum(v[0] for v in kernels.values()), "clocks": clk}
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     try:
         if args.workload == "ops" and args.impl == "ours":
             ops_arm(args, rank, world, local)
+        elif args.workload == "streamed" and args.impl == "ours":
+            streamed_arm(args, rank, world, local)
         elif args.workload == "grouped" and args.impl == "ours":
             grouped(args, rank, world, local)
         elif args.impl == "reference":

@@ -277,6 +277,55 @@ hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
 hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, void *stream);
 
 /* ---------------------------------------------------------------------------
+ * Streamed products (out of core).  The paper's bilinear product moves its
+ * operands to the device piece by piece instead of holding every component
+ * there, so the largest matrix is bounded by host memory, not device memory
+ * (Sec. IV A, device-memory management of HMAT-bilinear).  Here C is computed
+ * in blocks of mb x nb (with the inner dimension in chunks of kb when a whole
+ * k does not fit): blocks of host-resident operands are copied into
+ * double-buffered device slots on a copy-in stream, the product of each block
+ * runs on `stream` through the same kernels as hmat_bq_gemm, and finished C
+ * blocks return on a copy-out stream, so copies overlap the products.
+ * Operands already in device memory are read in place.  With kb = k every
+ * block is the same computation as the corresponding part of hmat_bq_gemm,
+ * bit for bit, in both modes; with kb < k, C accumulates the chunks with
+ * beta = 1 (rounding differs; split-mode error is bounded per chunk).
+ * ------------------------------------------------------------------------- */
+
+/* Block sizes and device bytes the streamed product uses for a device
+ * budget of `budget` bytes: the largest square-ish mb x nb (multiples of 128
+ * unless the matrix is smaller) with kb = k if that fits, else k halved
+ * (rounded to 64) until it does.  *_on_host: whether each operand is
+ * host-resident (streamed) or device-resident (read in place).  Host-only;
+ * handle may be NULL (then the default algorithm and tile rule).
+ * Errors: INVALID_VALUE, WORKSPACE_TOO_SMALL (nothing fits),
+ * TOLERANCE_UNREACHABLE / UNSUPPORTED as hmat_workspace_size. */
+hmat_status hmat_streamed_plan(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+                               int64_t m, int64_t n, int64_t k, int32_t mode, double tol, size_t budget,
+                               int32_t a_on_host, int32_t b_on_host, int32_t c_on_host,
+                               int64_t *mb, int64_t *nb, int64_t *kb, size_t *bytes);
+
+/* C <- alpha op(A) op(B) + beta C with A, B, C each in host memory (pinned
+ * for copy / compute overlap; pageable works but serialises) or device
+ * memory; arguments and layout as hmat_bq_gemm.  `workspace` (device, 256-byte
+ * aligned) of `workspace_bytes` is the whole device budget: slots and product
+ * workspace are carved from it as hmat_streamed_plan describes.  The call
+ * returns once everything is enqueued; host buffers must stay valid and
+ * untouched until `stream` has completed the call.  The handle's copy streams
+ * and events are created on first use; streamed calls on one handle must not
+ * run concurrently from several host threads.
+ * Errors: as hmat_bq_gemm; WORKSPACE_TOO_SMALL when no block plan fits. */
+hmat_status hmat_bq_gemm_streamed(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+                                  int64_t m, int64_t n, int64_t k,
+                                  double alpha_re, double alpha_im,
+                                  const double *A, int64_t lda, int64_t strideA,
+                                  const double *B, int64_t ldb, int64_t strideB,
+                                  double beta_re, double beta_im,
+                                  double *C, int64_t ldc, int64_t strideC,
+                                  int32_t mode, double tol, void *workspace, size_t workspace_bytes,
+                                  void *stream);
+
+/* ---------------------------------------------------------------------------
  * Element-wise operations (Sec. III: complex scaling, addition, trace) and the
  * data movement of the diagonalisation path (Sec. III complex image and
  * Eq. mapping-formulas; Sec. III C Hadamard transformation).  All are

@@ -82,6 +82,12 @@ SIGNATURES = {
     "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
     "hmat_get_profile": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "hmat_reset_profile": (ctypes.c_int, [_ptr]),
+    "hmat_streamed_plan": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _i32, _dbl, _sz, _i32,
+                                          _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
+                                          ctypes.POINTER(_i64), ctypes.POINTER(_sz)]),
+    "hmat_bq_gemm_streamed": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _dbl, _dbl,
+                                             _ptr, _i64, _i64, _ptr, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
+                                             _i32, _dbl, _ptr, _sz, _ptr]),
     "hmat_bq_add": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
                                    _dbl, _dbl, _ptr, _i64, _i64, _ptr, _i64, _i64, _ptr]),
     "hmat_bq_scale": (ctypes.c_int, [_ptr, _i32, _u32, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64, _ptr, _i64, _i64,
@@ -356,6 +362,59 @@ def bq_gemm_host(handle: Handle, A_host, B_host, C_host, opA="N", opB="N", flags
     return C_host, h2d, C_host.numel() * 8
 
 
+# ----------------------------------------------------------------------------- streamed (out-of-core) products
+def _any_mat_args(X, rows, cols, name):
+    """(ptr, ld, stride, on_host) of an 8 x rows x cols float64 tensor on the host or the device."""
+    import torch
+    if X is None:
+        return None, max(cols, 1), 0, False
+    if not isinstance(X, torch.Tensor) or X.dtype != torch.float64:
+        raise TypeError(f"{name} must be a float64 tensor")
+    if X.dim() != 3 or X.shape[0] != 8 or X.shape[1] != rows or X.shape[2] != cols:
+        raise ValueError(f"{name} must have shape (8, {rows}, {cols}), got {tuple(X.shape)}")
+    if cols > 1 and X.stride(2) != 1:
+        raise ValueError(f"{name} components must be row-major (last stride 1)")
+    return X.data_ptr(), max(X.stride(1), cols, 1), X.stride(0), not X.is_cuda
+
+
+def streamed_plan(m, n, k, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, mode="split", tol=0.0,
+                  budget=8 << 30, on_host=(True, True, True), handle=None):
+    """(mb, nb, kb, device bytes) of the streamed product for a device budget (hmat_streamed_plan)."""
+    mb, nb, kb, nbytes = _i64(), _i64(), _i64(), _sz()
+    _check(lib().hmat_streamed_plan(handle.value if handle is not None else None, _op(opA), _op(opB), int(flagsA),
+                                    int(flagsB), int(m), int(n), int(k), _mode(mode), float(tol), int(budget),
+                                    int(on_host[0]), int(on_host[1]), int(on_host[2]), ctypes.byref(mb),
+                                    ctypes.byref(nb), ctypes.byref(kb), ctypes.byref(nbytes)), "hmat_streamed_plan")
+    return mb.value, nb.value, kb.value, nbytes.value
+
+
+def hmat_bq_gemm_streamed(handle: Handle, A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, alpha=1.0,
+                          beta=0.0, mode="split", tol=0.0, budget=None, workspace=None, stream=None):
+    """C <- alpha op(A) op(B) + beta C with host (pinned) or device tensors, computed block by block within a
+    device budget (hmat_bq_gemm_streamed).  workspace: a uint8 CUDA tensor (the budget), or None to allocate
+    `budget` bytes.  Returns C; host buffers are complete once the stream is."""
+    import torch
+    oa, ob = _op(opA), _op(opB)
+    ta, tb = oa in (HMAT_OP_T, HMAT_OP_H), ob in (HMAT_OP_T, HMAT_OP_H)
+    m = A.shape[2] if ta else A.shape[1]
+    k = A.shape[1] if ta else A.shape[2]
+    n = B.shape[1] if tb else B.shape[2]
+    a_ptr, lda, sa, _ = _any_mat_args(A, *((k, m) if ta else (m, k)), "A")
+    b_ptr, ldb, sb, _ = _any_mat_args(B, *((n, k) if tb else (k, n)), "B")
+    c_ptr, ldc, sc, _ = _any_mat_args(C, m, n, "C")
+    ws = workspace
+    if ws is None:
+        if budget is None:
+            raise ValueError("give a device budget (bytes) or a workspace tensor")
+        ws = torch.empty(int(budget), dtype=torch.uint8, device="cuda")
+    alpha, beta = complex(alpha), complex(beta)
+    _check(lib().hmat_bq_gemm_streamed(handle.value, oa, ob, int(flagsA), int(flagsB), m, n, k, alpha.real,
+                                       alpha.imag, a_ptr, lda, sa, b_ptr, ldb, sb, beta.real, beta.imag, c_ptr, ldc,
+                                       sc, _mode(mode), float(tol), ws.data_ptr(), ws.numel(),
+                                       _stream_ptr(stream)), "hmat_bq_gemm_streamed")
+    return C
+
+
 # ----------------------------------------------------------------------------- element-wise and mapping operations
 def _op_shape(X, op):
     """(rows, cols) of op(X) for a stored 8 x r x c tensor."""
@@ -470,7 +529,7 @@ def hmat_bq_hadamard_block(handle: Handle, X, alpha, flags=0xCC, Z=None, offdiag
 
 
 __all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gemm_grouped", "hmat_workspace_size",
-           "hmat_bq_gemm_split_noalloc", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
+           "hmat_bq_gemm_split_noalloc", "hmat_bq_gemm_streamed", "streamed_plan", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
            "hmat_complex_to_bq", "hmat_bq_hermiticity", "hmat_bq_hadamard_block",
            "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",
            "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]

@@ -103,6 +103,9 @@ struct SplitPrep {
   int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
   int64_t ws_needed = 0;
   int max_bits = 0, max_nmod = 0;
+  // one job whose A-side exponents and encoded factor tiles are already in the
+  // workspace from the previous call with the same A block and the same shape
+  bool reuse_a = false;
 };
 
 // Lay the jobs out in a workspace of ws_bytes (WORKSPACE_TOO_SMALL if it does not fit).
@@ -144,8 +147,8 @@ SplitState& handle_split(hmat_context* h);
 
 // Device-side kernel launchers (split_kernels.cu).
 struct SplitConsts;
-cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int grid, cudaStream_t s,
-                                   unsigned char* ws);
+cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int64_t first_unit,
+                                   cudaStream_t s, unsigned char* ws);
 // units are blocks: encode tiles of 32 rows x 32 k, CRT blocks of 256 elements
 cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int side, int64_t units,
                                 cudaStream_t s, unsigned char* ws, int max_bits);

@@ -254,14 +254,17 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
                          unsigned char* ws, cudaStream_t stream) {
   const int njobs = (int)sp.jobs.size();
   cudaError_t e;
+  // with reuse_a (one job) the A units come first in both stages and are skipped
+  const bool skip_a = sp.reuse_a && njobs == 1;
   {
     ProfScope ps(h, 1, stream);
-    e = launch_split_exponents(d_jobs, njobs, sp.exp_units, 0, stream, ws);
+    const int64_t first = skip_a ? (sp.jobs[0].d.m + 31) / 32 : 0;
+    e = launch_split_exponents(d_jobs, njobs, sp.exp_units, first, stream, ws);
   }
   if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 2, stream);
-    e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws, sp.max_bits);
+    if (!skip_a) e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws, sp.max_bits);
     if (e == cudaSuccess) e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws, sp.max_bits);
   }
   if (e != cudaSuccess) return split_cuda_error(e);

@@ -104,10 +104,20 @@ __device__ __forceinline__ int find_split_job(const SplitJob* jobs, int njobs, i
 // ------------------------------------------------------------------ 1. exponents
 // One block (256 threads) per group of 32 outputs: rows of op(A) or columns of op(B).
 // s = b - 1 - floor(log2 max|x|) over the eight present components and k.
-__global__ void __launch_bounds__(256) split_exponents_kernel(const SplitJob* __restrict__ jobs, int njobs,
-                                                              unsigned char* __restrict__ ws, uint32_t* err) {
-  __shared__ int red[8][32];
-  const int64_t unit = blockIdx.x;
+constexpr int kExpThreads = 1024;   // 32 warps per 32 outputs: k is split over the warps (or lanes)
+
+// biased exponent field of x; inf / NaN set `bad`
+__device__ __forceinline__ int exp_field(double x, bool& bad) {
+  const int ef = (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7FF);
+  bad |= (ef == 0x7FF);
+  return ef;
+}
+
+__global__ void __launch_bounds__(kExpThreads) split_exponents_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                                      unsigned char* __restrict__ ws,
+                                                                      uint32_t* err, int64_t first_unit) {
+  __shared__ int red[32][33];
+  const int64_t unit = first_unit + blockIdx.x;
   const int g = find_split_job(jobs, njobs, unit, 0);
   const SplitJob& sj = jobs[g];
   const JobDesc& d = sj.d;
@@ -119,6 +129,7 @@ __global__ void __launch_bounds__(256) split_exponents_kernel(const SplitJob* __
   const int64_t ld = sideB ? d.ldb : d.lda, cs = sideB ? d.sB : d.sA;
   const uint32_t flags = sideB ? d.fb : d.fa;
   const int nout = sideB ? d.n : d.m;
+  const int64_t K = d.k;
   // the reduction for output r runs along k; contiguous in memory when op(A) is
   // not transposed (A row) or op(B) is transposed (stored B row).
   const bool contiguous = sideB ? (d.transB != 0) : (d.transA == 0);
@@ -126,49 +137,49 @@ __global__ void __launch_bounds__(256) split_exponents_kernel(const SplitJob* __
   int best = 0;
   bool bad = false;
   if (contiguous) {
-    // warp handles outputs grp*32 + warp*4 + q, lanes stride k
-    for (int q = 0; q < 4; ++q) {
-      const int r = grp * 32 + warp * 4 + q;
-      int mx = 0;
-      if (r < nout) {
-        for (int c = 0; c < 8; ++c) {
-          if (!((flags >> c) & 1u)) continue;
-          const double* row = base + (int64_t)c * cs + (int64_t)r * ld;
-          for (int kk = lane; kk < d.k; kk += 32) {
-            const unsigned long long u = (unsigned long long)__double_as_longlong(__ldg(row + kk));
-            const int ef = (int)((u >> 52) & 0x7FF);
-            bad |= (ef == 0x7FF);
-            mx = max(mx, ef);
-          }
+    // warp w handles output grp*32 + w; lanes stride k, four loads in flight
+    const int r = grp * 32 + warp;
+    int mx = 0;
+    if (r < nout) {
+      for (int c = 0; c < 8; ++c) {
+        if (!((flags >> c) & 1u)) continue;
+        const double* row = base + (int64_t)c * cs + (int64_t)r * ld;
+        int64_t kk = lane;
+        for (; kk + 96 < K; kk += 128) {
+          const double x0 = __ldg(row + kk), x1 = __ldg(row + kk + 32);
+          const double x2 = __ldg(row + kk + 64), x3 = __ldg(row + kk + 96);
+          mx = max(mx, max(max(exp_field(x0, bad), exp_field(x1, bad)), max(exp_field(x2, bad), exp_field(x3, bad))));
         }
+        for (; kk < K; kk += 32) mx = max(mx, exp_field(__ldg(row + kk), bad));
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      if (lane == 0) red[0][warp * 4 + q] = mx;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) red[0][warp] = mx;
     __syncthreads();
     if (threadIdx.x < 32) best = red[0][threadIdx.x];
   } else {
-    // lanes over the 32 outputs (consecutive addresses), warps split k
+    // lanes over the 32 outputs (consecutive addresses), the 32 warps split k, four loads in flight
     const int r = grp * 32 + lane;
     int mx = 0;
     if (r < nout) {
       for (int c = 0; c < 8; ++c) {
         if (!((flags >> c) & 1u)) continue;
         const double* col = base + (int64_t)c * cs + r;
-        for (int kk = warp; kk < d.k; kk += 8) {
-          const unsigned long long u = (unsigned long long)__double_as_longlong(__ldg(col + (int64_t)kk * ld));
-          const int ef = (int)((u >> 52) & 0x7FF);
-          bad |= (ef == 0x7FF);
-          mx = max(mx, ef);
+        int64_t kk = warp;
+        for (; kk + 96 < K; kk += 128) {
+          const double x0 = __ldg(col + kk * ld), x1 = __ldg(col + (kk + 32) * ld);
+          const double x2 = __ldg(col + (kk + 64) * ld), x3 = __ldg(col + (kk + 96) * ld);
+          mx = max(mx, max(max(exp_field(x0, bad), exp_field(x1, bad)), max(exp_field(x2, bad), exp_field(x3, bad))));
         }
+        for (; kk < K; kk += 32) mx = max(mx, exp_field(__ldg(col + kk * ld), bad));
       }
     }
     red[warp][lane] = mx;
     __syncthreads();
     if (threadIdx.x < 32) {
       best = red[0][lane];
-      for (int w = 1; w < 8; ++w) best = max(best, red[w][lane]);
+      for (int w = 1; w < 32; ++w) best = max(best, red[w][lane]);
     }
   }
   if (bad) atomicOr(err, kErrNonFinite);
@@ -715,10 +726,11 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
   return cudaMemcpyToSymbol(c_Pf, pf, sizeof(pf));
 }
 
-cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int, cudaStream_t s,
-                                   unsigned char* ws) {
-  if (units <= 0) return cudaSuccess;
-  split_exponents_kernel<<<(unsigned)units, 256, 0, s>>>(d_jobs, njobs, ws, device_error_ptr());
+cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int64_t first_unit,
+                                   cudaStream_t s, unsigned char* ws) {
+  if (units <= first_unit) return cudaSuccess;
+  split_exponents_kernel<<<(unsigned)(units - first_unit), kExpThreads, 0, s>>>(d_jobs, njobs, ws,
+                                                                                 device_error_ptr(), first_unit);
   return cudaGetLastError();
 }
 

@@ -87,3 +87,24 @@ def test_config_n24576_fp64(handle):
     print(f"n=24576 fp64: {ms:.0f} ms, {64 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} TFLOP/s 64-equiv, "
           f"{24 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} executed, sampled error {err:.3e}")
     assert err <= 1e-14
+
+
+def test_streamed_n8192_from_host_equals_in_core(handle):
+    """The n = 8192 precision workload with A, B, C in pinned host memory and a
+    24 GB device budget: every block equals the in-core product bit for bit."""
+    n = 8192
+    dA = bi.fock_like(103, n, n, row_scale=True, device="cuda")
+    dB = bi.fock_like(104, n, n, row_scale=True, device="cuda")
+    dC = torch.empty((8, n, n), dtype=torch.float64, device="cuda")
+    hm.hmat_bq_gemm(handle, dA, dB, dC, mode="split", tol=TOL)
+    want = dC.cpu().numpy()
+    A, B = dA.cpu().pin_memory(), dB.cpu().pin_memory()
+    del dA, dB, dC
+    torch.cuda.empty_cache()
+    C = torch.empty((8, n, n), dtype=torch.float64).pin_memory()
+    budget = 24 << 30
+    mb, nb, kb, _ = hm.streamed_plan(n, n, n, mode="split", tol=TOL, budget=budget)
+    assert kb == n and mb < n
+    hm.hmat_bq_gemm_streamed(handle, A, B, C, mode="split", tol=TOL, budget=budget)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(C.numpy(), want)
