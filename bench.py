@@ -329,14 +329,15 @@ def ours(args, rank, world, local):
         Ah = A.cpu().pin_memory()
         Bh = B.cpu().pin_memory()
         Ch = torch.empty((8, n, n), dtype=torch.float64).pin_memory()
-        hm.bq_gemm_host(h, Ah, Bh, Ch, mode=args.mode, tol=args.tol, device_buffers=(A, B, C), workspace=ws)
+        hm.bq_gemm_host(h, Ah, Bh, Ch, args.opA, "N", fa, fb, mode=args.mode, tol=args.tol, device_buffers=(A, B, C),
+                        workspace=ws)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         h2d = d2h = 0
         for _ in range(args.e2e_steps):
-            _, h2d, d2h = hm.bq_gemm_host(h, Ah, Bh, Ch, mode=args.mode, tol=args.tol, device_buffers=(A, B, C),
-                                          workspace=ws)
+            _, h2d, d2h = hm.bq_gemm_host(h, Ah, Bh, Ch, args.opA, "N", fa, fb, mode=args.mode, tol=args.tol,
+                                          device_buffers=(A, B, C), workspace=ws)
         e1.record(stream)
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / args.e2e_steps
