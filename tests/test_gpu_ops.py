@@ -210,3 +210,24 @@ def test_ops_at_n2048(handle):
     tw = ops.trace(hA)
     assert abs(complex(t[0], t[1]) - tw) <= 8 * n * np.finfo(float).eps * 2 * np.abs(np.diagonal(hA[0])).sum() + 1e-300
     assert handle.device_error() == 0
+
+
+def test_empty_and_degenerate_shapes(handle):
+    """m or n = 0 returns at once; 1 x 1 and single rows / columns go through the ragged tails."""
+    E = torch.empty((8, 0, 5), dtype=torch.float64, device=DEV)
+    hm.hmat_bq_add(handle, E, E, torch.empty_like(E))
+    hm.hmat_bq_scale(handle, E, torch.empty_like(E), 2.0)
+    assert hm.hmat_bq_to_complex(handle, E).shape == (0, 10)
+    t = hm.hmat_bq_trace(handle, torch.empty((8, 0, 0), dtype=torch.float64, device=DEV)).cpu().numpy()
+    assert t[0] == 0.0 and t[1] == 0.0
+    d = hm.hmat_bq_hermiticity(handle, torch.empty((8, 0, 0), dtype=torch.float64, device=DEV)).cpu().numpy()
+    assert d[0] == 0.0
+    for m, n in [(1, 1), (1, 257), (257, 1), (3, 2)]:
+        X = bi.uniform(340 + m, m, n)
+        Y = bi.uniform(350 + n, m, n)
+        C = torch.empty((8, m, n), dtype=torch.float64, device=DEV)
+        hm.hmat_bq_add(handle, X.to(DEV), Y.to(DEV), C, 1 - 2j, 3.0)
+        np.testing.assert_array_equal(C.cpu().numpy(), ops.add(X.numpy(), Y.numpy(), 1 - 2j, 3.0))
+        Z = hm.hmat_bq_to_complex(handle, X.to(DEV))
+        np.testing.assert_array_equal(Z.cpu().numpy(), iso.to_isomorph(X.numpy()))
+        np.testing.assert_array_equal(hm.hmat_complex_to_bq(handle, Z).cpu().numpy(), iso.from_isomorph(Z.cpu().numpy()))

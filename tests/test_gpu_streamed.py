@@ -120,3 +120,27 @@ def test_streamed_budget_too_small(handle):
     with pytest.raises(hm.HmatError) as ei:
         hm.hmat_bq_gemm_streamed(handle, A, A, C, mode="split", tol=TOL, workspace=ws)
     assert ei.value.status == 4
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+def test_streamed_degenerate_shapes(handle, mode):
+    """k = 0 (C <- beta C), a single row, and m = 0 through the streamed path."""
+    m, n = 130, 70
+    A = torch.empty((8, m, 0), dtype=torch.float64).pin_memory()
+    B = torch.empty((8, 0, n), dtype=torch.float64).pin_memory()
+    C0 = bi.uniform(440, m, n)
+    C = C0.clone().pin_memory()
+    hm.hmat_bq_gemm_streamed(handle, A, B, C, beta=2 - 1j, mode=mode, tol=TOL, budget=64 << 20)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(C.numpy(), oracle.bq_gemm(A.numpy(), B.numpy(), beta=2 - 1j, C=C0.numpy()))
+    A1 = bi.uniform(441, 1, 300).pin_memory()
+    B1 = bi.uniform(442, 300, 1).pin_memory()
+    C1 = torch.empty((8, 1, 1), dtype=torch.float64).pin_memory()
+    hm.hmat_bq_gemm_streamed(handle, A1, B1, C1, mode=mode, tol=TOL, budget=64 << 20)
+    torch.cuda.synchronize()
+    want = oracle.bq_gemm(A1.numpy(), B1.numpy())
+    assert np.linalg.norm(C1.numpy() - want) <= TOL * np.linalg.norm(want)
+    A0 = torch.empty((8, 0, 10), dtype=torch.float64).pin_memory()
+    C0e = torch.empty((8, 0, 1), dtype=torch.float64).pin_memory()
+    hm.hmat_bq_gemm_streamed(handle, A0, bi.uniform(443, 10, 1).pin_memory(), C0e, mode=mode, tol=TOL,
+                             budget=64 << 20)
