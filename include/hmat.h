@@ -293,9 +293,12 @@ hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, v
  * ------------------------------------------------------------------------- */
 
 /* Block sizes and device bytes the streamed product uses for a device
- * budget of `budget` bytes: the largest square-ish mb x nb (multiples of 128
- * unless the matrix is smaller) with kb = k if that fits, else k halved
- * (rounded to 64) until it does.  *_on_host: whether each operand is
+ * budget of `budget` bytes, with kb = k if anything fits, else k halved
+ * (rounded to 64) until something does.  Shapes in order of preference: when
+ * an operand is host-resident (and n >= 512), column panels mb = m,
+ * nb = n/4 then n/2 (A copied and encoded once; B and C panels stream behind
+ * the products); then square blocks mb = nb from the whole matrix down to 128
+ * (multiples of 128 unless the matrix is smaller).  *_on_host: whether each operand is
  * host-resident (streamed) or device-resident (read in place).  Host-only;
  * handle may be NULL (then the default algorithm and tile rule).
  * Errors: INVALID_VALUE, WORKSPACE_TOO_SMALL (nothing fits),

@@ -1104,17 +1104,25 @@ hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d
     kbs.push_back(kb);
     if (kb <= 1024) break;
   }
-  std::vector<int64_t> sides;
+  // candidate block shapes in order of preference: with a host-resident
+  // operand first column panels (all rows of C, n split in 4 then 2), which
+  // copy and encode A once and stream B and C panels behind the products;
+  // then square blocks from the whole matrix down to 128
+  std::vector<std::pair<int64_t, int64_t>> shapes;
+  if ((a_host || b_host || c_host) && n >= 512) {
+    shapes.push_back({m, round_up((n + 3) / 4, 128)});
+    shapes.push_back({m, round_up((n + 1) / 2, 128)});
+  }
   const int64_t top = std::max(m, n);
   for (int64_t b = round_up(top, 128); b >= 128; b = round_up(b / 2, 128)) {
-    sides.push_back(b);
+    shapes.push_back({b, b});
     if (b == 128) break;
   }
   for (int64_t kb : kbs) {
-    for (int64_t b : sides) {
+    for (const auto& sh : shapes) {
       StreamedPlan p;
-      p.mb = std::min(m, b);
-      p.nb = std::min(n, b);
+      p.mb = std::min(m, sh.first);
+      p.nb = std::min(n, sh.second);
       p.kb = std::min(k, kb);
       p.a_blk = a_host ? blk_bytes(p.mb, p.kb) : 0;
       p.b_blk = b_host ? blk_bytes(p.kb, p.nb) : 0;

@@ -171,18 +171,23 @@ def test_streamed_plan_fits_budget_and_prefers_whole_k():
     m = n = k = 4096
     prev = None
     for budget in [1 << 40, 64 << 30, 16 << 30, 4 << 30, 1 << 30]:
-        mb, nb, kb, nbytes = hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=budget)
+        mb, nb, kb, nbytes = hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=budget,
+                                              on_host=(False, True, True))
         assert nbytes <= budget
         assert mb % 128 == 0 or mb == m
         if prev is not None:
             assert mb * nb * kb <= prev
         prev = mb * nb * kb
-    assert hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 40)[:3] == (m, n, k)
+    # host-resident operands: column panels (A copied and encoded once); device-resident: one block
+    assert hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 40)[:3] == (m, n // 4, k)
+    assert hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 40,
+                            on_host=(False, False, False))[:3] == (m, n, k)
     assert hm.streamed_plan(m, n, k, mode="fp64", budget=1 << 30)[2] == k     # FP64: only slots, k stays whole
     # device-resident operands need no slots
     full = hm.streamed_plan(m, n, k, mode="fp64", budget=1 << 40, on_host=(True, True, True))[3]
     none = hm.streamed_plan(m, n, k, mode="fp64", budget=1 << 40, on_host=(False, False, False))[3]
-    assert none == 0 and full == 2 * 3 * 8 * 8 * m * n
+    nb = n // 4                                    # column panels: A whole, B and C in quarters
+    assert none == 0 and full == 2 * 64 * (m * k + k * nb + m * nb)
     with pytest.raises(hm.HmatError) as ei:
         hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 20)
     assert ei.value.status == 4
