@@ -216,6 +216,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // Centred residue (as float) of a scaled integer given by its float limbs:
 // X = hi 2^23 + lo for |X| <= 2^47 (LIMBS == 2), else X = x2 2^36 + x1 2^18 + x0
 // (|X| <= 2^52); every limb and partial sum stays below 2^24 (exact floats).
+// (Three 16-bit limbs with one reduction would take two fewer instructions per
+// residue but a third staged float per value; measured slower: spills, fewer
+// resident blocks.)
 template <int LIMBS>
 __device__ __forceinline__ float residue_of(const float* x, const ModConst& mc) {
   if (LIMBS == 2) return fmod_c(fmaf(fmod_c(x[1], mc), mc.c23, x[0]), mc);
@@ -315,18 +318,26 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
     for (int c = 0; c < 8; ++c) sg[c] = (float)sign[c];
     // single-coefficient groups: left a1, a4, a2, a3; right b1, b3, b4, b2
     const int pick0 = 0, pick1 = side ? 2 : 3, pick2 = side ? 3 : 1, pick3 = side ? 1 : 2;
-    auto emit = [&](int gi, const float (&re)[4], const float (&im)[4], int l, const ModConst& mc) {
+    // reduced: re and im are residues already (the single-coefficient groups);
+    // otherwise (Hadamard sums) they are reduced first.  Re + Im is reduced
+    // from the two residues.
+    auto put = [&](int f, const float (&v)[4], int l) {
+      if (f < 0) return;
+      const uint2 pkd = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
+                                   __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
+      *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pkd;
+    };
+    auto emit = [&](int gi, const float (&re)[4], const float (&im)[4], int l, const ModConst& mc, bool reduced) {
+      float v0[4], v1[4], v2[4];
 #pragma unroll
-      for (int part = 0; part < 3; ++part) {
-        const int f = s_slot[gi][part];
-        if (f < 0) continue;
-        float v[4];
+      for (int q = 0; q < 4; ++q) v0[q] = reduced ? re[q] : fmod_c(re[q], mc);
+      put(s_slot[gi][0], v0, l);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = fmod_c(part == 0 ? re[q] : (part == 1 ? im[q] : re[q] + im[q]), mc);
-        const uint2 pkd = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
-                                     __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
-        *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pkd;
-      }
+      for (int q = 0; q < 4; ++q) v1[q] = reduced ? im[q] : fmod_c(im[q], mc);
+      put(s_slot[gi][1], v1, l);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) v2[q] = fmod_c(v0[q] + v1[q], mc);
+      put(s_slot[gi][2], v2, l);
     };
     for (int l = 0; l < sj.nmod; ++l) {
       const ModConst& mc = c_mod[l];
@@ -340,7 +351,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
         }
       const int pk[4] = {pick0, pick1, pick2, pick3};
 #pragma unroll
-      for (int g = 0; g < 4; ++g) emit(g, xr[pk[g]], xi[pk[g]], l, mc);
+      for (int g = 0; g < 4; ++g) emit(g, xr[pk[g]], xi[pk[g]], l, mc, true);
       // Hadamard rows by two butterfly stages, in place
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
@@ -352,7 +363,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
         xi[0][q] = si01 + si23; xi[1][q] = si01 - si23; xi[2][q] = di01 + di23; xi[3][q] = di01 - di23;
       }
 #pragma unroll
-      for (int g = 0; g < 4; ++g) emit(4 + g, xr[g], xi[g], l, mc);
+      for (int g = 0; g < 4; ++g) emit(4 + g, xr[g], xi[g], l, mc, false);
     }
     return;
   }
