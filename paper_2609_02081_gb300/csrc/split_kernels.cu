@@ -486,13 +486,29 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
   const int64_t cavail = (ncols - (int64_t)jb * kCrtThreads) / 16;
   const int cmax = cavail < kCrtThreads / 16 ? (int)cavail : kCrtThreads / 16;
 
-  // prefetch modulus l's np residue rows (128 bytes each) into ring slot l % 3
+  // prefetch modulus l's np residue rows (128 bytes each) into ring slot l % 3;
+  // this thread's 16-byte chunks (at most kMaxProducts * 8 / kCrtThreads) are fixed
+  constexpr int kMaxChunks = kMaxProducts * (kCrtThreads / 16) / kCrtThreads;
+  int64_t c_src[kMaxChunks];
+  int c_dst[kMaxChunks];
+  int nchunks = 0;
+#pragma unroll
+  for (int u = 0; u < kMaxChunks; ++u) {
+    const int idx = tid + u * kCrtThreads;
+    const int p = idx / (kCrtThreads / 16), c = idx % (kCrtThreads / 16);
+    c_src[u] = (int64_t)p * plane + c * 16;
+    c_dst[u] = p * kCrtThreads + c * 16;
+    if (idx < np * (kCrtThreads / 16) && c < cmax) nchunks = u + 1;
+  }
   auto issue = [&](int l) {
     if (l < nm) {
-      uint8_t(*slot)[kCrtThreads] = ring[l % kStages];
-      for (int idx = tid; idx < np * (kCrtThreads / 16); idx += kCrtThreads) {
-        const int p = idx / (kCrtThreads / 16), c = idx % (kCrtThreads / 16);
-        if (c < cmax) cp_async16(&slot[p][c * 16], rowbase + ((int64_t)l * np + p) * plane + c * 16);
+      uint8_t* slot = &ring[l % kStages][0][0];
+      const unsigned char* src = rowbase + (int64_t)l * np * plane;
+#pragma unroll
+      for (int u = 0; u < kMaxChunks; ++u) {
+        const int idx = tid + u * kCrtThreads;
+        if (u < nchunks && idx < np * (kCrtThreads / 16) && (idx % (kCrtThreads / 16)) < cmax)
+          cp_async16(slot + c_dst[u], src + c_src[u]);
       }
     }
     cp_async_commit();
@@ -516,35 +532,34 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
     if (structured) {
       // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
       // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
-      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); all exact floats
-      float pre[8], pim[8];
+      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); in 32-bit
+      // integers (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
+      int pre[8], pim[8];
 #pragma unroll
       for (int r = 0; r < 8; ++r) {
-        float t[3];
-#pragma unroll
-        for (int u = 0; u < 3; ++u)   // int8 -> float through the 1.5 * 2^23 bias
-          t[u] = __int_as_float(0x4B400000 + (int)(int8_t)slot[3 * r + u][tid]) - 12582912.0f;
-        pre[r] = t[0] - t[1];
-        pim[r] = t[2] - t[0] - t[1];
+        const int t0 = (int8_t)slot[3 * r][tid], t1 = (int8_t)slot[3 * r + 1][tid];
+        const int t2 = (int8_t)slot[3 * r + 2][tid];
+        pre[r] = t0 - t1;
+        pim[r] = t2 - t0 - t1;
       }
-      float q4[8];
+      int q4[8];
       {
-        const float a = pre[4] + pre[5], b = pre[4] - pre[5], c = pre[6] + pre[7], dd = pre[6] - pre[7];
-        q4[0] = fmaf(8.f, pre[0], -(a + c));
-        q4[1] = fmaf(-8.f, pre[1], a - c);
-        q4[2] = fmaf(-8.f, pre[2], b + dd);
-        q4[3] = fmaf(-8.f, pre[3], b - dd);
-        const float ai = pim[4] + pim[5], bi = pim[4] - pim[5], ci = pim[6] + pim[7], di = pim[6] - pim[7];
-        q4[4] = fmaf(8.f, pim[0], -(ai + ci));
-        q4[5] = fmaf(-8.f, pim[1], ai - ci);
-        q4[6] = fmaf(-8.f, pim[2], bi + di);
-        q4[7] = fmaf(-8.f, pim[3], bi - di);
+        const int a = pre[4] + pre[5], b = pre[4] - pre[5], c = pre[6] + pre[7], dd = pre[6] - pre[7];
+        q4[0] = 8 * pre[0] - (a + c);
+        q4[1] = -8 * pre[1] + (a - c);
+        q4[2] = -8 * pre[2] + (b + dd);
+        q4[3] = -8 * pre[3] + (b - dd);
+        const int ai = pim[4] + pim[5], bi = pim[4] - pim[5], ci = pim[6] + pim[7], di = pim[6] - pim[7];
+        q4[4] = 8 * pim[0] - (ai + ci);
+        q4[5] = -8 * pim[1] + (ai - ci);
+        q4[6] = -8 * pim[2] + (bi + di);
+        q4[7] = -8 * pim[3] + (bi - di);
       }
-      const float inv4 = (float)mc.inv4;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        // |4Q| <= 8*254 + 4*254 and 4^-1 < 2^8: the product is an exact float below 2^22
-        float r = fmod_c(q4[e] * inv4, mc);
+        // |4Q * 4^-1| < 4572 * 255 < 2^21: int -> float through the 1.5 * 2^23 bias is exact
+        const float qf = __int_as_float(q4[e] * mc.inv4 + 0x4B400000) - 12582912.0f;
+        float r = fmod_c(qf, mc);
         if (r < 0.f) r += mc.pf;
         const uint32_t ru = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
 #pragma unroll
