@@ -487,8 +487,9 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
   const int cmax = cavail < kCrtThreads / 16 ? (int)cavail : kCrtThreads / 16;
 
   // prefetch modulus l's np residue rows (128 bytes each) into ring slot l % 3;
-  // this thread's 16-byte chunks (at most kMaxProducts * 8 / kCrtThreads) are fixed
-  constexpr int kMaxChunks = kMaxProducts * (kCrtThreads / 16) / kCrtThreads;
+  // this thread's first two 16-byte chunks (all of them for np <= 32) are fixed,
+  // further ones (larger plans) are computed per modulus
+  constexpr int kMaxChunks = 2;
   int64_t c_src[kMaxChunks];
   int c_dst[kMaxChunks];
   int nchunks = 0;
@@ -509,6 +510,10 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
         const int idx = tid + u * kCrtThreads;
         if (u < nchunks && idx < np * (kCrtThreads / 16) && (idx % (kCrtThreads / 16)) < cmax)
           cp_async16(slot + c_dst[u], src + c_src[u]);
+      }
+      for (int idx = tid + kMaxChunks * kCrtThreads; idx < np * (kCrtThreads / 16); idx += kCrtThreads) {
+        const int p = idx / (kCrtThreads / 16), c = idx % (kCrtThreads / 16);
+        if (c < cmax) cp_async16(slot + p * kCrtThreads + c * 16, src + (int64_t)p * plane + c * 16);
       }
     }
     cp_async_commit();
