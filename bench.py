@@ -51,6 +51,9 @@ def parse(argv=None):
     ap.add_argument("--budget-gb", type=float, default=64.0, help="streamed: device budget in GB")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
+    ap.add_argument("--results", default=None,
+                    help="JSON-lines file: append each result with its configuration key; a configuration already "
+                         "in the file is not run again (its stored line is printed)")
     ap.add_argument("--flags", choices=["BQxBQ", "TRSxTRA", "TRSxTRS", "CxBQ"], default="BQxBQ",
                     help="subalgebra flags of A x B (single workload)")
     ap.add_argument("--opA", choices=["N", "T", "C", "H", "QC"], default="N", help="op(A) (single workload)")
@@ -181,6 +184,38 @@ def recorded_traffic(kernel_file, workload_key, record="split_residue_gemm_traff
     return rec.get("dram_bytes_per_launch")
 
 
+def run_key(args):
+    """The configuration a result line belongs to (for --results resume)."""
+    keys = ["impl", "workload", "n", "mode", "tol", "flags", "opA", "algo", "seed", "gpus", "no_row_scale",
+            "budget_gb", "graph", "tile_table"]
+    return {k: getattr(args, k, None) for k in keys}
+
+
+def emit(args, line):
+    """Print the result line; with --results also append it (with its key) to that JSON-lines file."""
+    print(json.dumps(line), flush=True)
+    if getattr(args, "results", None):
+        with open(args.results, "a") as f:
+            f.write(json.dumps({"key": run_key(args), "line": line}) + "\n")
+
+
+def completed(args):
+    """The stored line of this configuration in --results, if any."""
+    path = getattr(args, "results", None)
+    if not path or not os.path.exists(path):
+        return None
+    key = run_key(args)
+    with open(path) as f:
+        for text in f:
+            try:
+                rec = json.loads(text)
+            except ValueError:
+                continue
+            if rec.get("key") == key:
+                return rec.get("line")
+    return None
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -236,7 +271,7 @@ def reference_arm(args, rank, world):
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    emit(args, line)
 
 
 # ----------------------------------------------------------------------------- our arm
@@ -414,7 +449,7 @@ def ours(args, rank, world, local):
                 "executed_tflops": value * size * (len(mods) * P if args.mode == "split" else P) / 64.0,
                 "naive_equiv_tflops": value * naive / 64.0,
                 "naive_equiv_note": f"counted as {naive} component-wise real GEMMs of n^3"}
-        print(json.dumps(line), flush=True)
+        emit(args, line)
     barrier(world)
     h.close()
 
@@ -489,7 +524,7 @@ def grouped(args, rank, world, local):
                            "tol": args.tol, "total_flops_64equiv": flops64,
                            "tile_table": args.tile_table, "workspace_bytes": ws_bytes},
                 "max_rel_fro_err_16_sampled": max(errs), "clocks": clk, "stages_one_step": stages}
-        print(json.dumps(line), flush=True)
+        emit(args, line)
     barrier(world)
     h.close()
 
@@ -562,7 +597,7 @@ def ops_arm(args, rank, world, local):
                              "kernel": "axpby_rows_kernel<2>",
                              "peak_source": f"hbm copy ({src})"},
                 "ops": out, "clocks": clk, "gpu_launches": args.steps * len(cases)}
-        print(json.dumps(line), flush=True)
+        emit(args, line)
     h.close()
 
 
@@ -645,12 +680,17 @@ def streamed_arm(args, rank, world, local):
                                  "sample": f"{len(rows)} of {n} output rows, {t_or:.1f} s"},
                 "stages": {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items() if v[0] > 0},
                 "gpu_launches": sum(v[0] for v in kernels.values()), "clocks": clk}
-        print(json.dumps(line), flush=True)
+        emit(args, line)
     h.close()
 
 
 def main():
     args = parse()
+    done = completed(args)
+    if done is not None:
+        if int(os.environ.get("RANK", 0)) == 0:
+            print(json.dumps(done), flush=True)
+        return
     rank, world, local = dist_init(args)
     try:
         if args.workload == "ops" and args.impl == "ours":

@@ -126,6 +126,16 @@ typedef struct {
     double *C;       int64_t ldc; int64_t strideC;
 } hmat_gemm_desc;
 
+/* Environment read by hmat_create:
+ *   HMAT_LOG=1            one line on stderr per hmat_bq_gemm /
+ *                         hmat_bq_gemm_grouped (per descriptor) /
+ *                         hmat_bq_gemm_streamed call: ops, flags, sizes,
+ *                         mode, algorithm and the returned status.
+ *   HMAT_TUNE_TABLE=file  install a tile-width table (the autotuner's JSON:
+ *                         256 codes 0..3 after a "table" key) on the new
+ *                         handle, as hmat_set_tile_table would; an unreadable
+ *                         file keeps the built-in rule and prints a warning. */
+
 /* Library version as major*10000 + minor*100 + patch. */
 int32_t hmat_version(void);
 

@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <string>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -126,6 +128,7 @@ struct hmat_context {
   cudaStream_t s_in = nullptr, s_out = nullptr;
   static constexpr int kStreamEvents = 16;
   cudaEvent_t sev[kStreamEvents] = {};
+  bool log = false;                    // HMAT_LOG: one stderr line per product call
 };
 
 namespace {
@@ -615,6 +618,64 @@ const char* hmat_status_string(hmat_status s) {
   return "unknown status";
 }
 
+namespace {
+
+// HMAT_TUNE_TABLE=<file>: a tile-width table (the autotuner's JSON: a "table"
+// key followed by 16 x 16 integer codes 0..3) installed on every new handle.
+// A file that cannot be read or parsed leaves the built-in rule and prints one
+// warning line.
+void load_env_tile_table(hmat_context* h) {
+  const char* path = std::getenv("HMAT_TUNE_TABLE");
+  if (!path || !*path) return;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) {
+    std::fprintf(stderr, "hmat: HMAT_TUNE_TABLE %s: cannot open; using the built-in tile rule\n", path);
+    return;
+  }
+  std::string text;
+  char buf[4096];
+  size_t got;
+  while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+  std::fclose(f);
+  const size_t key = text.find("\"table\"");
+  int8_t table[kTileBins * kTileBins];
+  int count = 0;
+  bool ok = key != std::string::npos;
+  for (size_t i = ok ? key + 7 : text.size(); i < text.size() && count < kTileBins * kTileBins; ++i) {
+    const char c = text[i];
+    if (c >= '0' && c <= '9') {
+      int v = 0;
+      while (i < text.size() && text[i] >= '0' && text[i] <= '9') v = 10 * v + (text[i++] - '0');
+      if (v > 3) { ok = false; break; }
+      table[count++] = (int8_t)v;
+      --i;
+    } else if (c == '-' || c == '}') {
+      ok = false;
+      break;
+    }
+  }
+  if (!ok || count != kTileBins * kTileBins) {
+    std::fprintf(stderr, "hmat: HMAT_TUNE_TABLE %s: expected %d codes 0..3 after \"table\"; using the built-in "
+                 "tile rule\n", path, kTileBins * kTileBins);
+    return;
+  }
+  std::memcpy(h->split.tile_table, table, sizeof(table));
+  h->split.has_table = true;
+}
+
+const char* kModeNames[] = {"fp64", "split"};
+const char* kAlgoNames[] = {"bilinear", "standard", "isomorph"};
+
+void log_call(const hmat_context* h, const char* fn, const hmat_gemm_desc& d, int32_t mode, hmat_status st) {
+  if (!h || !h->log) return;
+  std::fprintf(stderr, "hmat: %s op=%d,%d flags=0x%02x,0x%02x m=%lld n=%lld k=%lld mode=%s algo=%s -> %s\n", fn,
+               d.opA, d.opB, d.flagsA, d.flagsB, (long long)d.m, (long long)d.n, (long long)d.k,
+               (mode == 0 || mode == 1) ? kModeNames[mode] : "?",
+               (h->algo >= 0 && h->algo <= 2) ? kAlgoNames[h->algo] : "?", hmat_status_string(st));
+}
+
+}  // namespace
+
 hmat_status hmat_create(hmat_handle* handle) {
   if (!handle) return HMAT_STATUS_INVALID_VALUE;
   *handle = nullptr;
@@ -632,6 +693,9 @@ hmat_status hmat_create(hmat_handle* handle) {
     hmat_destroy(h);
     return cuda_status(e);
   }
+  const char* lg = std::getenv("HMAT_LOG");
+  h->log = lg && *lg && std::strcmp(lg, "0") != 0;
+  load_env_tile_table(h);
   *handle = h;
   return HMAT_STATUS_SUCCESS;
 }
@@ -716,14 +780,21 @@ hmat_status hmat_bq_gemm(hmat_handle h, int32_t opA, int32_t opB, uint32_t flags
   d.A = A; d.lda = lda; d.strideA = strideA;
   d.B = B; d.ldb = ldb; d.strideB = strideB;
   d.C = C; d.ldc = ldc; d.strideC = strideC;
-  return run(h, 1, &d, mode, tol, workspace, workspace_bytes, stream);
+  const hmat_status st = run(h, 1, &d, mode, tol, workspace, workspace_bytes, stream);
+  log_call(h, "hmat_bq_gemm", d, mode, st);
+  return st;
 }
 
 hmat_status hmat_bq_gemm_grouped(hmat_handle h, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
                                  double tol, void* workspace, size_t workspace_bytes, void* stream,
                                  int32_t use_graph) {
-  if (!use_graph) return run(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
-  return run_graph(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
+  const hmat_status st = use_graph ? run_graph(h, count, descs, mode, tol, workspace, workspace_bytes, stream)
+                                   : run(h, count, descs, mode, tol, workspace, workspace_bytes, stream);
+  if (h && h->log) {
+    for (int32_t i = 0; i < count && descs; ++i) log_call(h, use_graph ? "hmat_bq_gemm_grouped[graph]" :
+                                                               "hmat_bq_gemm_grouped", descs[i], mode, st);
+  }
+  return st;
 }
 
 hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
@@ -1182,11 +1253,37 @@ hmat_status hmat_streamed_plan(hmat_handle h, int32_t opA, int32_t opB, uint32_t
   return HMAT_STATUS_SUCCESS;
 }
 
+namespace {
+hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
+                          int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A, int64_t lda,
+                          int64_t strideA, const double* B, int64_t ldb, int64_t strideB, double beta_re,
+                          double beta_im, double* C, int64_t ldc, int64_t strideC, int32_t mode, double tol,
+                          void* workspace, size_t workspace_bytes, void* stream);
+}  // namespace
+
 hmat_status hmat_bq_gemm_streamed(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                                   int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A,
                                   int64_t lda, int64_t strideA, const double* B, int64_t ldb, int64_t strideB,
                                   double beta_re, double beta_im, double* C, int64_t ldc, int64_t strideC,
                                   int32_t mode, double tol, void* workspace, size_t workspace_bytes, void* stream) {
+  const hmat_status st = streamed_impl(h, opA, opB, flagsA, flagsB, m, n, k, alpha_re, alpha_im, A, lda, strideA, B,
+                                       ldb, strideB, beta_re, beta_im, C, ldc, strideC, mode, tol, workspace,
+                                       workspace_bytes, stream);
+  if (h && h->log) {
+    hmat_gemm_desc d;
+    std::memset(&d, 0, sizeof(d));
+    d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB; d.m = m; d.n = n; d.k = k;
+    log_call(h, "hmat_bq_gemm_streamed", d, mode, st);
+  }
+  return st;
+}
+
+namespace {
+hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
+                          int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A, int64_t lda,
+                          int64_t strideA, const double* B, int64_t ldb, int64_t strideB, double beta_re,
+                          double beta_im, double* C, int64_t ldc, int64_t strideC, int32_t mode, double tol,
+                          void* workspace, size_t workspace_bytes, void* stream) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
   hmat_gemm_desc d;
   d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB;
@@ -1346,5 +1443,6 @@ hmat_status hmat_bq_gemm_streamed(hmat_handle h, int32_t opA, int32_t opB, uint3
   if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fin, 0);
   return cuda_status(e);
 }
+}  // namespace
 
 }  // extern "C"

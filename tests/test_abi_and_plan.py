@@ -191,3 +191,26 @@ def test_streamed_plan_fits_budget_and_prefers_whole_k():
     with pytest.raises(hm.HmatError) as ei:
         hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 20)
     assert ei.value.status == 4
+
+
+def test_bench_results_file_resume(tmp_path):
+    """bench.py --results: a configuration already in the file is not run again."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = tmp_path / "results.jsonl"
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--n", "24", "--steps", "1",
+           "--warmup", "0", "--results", str(res)]
+    first = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root)
+    assert first.returncode == 0, first.stderr
+    line1 = json.loads(first.stdout.strip().splitlines()[-1])
+    assert len(res.read_text().strip().splitlines()) == 1
+    second = subprocess.run(cmd, capture_output=True, text=True, timeout=300, cwd=root)
+    assert second.returncode == 0, second.stderr
+    assert json.loads(second.stdout.strip().splitlines()[-1]) == line1
+    assert len(res.read_text().strip().splitlines()) == 1          # not run again
+    third = subprocess.run(cmd[:-2] + ["--seed", "7", "--results", str(res)], capture_output=True, text=True,
+                           timeout=300, cwd=root)
+    assert third.returncode == 0, third.stderr
+    assert len(res.read_text().strip().splitlines()) == 2          # another key runs
