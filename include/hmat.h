@@ -326,7 +326,8 @@ hmat_status hmat_streamed_plan(hmat_handle handle, int32_t opA, int32_t opB, uin
  * returns once everything is enqueued; host buffers must stay valid and
  * untouched until `stream` has completed the call.  The handle's copy streams
  * and events are created on first use; streamed calls on one handle must not
- * run concurrently from several host threads.
+ * run concurrently from several host threads.  When the call fails after
+ * queueing copies, `stream` still completes only after them.
  * Errors: as hmat_bq_gemm; WORKSPACE_TOO_SMALL when no block plan fits. */
 hmat_status hmat_bq_gemm_streamed(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                                   int64_t m, int64_t n, int64_t k,

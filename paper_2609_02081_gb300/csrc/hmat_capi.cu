@@ -1269,6 +1269,14 @@ hmat_status hmat_bq_gemm_streamed(hmat_handle h, int32_t opA, int32_t opB, uint3
   const hmat_status st = streamed_impl(h, opA, opB, flagsA, flagsB, m, n, k, alpha_re, alpha_im, A, lda, strideA, B,
                                        ldb, strideB, beta_re, beta_im, C, ldc, strideC, mode, tol, workspace,
                                        workspace_bytes, stream);
+  if (st != HMAT_STATUS_SUCCESS && h && h->s_in && h->s_out) {
+    // copies queued before the failure may still touch the host buffers: the
+    // caller's stream completes only after them
+    cudaStream_t cs = static_cast<cudaStream_t>(stream);
+    if (cudaEventRecord(h->sev[15], h->s_in) == cudaSuccess) (void)cudaStreamWaitEvent(cs, h->sev[15], 0);
+    if (cudaEventRecord(h->sev[14], h->s_out) == cudaSuccess) (void)cudaStreamWaitEvent(cs, h->sev[14], 0);
+    (void)cudaGetLastError();
+  }
   if (h && h->log) {
     hmat_gemm_desc d;
     std::memset(&d, 0, sizeof(d));
