@@ -169,7 +169,9 @@ hmat_status hmat_workspace_size(hmat_handle handle, int32_t count,
  *   (may be NULL/0 for FP64).  stream: cudaStream_t or NULL.
  * m, n or k == 0 returns SUCCESS after, for k == 0, scaling C by beta.
  * Errors: NOT_INITIALIZED, INVALID_VALUE, MISALIGNED, WORKSPACE_TOO_SMALL,
- * TOLERANCE_UNREACHABLE, UNSUPPORTED, CUDA_ERROR. */
+ * TOLERANCE_UNREACHABLE, UNSUPPORTED (any dimension above 2^30; in split
+ * mode also m k or k n at or above 2^31, where one factor plane of the
+ * encoded operand would exceed 4 GB: use hmat_bq_gemm_streamed), CUDA_ERROR. */
 hmat_status hmat_bq_gemm(hmat_handle handle, int32_t opA, int32_t opB,
                          uint32_t flagsA, uint32_t flagsB,
                          int64_t m, int64_t n, int64_t k,

@@ -1202,6 +1202,7 @@ hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d
       bd.m = p.mb; bd.n = p.nb; bd.k = d.k > 0 ? p.kb : 0;
       size_t ws = 0;
       hmat_status st = workspace_bytes(algo, table, 1, &bd, mode, tol, &ws);
+      if (st == HMAT_STATUS_UNSUPPORTED) continue;    // a block too large for one split product
       if (st != HMAT_STATUS_SUCCESS) return st;
       p.ws = align_up256((int64_t)ws);
       p.total = 2 * (p.a_blk + p.b_blk + p.c_blk) + p.ws;

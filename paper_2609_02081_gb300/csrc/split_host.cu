@@ -168,6 +168,8 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
   // the same memory channels and cache sets).
   sj->encA_plane = (int64_t)sj->tiles_m * sj->nkb * kTileM * kTileK * 2 + kPlaneSkewEnc;
   sj->encB_plane = (int64_t)sj->tiles_n * sj->nkb * sj->bn * kTileK * 2 + kPlaneSkewEnc;
+  // the encoder addresses a factor plane with a 32-bit stride (m k or k n below 2^31)
+  if (sj->encA_plane >= ((int64_t)1 << 32) || sj->encB_plane >= ((int64_t)1 << 32)) return HMAT_STATUS_UNSUPPORTED;
   sj->res_plane = ((int64_t)sj->tiles_m * kTileM) * ((int64_t)sj->tiles_n * sj->bn) + kPlaneSkewRes;
   int64_t off = *offset;
   sj->off_sexp = off;

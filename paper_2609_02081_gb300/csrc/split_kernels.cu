@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
     float w = 0.f;
     if (gi < ng) {
       const int8_t* cf = c < 4 ? (side ? P.rre[gi] : P.lre[gi]) : (side ? P.rim[gi] : P.lim[gi]);
-      w = (float)(cf[c & 3] * sign[c]);
+      w = (float)cf[c & 3];          // the op signs are folded into the staged integers
     }
     s_coef[gi][c] = w;
   } else if (t < 64 + 24) {
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
     s_slot[gi][part] = gi < ng ? (side ? P.rslot[gi][part] : P.lslot[gi][part]) : -1;
   }
   __syncthreads();
-  // phase 1: stage scaled integers (reads coalesced along the contiguous index)
+  // phase 1: stage scaled integers, op sign applied (reads coalesced along the contiguous index)
   for (int idx = t; idx < 8 * kEncK * kEncRows; idx += kEncThreads) {
     const int c = idx / (kEncK * kEncRows);
     const int rem = idx % (kEncK * kEncRows);
@@ -284,6 +284,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
       const int64_t off = contiguous ? (int64_t)r * ld + kg : (int64_t)kg * ld + r;
       const unsigned long long bits = (unsigned long long)__double_as_longlong(__ldg(base + (int64_t)c * cs + off));
       X = scaled_int(bits, s_row[rr]);
+      if (sign[c] < 0) X = -X;
     }
     if (LIMBS == 2) {
       xs[c][kk][rr][0] = (float)(int)(X & 0x7FFFFF);
@@ -305,7 +306,9 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
   const int rt = r / tile_rows, rin = r % tile_rows;
   const int nf = side ? sj.nrf : sj.nlf;
   const int64_t tile_bytes = (int64_t)tile_rows * kTileK * 2;
-  const int64_t plane_bytes = side ? sj.encB_plane : sj.encA_plane;
+  // plane strides are below 2^32 (checked on the host), so a factor plane's
+  // offset is one 32 x 32 -> 64-bit multiply
+  const uint32_t plane_bytes = (uint32_t)(side ? sj.encB_plane : sj.encA_plane);
   unsigned char* enc = ws + (side ? sj.off_encB : sj.off_encA) + ((int64_t)rt * sj.nkb + kb) * tile_bytes +
                        (int64_t)(rin >> 3) * 1024 + (rin & 7) * 128 + ((c16 ^ (rin & 7)) << 4) + half8;
 
@@ -313,9 +316,6 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
   if (butterfly) {
     // the eight complex factors of Eq. bilinearH: four single coefficients and the
     // four Hadamard rows (two butterfly stages); each emits Re, Im and Re+Im
-    float sg[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) sg[c] = (float)sign[c];
     // single-coefficient groups: left a1, a4, a2, a3; right b1, b3, b4, b2
     const int pick0 = 0, pick1 = side ? 2 : 3, pick2 = side ? 3 : 1, pick3 = side ? 1 : 2;
     // reduced: re and im are residues already (the single-coefficient groups);
@@ -325,7 +325,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
       if (f < 0) return;
       const uint2 pkd = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
                                    __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
-      *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pkd;
+      *reinterpret_cast<uint2*>(enc + (uint64_t)(uint32_t)(l * nf + f) * plane_bytes) = pkd;
     };
     auto emit = [&](int gi, const float (&re)[4], const float (&im)[4], int l, const ModConst& mc, bool reduced) {
       float v0[4], v1[4], v2[4];
@@ -346,8 +346,8 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
       for (int e = 0; e < 4; ++e)
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          xr[e][q] = sg[e] * residue_of<LIMBS>(xs[e][k4 * 4 + q][rr], mc);
-          xi[e][q] = sg[e + 4] * residue_of<LIMBS>(xs[e + 4][k4 * 4 + q][rr], mc);
+          xr[e][q] = residue_of<LIMBS>(xs[e][k4 * 4 + q][rr], mc);
+          xi[e][q] = residue_of<LIMBS>(xs[e + 4][k4 * 4 + q][rr], mc);
         }
       const int pk[4] = {pick0, pick1, pick2, pick3};
 #pragma unroll
@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
         // |v| <= 128 is exact in BF16, whose bits are the upper half of the float's
         const uint2 pk = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
                                     __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
-        *reinterpret_cast<uint2*>(enc + ((int64_t)l * nf + f) * plane_bytes) = pk;
+        *reinterpret_cast<uint2*>(enc + (uint64_t)(uint32_t)(l * nf + f) * plane_bytes) = pk;
       }
     }
   }
