@@ -214,3 +214,28 @@ def test_bench_results_file_resume(tmp_path):
                            timeout=300, cwd=root)
     assert third.returncode == 0, third.stderr
     assert len(res.read_text().strip().splitlines()) == 2          # another key runs
+
+
+def _build_c_client(out_dir):
+    """Compile tests/c_abi_client.c against include/hmat.h and libhmat.so with the host C compiler."""
+    import shutil
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    cuda = "/usr/local/cuda"
+    libdir = os.path.dirname(hm.library_path())
+    exe = os.path.join(str(out_dir), "c_abi_client")
+    cmd = [cc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-O2", "-I", os.path.join(root, "include"),
+           "-I", os.path.join(cuda, "include"), os.path.join(root, "tests", "c_abi_client.c"), "-L", libdir,
+           "-lhmat", "-L", os.path.join(cuda, "lib64"), "-lcudart", "-Wl,-rpath," + libdir, "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    return exe
+
+
+def test_c_client_compiles_against_the_header(tmp_path):
+    """The header is valid C11 and a C program links against libhmat.so (run on the GPU in test_gpu_c_abi)."""
+    hm.lib()
+    assert os.path.exists(_build_c_client(tmp_path))
