@@ -147,8 +147,13 @@ const char *hmat_status_string(hmat_status s);
 const char *hmat_last_cuda_error(void);
 
 /* Create a handle bound to the current CUDA device.  Allocates host-side
- * state only (pinned staging for grouped descriptors).  Errors:
- * INVALID_VALUE (NULL out pointer), CUDA_ERROR. */
+ * state only (pinned staging for grouped descriptors).  The first handle on a
+ * device also sets the kernels' attributes and uploads the constant tables
+ * (moduli, CRT basis) for that device, once per process and thread-safe;
+ * handles may be created and used from several host threads (one thread per
+ * handle at a time).  A process that resets a device (cudaDeviceReset) must
+ * not use the library on it afterwards.  Errors: INVALID_VALUE (NULL out
+ * pointer), CUDA_ERROR. */
 hmat_status hmat_create(hmat_handle *handle);
 
 /* Destroy a handle (NULL is accepted).  Synchronises nothing; the caller
@@ -268,7 +273,10 @@ hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
 /* Read and clear the device error word (0 = none; otherwise a bit mask:
  * 0x1 producer, 0x2 MMA issuer, 0x4 epilogue wait of the residue GEMM gave
  * up; 0x10 split mode met an Inf/NaN input; 0x20 the self-test wait gave up).
- * Synchronises the device. */
+ * Synchronises the device.  The word is one per device and process, shared by
+ * all handles on that device: a handle reads (and clears) bits that work of
+ * any handle set.  Errors: NOT_INITIALIZED, INVALID_VALUE (NULL code, or
+ * another device current), CUDA_ERROR. */
 hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
 
 /* Tile-width table for split mode (written by the autotuner,

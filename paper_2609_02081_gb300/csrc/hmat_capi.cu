@@ -21,8 +21,15 @@ namespace hmat {
 
 __device__ uint32_t g_hmat_device_error = 0;
 
-static uint32_t* g_err_ptr = nullptr;
-uint32_t* device_error_ptr() { return g_err_ptr; }
+// Device address of the error word on each device (set once per device by
+// configure_device); launches take the current device's.
+constexpr int kMaxConfigDevices = 64;
+static uint32_t* g_err_ptrs[kMaxConfigDevices] = {};
+uint32_t* device_error_ptr() {
+  int d = -1;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxConfigDevices) return nullptr;
+  return g_err_ptrs[d];
+}
 
 // Fixed device scratch for hmat_bq_gemm_split_noalloc: the split-mode
 // workspace (scale exponents, encoded factor tiles, product residues) and the
@@ -620,6 +627,27 @@ const char* hmat_status_string(hmat_status s) {
 
 namespace {
 
+// Kernel attributes and the constant tables (moduli, CRT basis) are per
+// device and the same for every handle: set once per device and process.
+// Re-uploading constant memory for each new handle could race with kernels of
+// another handle still running on that device.
+std::mutex g_config_mu;
+bool g_configured[kMaxConfigDevices] = {};
+
+cudaError_t configure_device(int device) {
+  if (device < 0 || device >= kMaxConfigDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_config_mu);
+  if (g_configured[device]) return cudaSuccess;
+  void* err = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&err, g_hmat_device_error);
+  if (e == cudaSuccess) g_err_ptrs[device] = static_cast<uint32_t*>(err);
+  if (e == cudaSuccess) e = fp64_configure();
+  if (e == cudaSuccess) e = split_configure();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();   // the uploads are complete before any product
+  if (e == cudaSuccess) g_configured[device] = true;
+  return e;
+}
+
 // HMAT_TUNE_TABLE=<file>: a tile-width table (the autotuner's JSON: a "table"
 // key followed by 16 x 16 integer codes 0..3) installed on every new handle.
 // A file that cannot be read or parsed leaves the built-in rule and prints one
@@ -686,9 +714,7 @@ hmat_status hmat_create(hmat_handle* handle) {
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_plans, kPlanSlots * sizeof(KPlan));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_plans, kPlanSlots * sizeof(KPlan));
   for (int i = 0; e == cudaSuccess && i < kStageSlots; ++i) e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaGetSymbolAddress(reinterpret_cast<void**>(&g_err_ptr), g_hmat_device_error);
-  if (e == cudaSuccess) e = fp64_configure();
-  if (e == cudaSuccess) e = split_configure();
+  if (e == cudaSuccess) e = configure_device(h->device);
   if (e != cudaSuccess) {
     hmat_destroy(h);
     return cuda_status(e);
@@ -890,6 +916,8 @@ hmat_status hmat_split_info(int64_t k, double tol, int32_t* n_moduli, int32_t* m
 hmat_status hmat_get_device_error(hmat_handle h, uint32_t* code) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
   if (!code) return HMAT_STATUS_INVALID_VALUE;
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) return HMAT_STATUS_INVALID_VALUE;
   cudaError_t e = cudaDeviceSynchronize();
   if (e == cudaSuccess) e = cudaMemcpyFromSymbol(code, g_hmat_device_error, sizeof(uint32_t));
   if (e == cudaSuccess) {

@@ -76,8 +76,8 @@ uint32_t inv_mod(uint32_t a, uint32_t m) {
 }  // namespace
 
 cudaError_t split_configure() {
-  static uint32_t crt[kMaxModuli + 1][kMaxModuli][kLimbs];
-  static uint32_t P[kMaxModuli + 1][kLimbs];
+  uint32_t crt[kMaxModuli + 1][kMaxModuli][kLimbs];
+  uint32_t P[kMaxModuli + 1][kLimbs];
   std::memset(crt, 0, sizeof(crt));
   std::memset(P, 0, sizeof(P));
   for (int n = 1; n <= kMaxModuli; ++n) {

@@ -302,3 +302,37 @@ def test_comparison_algorithms_random_and_grouped(handle, algo, mode):
                 assert rel(C.cpu().numpy(), want) <= (1e-14 if mode == "fp64" else TOL)
     finally:
         handle.set_algorithm("bilinear")
+
+
+def test_two_threads_two_handles_concurrently():
+    """Separate handles on separate streams from two host threads (ctypes releases the GIL)."""
+    import threading
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    dev = torch.device("cuda", 0)
+    results, errors = {}, []
+    cases = {t: (bi.small_int(700 + t, 150, 170), bi.small_int(710 + t, 170, 130)) for t in range(2)}
+
+    def worker(t):
+        try:
+            torch.cuda.set_device(dev)
+            stream = torch.cuda.Stream()
+            A, B = (x.to(dev) for x in cases[t])
+            C = torch.empty((8, 150, 130), dtype=torch.float64, device=dev)
+            with hm.Handle() as h, torch.cuda.stream(stream):
+                for _ in range(5):
+                    hm.hmat_bq_gemm(h, A, B, C, mode="split" if t else "fp64", tol=TOL, stream=stream)
+                stream.synchronize()
+            results[t] = C.cpu().numpy()
+        except Exception as e:          # reported below
+            errors.append(e)
+
+    threads = [threading.Thread(target=worker, args=(t,)) for t in range(2)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join(timeout=120)
+    assert not errors, errors
+    for t in range(2):
+        A, B = cases[t]
+        np.testing.assert_array_equal(results[t], oracle.bq_gemm(A.numpy(), B.numpy()))
