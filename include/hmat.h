@@ -45,7 +45,7 @@ extern "C" {
 typedef enum {
     HMAT_STATUS_SUCCESS = 0,
     HMAT_STATUS_INVALID_VALUE = 1,      /* bad size, op, flag, mode or pointer */
-    HMAT_STATUS_UNSUPPORTED = 2,        /* valid request this build cannot serve */
+    HMAT_STATUS_UNSUPPORTED = 2,        /* valid request the library does not serve */
     HMAT_STATUS_MISALIGNED = 3,         /* a pointer or stride violates alignment */
     HMAT_STATUS_WORKSPACE_TOO_SMALL = 4,/* workspace smaller than hmat_workspace_size() */
     HMAT_STATUS_CUDA_ERROR = 5,         /* a CUDA runtime call failed */

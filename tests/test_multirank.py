@@ -1,7 +1,7 @@
 """bench.py's multi-rank host logic on CPU: two gloo ranks (no GPU needed).
 
 Every rank of `bench.py --gpus N` runs an independent replica of the product
-(the path does not shard: DESIGN.md "replicas only"); ranks meet at barriers,
+(the product does not shard: replicas only); ranks meet at barriers,
 the step time is the maximum over ranks and only rank 0 prints.  Here the
 helpers are driven by two real processes over gloo on 127.0.0.1.
 """
