@@ -16,9 +16,10 @@
 // GB300 note: FP64 FMA throughput is 2 per clock per SM (1.2 TFLOP/s measured),
 // so a warp-wide DFMA occupies an SM sub-partition's FP64 pipe for 64 clocks;
 // the kernel is bound by that pipe alone.  What matters is the count of FP64
-// operations that are not product FMAs (pre-additions ~8% at 32x32 tiles) and
-// keeping the pipe fed: 24 accumulators per output point cap the tile at
-// 32x32 per SM (24 x 1024 doubles = 192 KB of registers).
+// operations that are not product FMAs (pre-additions and recombination: 17%
+// of the FP64 instructions at 32x32 tiles, measured) and keeping the pipe fed:
+// 24 accumulators per output point cap the tile at 32x32 per SM
+// (24 x 1024 doubles = 192 KB of registers).
 #include <cuda_runtime.h>
 
 #include "common.cuh"
