@@ -9,6 +9,17 @@ eight real components [M1..M8] = [E_R, E_I, F_R, F_I, G_I, -G_R, H_I, -H_R] of
 a biquaternion matrix (arXiv 2609.02081, Sec. III), each component row-major
 (last stride 1); ``stride(1)`` is the leading dimension, ``stride(0)`` the
 component stride.
+
+    import paper_2609_02081_gb300 as hm
+    with hm.Handle() as h:
+        hm.hmat_bq_gemm(h, A, B, C, "N", "H", mode="split", tol=1e-12)   # C = A B^dagger
+        hm.hmat_bq_gemm_grouped(h, [hm.make_desc(A1, B1, C1), hm.make_desc(A2, B2, C2)],
+                                mode="split", tol=1e-12, use_graph=True)
+        hm.hmat_bq_gemm_streamed(h, A_host, B_host, C_host, mode="split", tol=1e-12,
+                                 budget=64 << 30)                        # pinned host operands
+        hm.hmat_bq_add(h, A, B, C, alpha=1.0, beta=1j)                  # C = A + i B
+        Z = hm.hmat_bq_to_complex(h, A)                                 # complex 2m x 2n image
+        h.set_algorithm("standard")                                     # comparison algorithms
 """
 from __future__ import annotations
 
