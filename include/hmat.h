@@ -314,11 +314,16 @@ hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, v
 
 /* Block sizes and device bytes the streamed product uses for a device
  * budget of `budget` bytes, with kb = k if anything fits, else k halved
- * (rounded to 64) until something does.  Shapes in order of preference: when
- * an operand is host-resident (and n >= 512), column panels mb = m,
- * nb = n/4 then n/2 (A copied and encoded once; B and C panels stream behind
- * the products); then square blocks mb = nb from the whole matrix down to 128
- * (multiples of 128 unless the matrix is smaller).  *_on_host: whether each operand is
+ * (rounded to 64) until something does.  Shapes in order of preference when
+ * an operand is host-resident: in split mode (min(m, n) >= 512, built-in tile
+ * rule) square blocks of about m/4 x n/4 down to 256 with every column block's
+ * encoded B side kept in the budget, so each block row of A and each column
+ * block of B is copied and encoded once and only the first A and B blocks
+ * precede the first product; then column panels mb = m, nb = n/4 then n/2
+ * (n >= 512; A copied and encoded once, B and C panels stream behind the
+ * products); then square blocks mb = nb from the whole matrix down to 128
+ * (multiples of 128 unless the matrix is smaller), the only candidates when
+ * every operand is in device memory.  *_on_host: whether each operand is
  * host-resident (streamed) or device-resident (read in place).  Host-only;
  * handle may be NULL (then the default algorithm and tile rule).
  * Errors: INVALID_VALUE, WORKSPACE_TOO_SMALL (nothing fits),

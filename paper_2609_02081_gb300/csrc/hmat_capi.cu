@@ -480,11 +480,20 @@ hmat_status launch_iso_out(hmat_context* h, const Prepared& pr, cudaStream_t str
   return HMAT_STATUS_SUCCESS;
 }
 
-// reuse_a: the workspace still holds the A-side split-mode data (exponents and
-// encoded factor tiles) of the previous call, made from the same A block with
-// the same shape (streamed products set it; never for the isomorph route).
+// Split-mode data a streamed product shares between calls (one product per
+// call, never the isomorph route).  a: the workspace still holds the A side
+// (exponents, encoded factor tiles) of the previous call, made from the same A
+// block with the same shape.  b_offset >= 0: the B side lives at that byte
+// offset of the workspace instead of its own layout slot; b_cached: it already
+// holds this B block's data from an earlier call with the same shape.
+struct SplitReuse {
+  bool a = false;
+  int64_t b_offset = -1;
+  bool b_cached = false;
+};
+
 hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                void* workspace, size_t ws_bytes, void* stream_ptr, bool reuse_a = false) {
+                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse = SplitReuse{}) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
   std::lock_guard<std::mutex> lock(h->mu);
@@ -493,7 +502,13 @@ hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int
   Prepared pr;
   hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr);
   if (st != HMAT_STATUS_SUCCESS) return st;
-  if (reuse_a && pr.has_split && pr.sp.jobs.size() == 1 && h->algo != HMAT_ALGO_ISOMORPH) pr.sp.reuse_a = true;
+  if (pr.has_split && pr.sp.jobs.size() == 1 && h->algo != HMAT_ALGO_ISOMORPH) {
+    pr.sp.reuse_a = reuse.a;
+    if (reuse.b_offset >= 0) {
+      split_place_b(pr.sp.jobs[0], reuse.b_offset);
+      pr.sp.reuse_b = reuse.b_cached;
+    }
+  }
   st = launch_iso_in(h, pr, stream);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (pr.has_split) {
@@ -1190,6 +1205,8 @@ struct StreamedPlan {
   int64_t mb = 0, nb = 0, kb = 0;
   int64_t a_blk = 0, b_blk = 0, c_blk = 0;   // bytes of one device slot (0: operand read in place)
   int64_t ws = 0;                            // product workspace of the largest block
+  int64_t b_region = 0;                      // split mode with a B cache: bytes per column block
+  int64_t n_jblocks = 0;                     // (0: no cache)
   int64_t total = 0;
 };
 
@@ -1216,6 +1233,42 @@ hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d
   for (int64_t b = round_up(top, 128); b >= 128; b = round_up(b / 2, 128)) {
     shapes.push_back({b, b});
     if (b == 128) break;
+  }
+  // Split mode with a host-resident operand and the whole k: first try square
+  // blocks of about a quarter of m and n with every column block's B side
+  // (exponents and encoded tiles) kept in the budget.  Each A block row and
+  // each B column block is then copied and encoded once, and only the first
+  // A and B blocks are copied before the first product.
+  // (Only under the built-in tile rule, whose width depends on n alone: a tuned
+  // table could give a ragged last block row another width than the cached B.)
+  if (mode == HMAT_MODE_SPLIT && algo != HMAT_ALGO_ISOMORPH && (a_host || b_host || c_host) && d.k > 0 &&
+      std::min(m, n) >= 512 && table == nullptr) {
+    KPlan kp;
+    if (!build_plan(d.flagsA, d.flagsB, &kp, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
+      return HMAT_STATUS_INTERNAL;
+    for (int64_t b = round_up((std::min(m, n) + 3) / 4, 128); b >= 256 && kp.np > 0; b = round_up(b / 2, 128)) {
+      StreamedPlan p;
+      p.mb = std::min(m, b);
+      p.nb = std::min(n, b);
+      p.kb = k;
+      p.a_blk = a_host ? blk_bytes(p.mb, p.kb) : 0;
+      p.b_blk = b_host ? blk_bytes(p.kb, p.nb) : 0;
+      p.c_blk = c_host ? blk_bytes(p.mb, p.nb) : 0;
+      hmat_gemm_desc bd = d;
+      bd.m = p.mb; bd.n = p.nb; bd.k = p.kb;
+      size_t ws = 0;
+      hmat_status st = workspace_bytes(algo, table, 1, &bd, mode, tol, &ws);
+      if (st == HMAT_STATUS_UNSUPPORTED) continue;
+      if (st != HMAT_STATUS_SUCCESS) return st;
+      int64_t region = 0;
+      st = split_b_region_bytes(SplitShape{p.mb, p.nb, p.kb, kp.np, kp.nlf, kp.nrf}, tol, table, &region);
+      if (st != HMAT_STATUS_SUCCESS) return st;
+      p.ws = align_up256((int64_t)ws);
+      p.b_region = align_up256(region);
+      p.n_jblocks = (n + p.nb - 1) / p.nb;
+      p.total = 2 * (p.a_blk + p.b_blk + p.c_blk) + p.ws + p.n_jblocks * p.b_region;
+      if ((size_t)p.total <= budget) { *out = p; return HMAT_STATUS_SUCCESS; }
+    }
   }
   for (int64_t kb : kbs) {
     for (const auto& sh : shapes) {
@@ -1354,6 +1407,7 @@ hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flag
   double* c_slot[2] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + p.c_blk)};
   base += 2 * p.c_blk;
   void* ws = base;
+  const bool b_cache = p.n_jblocks > 0;      // B sides of the column blocks at ws + p.ws + J * p.b_region
   // events: A ready/free, B ready/free, C ready/computed/stored (two slots each) + final
   cudaEvent_t* ev = h->sev;
   cudaEvent_t a_ready[2] = {ev[0], ev[1]}, a_free[2] = {ev[2], ev[3]};
@@ -1430,7 +1484,11 @@ hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flag
           }
         }
         int bcur = -1;
-        if (need_ab && flagsB) {
+        const bool b_reused = b_cache && i0 > 0;  // encoded by the first block row
+        if (need_ab && flagsB && b_reused) {
+          bd.B = b_host ? b_slot[0] : (tb ? B + j0 * ldb + k0 : B + k0 * ldb + j0);   // not read
+          if (b_host) { bd.ldb = tb ? kb : nb; bd.strideB = (tb ? nb : kb) * (tb ? kb : nb); }
+        } else if (need_ab && flagsB) {
           const int64_t sr = tb ? nb : kb, sc = tb ? kb : nb;
           const double* src = tb ? B + j0 * ldb + k0 : B + k0 * ldb + j0;
           if (b_host) {
@@ -1450,8 +1508,13 @@ hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flag
           }
         }
         const int64_t key[5] = {i0, k0, mb, nb, kb};
-        const bool reuse = mode == HMAT_MODE_SPLIT && need_ab && flagsA && std::equal(key, key + 5, prev);
-        st = run(h, 1, &bd, mode, tol, ws, (size_t)p.ws, stream, reuse);
+        SplitReuse reuse;
+        reuse.a = mode == HMAT_MODE_SPLIT && need_ab && flagsA && std::equal(key, key + 5, prev);
+        if (b_cache) {
+          reuse.b_offset = p.ws + (j0 / p.nb) * p.b_region;
+          reuse.b_cached = b_reused;
+        }
+        st = run(h, 1, &bd, mode, tol, ws, (size_t)(p.ws + p.n_jblocks * p.b_region), stream, reuse);
         if (st != HMAT_STATUS_SUCCESS) return st;
         std::copy(key, key + 5, prev);
         if (a_host && need_ab && flagsA) {

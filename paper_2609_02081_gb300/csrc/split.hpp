@@ -106,7 +106,18 @@ struct SplitPrep {
   // one job whose A-side exponents and encoded factor tiles are already in the
   // workspace from the previous call with the same A block and the same shape
   bool reuse_a = false;
+  // one job whose B-side exponents and encoded tiles (at the job's off_texp /
+  // off_encB, see split_place_b) are already there from an earlier call with
+  // the same B block and the same shape
+  bool reuse_b = false;
 };
+
+// Bytes of a job's B side (column exponents and encoded right factors), the
+// region split_place_b points a job at.
+hmat_status split_b_region_bytes(const SplitShape& sh, double tol, const int8_t* table, int64_t* bytes);
+// Point the job's B side at `offset` (bytes into the split workspace) instead
+// of its own layout slot.
+void split_place_b(SplitJob& sj, int64_t offset);
 
 // Lay the jobs out in a workspace of ws_bytes (WORKSPACE_TOO_SMALL if it does not fit).
 hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,

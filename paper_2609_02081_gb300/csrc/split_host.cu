@@ -186,6 +186,21 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
   return HMAT_STATUS_SUCCESS;
 }
 
+hmat_status split_b_region_bytes(const SplitShape& sh, double tol, const int8_t* table, int64_t* bytes) {
+  SplitJob sj;
+  std::memset(&sj, 0, sizeof(sj));
+  int64_t off = 0;
+  hmat_status st = layout_job(sh, nullptr, tol, table, &sj, &off);
+  if (st != HMAT_STATUS_SUCCESS) return st;
+  *bytes = align256(4 * sh.n) + align256((int64_t)sj.nmod * sj.nrf * sj.encB_plane);
+  return HMAT_STATUS_SUCCESS;
+}
+
+void split_place_b(SplitJob& sj, int64_t offset) {
+  sj.off_texp = offset;
+  sj.off_encB = offset + align256(4 * (int64_t)sj.d.n);
+}
+
 hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const int8_t* table,
                                   size_t* bytes) {
   int64_t off = 0;
@@ -256,18 +271,22 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
                          unsigned char* ws, cudaStream_t stream) {
   const int njobs = (int)sp.jobs.size();
   cudaError_t e;
-  // with reuse_a (one job) the A units come first in both stages and are skipped
-  const bool skip_a = sp.reuse_a && njobs == 1;
+  // with reuse_a / reuse_b (one job) the A units, which come first in the
+  // exponent stage, or the B units after them, are skipped, and so is that
+  // side's encoder launch
+  const bool skip_a = sp.reuse_a && njobs == 1, skip_b = sp.reuse_b && njobs == 1;
   {
     ProfScope ps(h, 1, stream);
-    const int64_t first = skip_a ? (sp.jobs[0].d.m + 31) / 32 : 0;
-    e = launch_split_exponents(d_jobs, njobs, sp.exp_units, first, stream, ws);
+    const int64_t a_units = njobs == 1 ? (sp.jobs[0].d.m + 31) / 32 : 0;
+    const int64_t first = skip_a ? a_units : 0, end = skip_b ? a_units : sp.exp_units;
+    e = launch_split_exponents(d_jobs, njobs, end, first, stream, ws);
   }
   if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 2, stream);
     if (!skip_a) e = launch_split_encode(d_jobs, njobs, d_plans, 0, sp.encA_units, stream, ws, sp.max_bits);
-    if (e == cudaSuccess) e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws, sp.max_bits);
+    if (e == cudaSuccess && !skip_b)
+      e = launch_split_encode(d_jobs, njobs, d_plans, 1, sp.encB_units, stream, ws, sp.max_bits);
   }
   if (e != cudaSuccess) return split_cuda_error(e);
   {

@@ -178,8 +178,10 @@ def test_streamed_plan_fits_budget_and_prefers_whole_k():
         if prev is not None:
             assert mb * nb * kb <= prev
         prev = mb * nb * kb
-    # host-resident operands: column panels (A copied and encoded once); device-resident: one block
-    assert hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 40)[:3] == (m, n // 4, k)
+    # host-resident operands, split mode: quarter blocks with the B sides cached (each operand block
+    # copied and encoded once); FP64 mode: column panels; device-resident operands: one block
+    assert hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 40)[:3] == (m // 4, n // 4, k)
+    assert hm.streamed_plan(m, n, k, mode="fp64", budget=1 << 40)[:3] == (m, n // 4, k)
     assert hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 40,
                             on_host=(False, False, False))[:3] == (m, n, k)
     assert hm.streamed_plan(m, n, k, mode="fp64", budget=1 << 30)[2] == k     # FP64: only slots, k stays whole

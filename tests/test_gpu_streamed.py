@@ -144,3 +144,31 @@ def test_streamed_degenerate_shapes(handle, mode):
     C0e = torch.empty((8, 0, 1), dtype=torch.float64).pin_memory()
     hm.hmat_bq_gemm_streamed(handle, A0, bi.uniform(443, 10, 1).pin_memory(), C0e, mode=mode, tol=TOL,
                              budget=64 << 20)
+
+
+@pytest.mark.parametrize("opA,opB,fa,fb", [("N", "N", bi.BQ, bi.BQ), ("H", "T", bi.TRS, bi.TRA),
+                                           ("C", "N", bi.BQ, bi.COMPLEX)])
+def test_streamed_b_cache_equals_in_core(handle, opA, opB, fa, fb):
+    """Split mode, host operands, 4 x 4 blocks with every column block's encoded B kept in the budget:
+    A rows and B columns are each encoded once, and the result equals the in-core product bit for bit."""
+    m, n, k = 1100, 1030, 700
+    A = bi.uniform(450, *stored(opA, m, k), flags=fa).pin_memory()
+    B = bi.uniform(451, *stored(opB, k, n), flags=fb).pin_memory()
+    C0 = bi.uniform(452, m, n)
+    want = in_core(handle, A, B, C0, opA, opB, fa, fb, 1 - 1j, 0.5, "split")
+    budget = 6 << 30
+    mb, nb, kb, _ = hm.streamed_plan(m, n, k, opA, opB, fa, fb, "split", TOL, budget)
+    assert kb == k and mb < m and nb < n and mb == nb          # the cached-B block plan
+    C = C0.clone().pin_memory()
+    handle.set_profiling(True)
+    handle.reset_profile()
+    hm.hmat_bq_gemm_streamed(handle, A, B, C, opA, opB, fa, fb, 1 - 1j, 0.5, mode="split", tol=TOL, budget=budget)
+    torch.cuda.synchronize()
+    enc = handle.profile("split_encode")[0]
+    gemm = handle.profile("split_residue_gemm")[0]
+    handle.set_profiling(False)
+    np.testing.assert_array_equal(C.numpy(), want)
+    blocks_i, blocks_j = -(-m // mb), -(-n // nb)
+    assert gemm == blocks_i * blocks_j
+    # encoder launches: one per block row (A; the ragged last column block re-encodes it) plus B in row 0
+    assert enc <= blocks_i * 2 + blocks_j
