@@ -99,11 +99,13 @@ cudaError_t split_configure() {
 }
 
 void split_release(SplitState& s) {
-  if (s.used && s.done) cudaEventSynchronize(s.done);
-  if (s.done) cudaEventDestroy(s.done);
-  if (s.h_jobs) cudaFreeHost(s.h_jobs);
-  if (s.d_jobs) cudaFree(s.d_jobs);
-  s = SplitState();
+  for (SplitSlot& q : s.slots) {
+    if (q.used && q.done) cudaEventSynchronize(q.done);
+    if (q.done) cudaEventDestroy(q.done);
+    if (q.h_jobs) cudaFreeHost(q.h_jobs);
+    if (q.d_jobs) cudaFree(q.d_jobs);
+    q = SplitSlot();
+  }
 }
 
 // ----------------------------------------------------------------- layout
@@ -305,8 +307,10 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
 // Upload the job table through the handle's staging buffer and launch.
 hmat_status run_split(hmat_context* h, const SplitPrep& sp, const KPlan* d_plans, void* workspace,
                       cudaStream_t stream) {
-  SplitState& s = handle_split(h);
-  if (s.used) {
+  SplitState& st_all = handle_split(h);
+  SplitSlot& s = st_all.slots[st_all.next];
+  st_all.next = (st_all.next + 1) % kSplitSlots;
+  if (s.used) {   // the slot's previous call has finished reading its table
     if (cudaEventSynchronize(s.done) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
   }
   if (!s.done && cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess)
