@@ -562,6 +562,13 @@ def ops_arm(args, rank, world, local):
     B = bi.fock_like(args.seed + 1, n, n, device=dev)
     Hj = bi.apply_flags(A.clone(), 0xCC)
     C = torch.empty_like(A)
+    # a Hermitian matrix (A + A^dagger, formed by the library) and a pure-j Hermitian one
+    Herm = torch.empty_like(A)
+    hm_handle = hm.Handle()
+    hm.hmat_bq_add(hm_handle, A, A, Herm, 1.0, 1.0, "N", "H")
+    Pj = bi.apply_flags(Herm.clone(), 0x44)
+    torch.cuda.synchronize()
+    hm_handle.close()
     Z = torch.empty((2 * n, 2 * n), dtype=torch.complex128, device=dev)
     Zh = torch.empty((n, n), dtype=torch.complex128, device=dev)
     res = torch.empty(2, dtype=torch.float64, device=dev)
@@ -579,7 +586,10 @@ def ops_arm(args, rank, world, local):
         "to_complex_opT": (lambda: hm.hmat_bq_to_complex(h, A, Z, op="T", stream=stream), 2 * 64 * e),
         "from_complex": (lambda: hm.hmat_complex_to_bq(h, Z, C, stream=stream), 2 * 64 * e),
         "hermiticity": (lambda: hm.hmat_bq_hermiticity(h, A, out=res, stream=stream), 64 * e),
+        "hermiticity_of_hermitian": (lambda: hm.hmat_bq_hermiticity(h, Herm, out=res, stream=stream), 64 * e),
         "hadamard": (lambda: hm.hmat_bq_hadamard_block(h, Hj, 1j, 0xCC, Z=Zh, stream=stream), (32 + 16) * e),
+        "hadamard_pure_j": (lambda: hm.hmat_bq_hadamard_block(h, Pj, 1j, 0x44, Z=Zh, stream=stream),
+                            (16 + 16) * e),
     }
     peaks, src = measured_peaks()
     peak = peaks["hbm_gbs"]

@@ -57,13 +57,30 @@ __device__ __forceinline__ unsigned long long umax(unsigned long long a, unsigne
   return a > b ? a : b;
 }
 
-// x / 2, correctly rounded: exponent decrement for normal results, a multiply otherwise.
+// x / 2, correctly rounded, in integer instructions only.  Normal results:
+// the exponent field drops by one; inf and NaN are unchanged; for biased
+// exponents 0 and 1 the magnitude's bit pattern is the significand in units of
+// 2^-1074, so halving it with round-half-to-even gives the result's bits
+// directly (a carry into the exponent field included).  No FP64 instruction
+// and no branch: both would cost more than the memory traffic here.
 __device__ __forceinline__ double half(double x) {
-  const long long b = __double_as_longlong(x);
-  const int e = (int)((b >> 52) & 0x7FF);
-  if (e >= 2 && e < 0x7FF) return __longlong_as_double(b - (1ll << 52));
-  if (e == 0x7FF) return x;
-  return __dmul_rn(x, 0.5);
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long mag = u & ~kSign;
+  const unsigned e = (unsigned)(mag >> 52);
+  const unsigned long long small = (mag >> 1) + (mag & (mag >> 1) & 1ull);
+  const unsigned long long r = e >= 0x7FFu ? mag : (e >= 2u ? mag - (1ull << 52) : small);
+  return __longlong_as_double((long long)((u & kSign) | r));
+}
+
+// x / 2 for zeros and values whose biased exponent is 2..2046 (one 32-bit
+// subtraction on the high word); `bad` is set for anything else (subnormals,
+// the smallest normals, inf, NaN), which half() must redo.
+__device__ __forceinline__ double half_fast(double x, bool& bad) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7FFu;
+  const bool zero = ((hi & 0x7FFFFFFF) | lo) == 0;
+  bad |= !zero && (e - 2u) > 2044u;
+  return zero ? x : __hiloint2double(hi - (1 << 20), lo);
 }
 
 // (x0 + i x1) times the scalar of kind k (ScalarKind), step by step as
@@ -82,6 +99,15 @@ __device__ __forceinline__ void scale_pair(int k, double ar, double ai, double x
       break;
     default: *re = 0.0; *im = 0.0; break;
   }
+}
+
+// a - b, correctly rounded, as a volatile instruction: it stays inside the
+// branch that guards it (the compiler may otherwise hoist a plain subtraction
+// above the branch and run it for every entry).
+__device__ __forceinline__ double dsub_in_place(double a, double b) {
+  double r;
+  asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
+  return r;
 }
 
 // Block max of bit patterns, then one atomicMax.  Every thread of the block
@@ -254,31 +280,55 @@ __device__ __forceinline__ void tri_index(int64_t b, int64_t* I, int64_t* J) {
 }
 
 // One block per tile pair (I <= J): |X - X^dagger| on tile (I, J) covers tile
-// (J, I) too, since |a - s b| = |b - s a| for s = +-1.
+// (J, I) too, since |a - s b| = |b - s a| for s = +-1.  The direct tile stays
+// in the registers it was loaded into (thread (x, y) holds rows y, y + 8, ...
+// of column x, exactly the entries it compares); only the transposed tile goes
+// through shared memory, and the next component's two tiles are loaded while
+// the current one is compared.
 __global__ void __launch_bounds__(TT * TY) hermiticity_kernel(HermParams p) {
-  __shared__ Tile s1, s2;
+  __shared__ Tile s2;
   int64_t I, J;
   tri_index(blockIdx.x, &I, &J);
   const int64_t r0 = I * TT, q0 = J * TT;
+  const uint32_t flags = p.x.flags & 0xFFu;
   unsigned long long dev = 0;
-  for (int c = 0; c < 8; ++c) {
-    if (!((p.x.flags >> c) & 1u)) continue;
+  auto next_component = [&](int c) {
+    while (c < 8 && !((flags >> c) & 1u)) ++c;
+    return c;
+  };
+  int c = next_component(0);
+  TileRegs t1, t2;
+  if (c < 8) {
     const double* base = p.x.X + (int64_t)c * p.x.cs;
-    TileRegs t1, t2;
     fetch_tile(base, p.x.ld, true, false, false, r0, q0, p.n, p.n, t1);             // X[r0 + r][q0 + q]
     fetch_tile(base, p.x.ld, true, true, p.x.sign[c] < 0, r0, q0, p.n, p.n, t2);    // s_c X[q0 + q][r0 + r]
-    put_tile(t1, false, s1);
+  }
+  while (c < 8) {
     put_tile(t2, true, s2);
     __syncthreads();
+    const int cn = next_component(c + 1);
+    TileRegs t1n, t2n;
+    if (cn < 8) {
+      const double* base = p.x.X + (int64_t)cn * p.x.cs;
+      fetch_tile(base, p.x.ld, true, false, false, r0, q0, p.n, p.n, t1n);
+      fetch_tile(base, p.x.ld, true, true, p.x.sign[cn] < 0, r0, q0, p.n, p.n, t2n);
+    }
 #pragma unroll
-    for (int k = 0; k < TT; k += TY) {
-      const int r = threadIdx.y + k, q = threadIdx.x;
-      const double a = s1[r][q], b = s2[r][q];
+    for (int k = 0; k < TT / TY; ++k) {
+      const double a = t1.v[k], b = s2[threadIdx.y + k * TY][threadIdx.x];
       const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
-      // equal bits of a finite value: deviation 0 without an FP64 instruction
-      if (ab != bb || ((ab >> 52) & 0x7FF) == 0x7FF) dev = umax(dev, abs_bits(__dsub_rn(a, b)));
+      // equal bits of a finite value: deviation 0 without an FP64 instruction.
+      // The warp-uniform test keeps the subtraction behind a real branch (the
+      // compiler would otherwise evaluate it for every entry and select).
+      const bool differ = ab != bb || ((ab >> 52) & 0x7FF) == 0x7FF;
+      if (__any_sync(0xffffffffu, differ)) {
+        if (differ) dev = umax(dev, abs_bits(dsub_in_place(a, b)));
+      }
     }
     __syncthreads();
+    t1 = t1n;
+    t2 = t2n;
+    c = cn;
   }
   block_max_to<TT * TY>(p.result, dev);
 }
@@ -441,15 +491,31 @@ __global__ void __launch_bounds__(RT) from_complex_rows_kernel(FromComplexParams
     A[u] = __ldcs(top + uu); B[u] = __ldcs(top + n + uu); C[u] = __ldcs(bot + uu); D[u] = __ldcs(bot + n + uu);
   }
   double y[8][V];
+  double sums[8][V];
+  bool bad = false;
 #pragma unroll
   for (int u = 0; u < V; ++u) {
     // E = (A + D*)/2, F = (B - C*)/2, G = (A - D*)/2, H = (B + C*)/2
-    const double er = half(__dadd_rn(A[u].x, D[u].x)), ei = half(__dadd_rn(A[u].y, neg(D[u].y)));
-    const double fr = half(__dsub_rn(B[u].x, C[u].x)), fi = half(__dsub_rn(B[u].y, neg(C[u].y)));
-    const double gr = half(__dsub_rn(A[u].x, D[u].x)), gi = half(__dsub_rn(A[u].y, neg(D[u].y)));
-    const double hr = half(__dadd_rn(B[u].x, C[u].x)), hi = half(__dadd_rn(B[u].y, neg(C[u].y)));
-    y[0][u] = er; y[1][u] = ei; y[2][u] = fr; y[3][u] = fi;
-    y[4][u] = gi; y[5][u] = neg(gr); y[6][u] = hi; y[7][u] = neg(hr);
+    sums[0][u] = __dadd_rn(A[u].x, D[u].x);  sums[1][u] = __dadd_rn(A[u].y, neg(D[u].y));
+    sums[2][u] = __dsub_rn(B[u].x, C[u].x);  sums[3][u] = __dsub_rn(B[u].y, neg(C[u].y));
+    sums[4][u] = __dsub_rn(A[u].y, neg(D[u].y));  sums[5][u] = __dsub_rn(A[u].x, D[u].x);
+    sums[6][u] = __dadd_rn(B[u].y, neg(C[u].y));  sums[7][u] = __dadd_rn(B[u].x, C[u].x);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) y[c][u] = half_fast(sums[c][u], bad);
+  }
+  // one vote for the rare values the fast halving does not cover
+  if (__any_sync(__activemask(), bad)) {
+    if (bad) {
+#pragma unroll
+      for (int u = 0; u < V; ++u)
+#pragma unroll
+        for (int c = 0; c < 8; ++c) y[c][u] = half(sums[c][u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < V; ++u) {   // stored as [E_R, E_I, F_R, F_I, G_I, -G_R, H_I, -H_R]
+    y[5][u] = neg(y[5][u]);
+    y[7][u] = neg(y[7][u]);
   }
   double* out = p.Y + i * p.ldy + j;
 #pragma unroll
@@ -462,39 +528,74 @@ __global__ void __launch_bounds__(RT) from_complex_rows_kernel(FromComplexParams
 //   (alpha A - alpha* B) / 2 =  (a M3 - b M4) + i (a M7 - b M8),
 // which for alpha = +-1, +-i are signed components (no FP64 instruction) and
 // otherwise take four products each.
-__device__ __forceinline__ double lin2(int k, double a, double b, double x, double y) {
-  // a x + b y for the scalar kinds: +-1 -> +-x, +-i -> +-y
-  switch (k) {
-    case kScalarOne: return x;
-    case kScalarMinusOne: return neg(x);
-    case kScalarI: return y;
-    case kScalarMinusI: return neg(y);
-    default: return __dadd_rn(__dmul_rn(a, x), __dmul_rn(b, y));
-  }
+
+// a x + b y for alpha = a + i b of a unit kind: +-1 -> +-x, +-i -> +-y
+__device__ __forceinline__ double unit_pick(int k, double x, double y) {
+  const double v = (k == kScalarOne || k == kScalarMinusOne) ? x : y;
+  return flip_if(v, k == kScalarMinusOne || k == kScalarMinusI);
 }
 
-template <int V>
+constexpr int kHadRows = 4;   // rows per Hadamard block: their loads are all in flight together
+
+// UNIT: alpha is +-1 or +-i (a signed pick of a component, no FP64 instruction)
+template <int V, bool UNIT>
 __global__ void __launch_bounds__(RT) hadamard_rows_kernel(HadamardParams p) {
-  int64_t i, j;
-  row_origin(p.n, V, &i, &j);
+  const int64_t segs = (p.n + (int64_t)RT * V - 1) / ((int64_t)RT * V);
+  const int64_t i0 = (blockIdx.x / segs) * kHadRows;
+  const int64_t j = (blockIdx.x % segs) * ((int64_t)RT * V) + (int64_t)threadIdx.x * V;
   const int nv = valid_count(j, p.n, V);     // no early return: the block reduction needs every thread
+  const uint32_t f = p.x.flags & 0xCCu;      // only F and H (M3, M4, M7, M8) feed the anti-diagonal blocks
+  const int comp[4] = {2, 3, 6, 7};
+  double x[kHadRows][4][V];
+#pragma unroll
+  for (int rr = 0; rr < kHadRows; ++rr) {
+    const int64_t i = i0 + rr;
+    const bool row_ok = i < p.n && nv > 0;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const bool present = row_ok && ((f >> comp[cc]) & 1u);
+      const double* ptr = p.x.X + (int64_t)comp[cc] * p.x.cs + i * p.x.ld + j;
+      if (V == 2 && nv == V) {
+        const double2 t = present ? __ldcs(reinterpret_cast<const double2*>(ptr)) : make_double2(0.0, 0.0);
+        x[rr][cc][0] = t.x;
+        x[rr][cc][V - 1] = t.y;
+      } else {
+#pragma unroll
+        for (int u = 0; u < V; ++u) x[rr][cc][u] = (present && u < nv) ? __ldcs(ptr + u) : 0.0;
+      }
+    }
+  }
+  const double a = p.alpha_re, b = p.alpha_im;
+  // kind of alpha* (the scalar of a x - b y)
+  const int kc = p.kind == kScalarI ? kScalarMinusI : (p.kind == kScalarMinusI ? kScalarI : p.kind);
   unsigned long long off = 0;                // bits of the largest squared modulus of (alpha A - alpha* B) / 2
-  if (nv > 0) {
-    double x[8][V];
-    load_row<V>(p.x, p.x.flags & 0xCCu, i, j, nv, x);   // only F and H feed the anti-diagonal blocks
-    const double a = p.alpha_re, b = p.alpha_im;
-    // kind of alpha* (the scalar of a x - b y)
-    const int kc = p.kind == kScalarI ? kScalarMinusI : (p.kind == kScalarMinusI ? kScalarI : p.kind);
+#pragma unroll
+  for (int rr = 0; rr < kHadRows; ++rr) {
+    const int64_t i = i0 + rr;
     double2 z[V];
 #pragma unroll
     for (int u = 0; u < V; ++u) {
-      const double m3 = x[2][u], m4 = x[3][u], m7 = x[6][u], m8 = x[7][u];
-      z[u] = make_double2(neg(lin2(p.kind, a, b, m8, m7)), lin2(p.kind, a, b, m4, m3));
-      const double dr = lin2(kc, a, neg(b), m3, m4), di = lin2(kc, a, neg(b), m7, m8);
-      // entries past the row end are zeros: their difference is 0
-      if (abs_bits(dr) | abs_bits(di)) off = umax(off, abs_bits(__fma_rn(dr, dr, __dmul_rn(di, di))));
+      const double m3 = x[rr][0][u], m4 = x[rr][1][u], m7 = x[rr][2][u], m8 = x[rr][3][u];
+      double dr, di;
+      if (UNIT) {
+        z[u] = make_double2(neg(unit_pick(p.kind, m8, m7)), unit_pick(p.kind, m4, m3));
+        dr = unit_pick(kc, m3, m4);
+        di = unit_pick(kc, m7, m8);
+      } else {
+        z[u] = make_double2(neg(__dadd_rn(__dmul_rn(a, m8), __dmul_rn(b, m7))),
+                            __dadd_rn(__dmul_rn(a, m4), __dmul_rn(b, m3)));
+        dr = __dsub_rn(__dmul_rn(a, m3), __dmul_rn(b, m4));
+        di = __dsub_rn(__dmul_rn(a, m7), __dmul_rn(b, m8));
+      }
+      // entries past the matrix are zeros: their difference is 0; the squared
+      // modulus stays behind a warp-uniform branch (no FP64 work where the
+      // block reduces)
+      const bool nz = (abs_bits(dr) | abs_bits(di)) != 0;
+      if (__any_sync(0xffffffffu, nz)) {
+        if (nz) off = umax(off, abs_bits(__fma_rn(dr, dr, __dmul_rn(di, di))));
+      }
     }
-    store_cplx<V>(reinterpret_cast<double2*>(p.Z) + i * p.ldz + j, nv, z);
+    if (i < p.n && nv > 0) store_cplx<V>(reinterpret_cast<double2*>(p.Z) + i * p.ldz + j, nv, z);
   }
   if (p.offdiag) {
     // max |d| = sqrt(max |d|^2): one square root per block
@@ -619,10 +720,14 @@ cudaError_t launch_hadamard(const HadamardParams& p, cudaStream_t s) {
     if (e != cudaSuccess) return e;
   }
   if (p.n <= 0) return cudaSuccess;
-  if (vec2_ok(p.x.X, p.x.ld, p.x.cs))
-    hadamard_rows_kernel<2><<<rows_grid(p.n, p.n, 2), RT, 0, s>>>(p);
-  else
-    hadamard_rows_kernel<1><<<rows_grid(p.n, p.n, 1), RT, 0, s>>>(p);
+  const int64_t row_groups = (p.n + kHadRows - 1) / kHadRows;
+  const bool unit = p.kind >= kScalarOne && p.kind <= kScalarMinusI;
+  const bool v2 = vec2_ok(p.x.X, p.x.ld, p.x.cs);
+  const unsigned g2 = rows_grid(row_groups, p.n, 2), g1 = rows_grid(row_groups, p.n, 1);
+  if (v2 && unit) hadamard_rows_kernel<2, true><<<g2, RT, 0, s>>>(p);
+  else if (v2) hadamard_rows_kernel<2, false><<<g2, RT, 0, s>>>(p);
+  else if (unit) hadamard_rows_kernel<1, true><<<g1, RT, 0, s>>>(p);
+  else hadamard_rows_kernel<1, false><<<g1, RT, 0, s>>>(p);
   return cudaGetLastError();
 }
 

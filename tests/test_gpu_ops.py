@@ -231,3 +231,19 @@ def test_empty_and_degenerate_shapes(handle):
         Z = hm.hmat_bq_to_complex(handle, X.to(DEV))
         np.testing.assert_array_equal(Z.cpu().numpy(), iso.to_isomorph(X.numpy()))
         np.testing.assert_array_equal(hm.hmat_complex_to_bq(handle, Z).cpu().numpy(), iso.from_isomorph(Z.cpu().numpy()))
+
+
+def test_from_complex_edge_values(handle):
+    """The inverse map halves in integer arithmetic: zeros, subnormals and the smallest normals come
+    out exactly as numpy's correctly rounded halving.  (Infinities are left out: numpy's complex
+    division by 2 turns an infinite imaginary part into a NaN real part.)"""
+    m, n = 3, 70
+    g = np.random.default_rng(360)
+    special = np.array([0.0, -0.0, 5e-324, -5e-324, 1e-310, -3e-320, 2.2250738585072014e-308,
+                        4.450147717014403e-308, 1e307, 3.0])
+    re = g.choice(special, size=(2 * m, 2 * n)) * g.choice([1.0, 0.5, -3.0], size=(2 * m, 2 * n))
+    im = g.choice(special, size=(2 * m, 2 * n))
+    Z = torch.complex(torch.from_numpy(re), torch.from_numpy(im))
+    Y = hm.hmat_complex_to_bq(handle, Z.to(DEV))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(Y.cpu().numpy(), iso.from_isomorph(Z.numpy()))
