@@ -42,7 +42,7 @@ constexpr int kTileM = 128;        // tcgen05 M (one TMEM lane per output row)
 constexpr int kTileK = 64;         // BF16 elements per 128-byte swizzled row
 constexpr int kChunkK = 1024;      // inner steps per exact FP32 accumulation chunk
 constexpr int kTileBins = 16;      // tile-width table: bins of ceil(log2 m) x ceil(log2 n)
-constexpr int kCrtThreads = 128;   // CRT block size (elements per block)
+constexpr int kCrtCols = 128;      // CRT output columns per block (two threads per element)
 
 struct SplitParams {
   int nmod = 0;

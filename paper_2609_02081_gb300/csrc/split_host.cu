@@ -141,8 +141,8 @@ static constexpr int64_t kPlaneSkewRes = 3 * 256;
 
 // encode blocks: tiles of 16 rows x 32 k over the padded operand
 static inline int64_t enc_blocks(int64_t rows_pad, int64_t nkb) { return (rows_pad / 16) * (nkb * kTileK / 32); }
-// CRT blocks: one per output row and kCrtThreads consecutive columns
-static inline int64_t crt_blocks(int64_t m, int64_t n) { return m * ((n + kCrtThreads - 1) / kCrtThreads); }
+// CRT blocks: one per output row and kCrtCols consecutive columns
+static inline int64_t crt_blocks(int64_t m, int64_t n) { return m * ((n + kCrtCols - 1) / kCrtCols); }
 
 // Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
 static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const int8_t* table, SplitJob* sj,

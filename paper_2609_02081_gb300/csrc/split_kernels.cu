@@ -22,6 +22,7 @@ struct ModConst {
   float c36;    // 2^36 mod p, centred
   float c23;    // 2^23 mod p, in [0, p)
   int inv4;     // 4^-1 mod p
+  float pbias;  // p + 1.5 * 2^23 (residue + p to integer in one add)
   unsigned long long fm;  // floor(2^64 / p) + 1 (fast exact 32-bit mod)
 };
 
@@ -271,21 +272,35 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
     s_slot[gi][part] = gi < ng ? (side ? P.rslot[gi][part] : P.lslot[gi][part]) : -1;
   }
   __syncthreads();
-  // phase 1: stage scaled integers, op sign applied (reads coalesced along the contiguous index)
-  for (int idx = t; idx < 8 * kEncK * kEncRows; idx += kEncThreads) {
+  // phase 1: stage scaled integers, op sign applied (reads coalesced along the
+  // contiguous index).  All of this thread's loads are issued before the first
+  // conversion, so the block waits for one DRAM round trip, not one per load.
+  constexpr int kPer = 8 * kEncK * kEncRows / kEncThreads;   // values per thread (component u / 4)
+  static_assert(kEncK * kEncRows % kEncThreads == 0, "a component's values split evenly over the threads");
+  unsigned long long raw[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int idx = t + u * kEncThreads;
     const int c = idx / (kEncK * kEncRows);
     const int rem = idx % (kEncK * kEncRows);
-    int rr, kk;
-    if (contiguous) { rr = rem / kEncK; kk = rem % kEncK; }
-    else { kk = rem / kEncRows; rr = rem % kEncRows; }
-    long long X = 0;
+    const int rr = contiguous ? rem / kEncK : rem % kEncRows;
+    const int kk = contiguous ? rem % kEncK : rem / kEncRows;
     const int r = r0 + rr, kg = k0 + kk;
+    raw[u] = 0ull;
     if (((flags >> c) & 1u) && r < nout && kg < d.k) {
       const int64_t off = contiguous ? (int64_t)r * ld + kg : (int64_t)kg * ld + r;
-      const unsigned long long bits = (unsigned long long)__double_as_longlong(__ldg(base + (int64_t)c * cs + off));
-      X = scaled_int(bits, s_row[rr]);
-      if (sign[c] < 0) X = -X;
+      raw[u] = (unsigned long long)__double_as_longlong(__ldcs(base + (int64_t)c * cs + off));
     }
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    const int idx = t + u * kEncThreads;
+    const int c = idx / (kEncK * kEncRows);
+    const int rem = idx % (kEncK * kEncRows);
+    const int rr = contiguous ? rem / kEncK : rem % kEncRows;
+    const int kk = contiguous ? rem % kEncK : rem / kEncRows;
+    long long X = scaled_int(raw[u], s_row[rr]);   // zero bits give 0
+    if (sign[c] < 0) X = -X;
     if (LIMBS == 2) {
       xs[c][kk][rr][0] = (float)(int)(X & 0x7FFFFF);
       xs[c][kk][rr][LIMBS - 1] = (float)(long long)(X >> 23);
@@ -405,30 +420,40 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
 }
 
 // ------------------------------------------------------------------ 4. CRT + recombination + alpha/beta
-// One block per output row segment of kCrtThreads columns; one thread per
-// element.  The np residue rows of each modulus are prefetched into a
-// three-slot shared-memory ring with cp.async two moduli ahead.  Per modulus the np product residues are packed four to a word
-// and the eight output residues sum_p w4[e][p] T_p come from __dp4a against
-// the plan's weights (packed the same way, in shared memory); times 4^-1 mod p
-// gives the residue of the output.  S_e = sum_l r_{l,e} c_l accumulates in
-// 64-bit limbs (c_l the CRT basis), is reduced mod P, centred, converted to
-// FP64 with one rounding and scaled by 2^-(s_i + t_j); then the complex
-// alpha / beta update (Sec. III scaling and addition).
+// One block per output row segment of kCrtCols columns and two threads per
+// element: threads [0, kCrtCols) form the four real-part components
+// (M1..M4 of the storage order), threads [kCrtCols, 2 kCrtCols) the four
+// imaginary-part ones (M5..M8); the split is warp-uniform.  The np residue
+// rows of each modulus are prefetched into a three-slot shared-memory ring
+// with cp.async two moduli ahead.  Per modulus the output residues
+// sum_p w4[e][p] T_p are formed (the paper's recombination for the bilinear
+// plan, __dp4a against the packed weights otherwise), times 4^-1 mod p gives
+// the residue of the output.  S_e = sum_l r_{l,e} c_l accumulates in 64-bit
+// limbs (c_l the CRT basis), is reduced mod P, centred, converted to FP64 with
+// one rounding and scaled by 2^-(s_i + t_j); then the complex alpha / beta
+// update (Sec. III scaling and addition), for which the two halves trade
+// their four components through shared memory.
 template <int L>
-__device__ __forceinline__ double limbs_to_double(const uint32_t* x, int neg, int scale_exp) {
-  int h = 0;
+__device__ __forceinline__ double limbs_to_double(const uint32_t* xin, int neg, int scale_exp) {
+  // whole-limb shifts bring the top nonzero limb (index h) to position L - 1;
+  // selects only, so the limbs stay in registers
+  uint32_t x[L];
 #pragma unroll
-  for (int q = 0; q < L; ++q)
-    if (x[q]) h = q;
-  if (x[h] == 0) return neg ? -0.0 : 0.0;
-  uint32_t l2 = 0, l1 = 0, l0 = 0, sticky = 0;
+  for (int q = 0; q < L; ++q) x[q] = xin[q];
+  int h = L - 1;
 #pragma unroll
-  for (int q = 0; q < L; ++q) {
-    if (q == h) l2 = x[q];
-    else if (q == h - 1) l1 = x[q];
-    else if (q == h - 2) l0 = x[q];
-    else if (q < h - 2) sticky |= x[q];
+  for (int s = 0; s < L - 1; ++s) {
+    const bool z = x[L - 1] == 0;
+#pragma unroll
+    for (int q = L - 1; q > 0; --q) x[q] = z ? x[q - 1] : x[q];
+    x[0] = z ? 0u : x[0];
+    h -= z ? 1 : 0;
   }
+  const uint32_t l2 = x[L - 1], l1 = x[L - 2], l0 = x[L - 3];
+  if (l2 == 0) return neg ? -0.0 : 0.0;
+  uint32_t sticky = 0;
+#pragma unroll
+  for (int q = 0; q < L - 3; ++q) sticky |= x[q];
   const int lz = __clz(l2);                       // normalise the 96-bit window [l2 l1 l0]
   unsigned long long hi = ((unsigned long long)l2 << 32) | l1;
   unsigned long long lo = (unsigned long long)l0 << 32;
@@ -443,19 +468,40 @@ __device__ __forceinline__ double limbs_to_double(const uint32_t* x, int neg, in
   return neg ? -r : r;
 }
 
+// Sign of x - y for L-limb unsigned integers (most significant limb last).
+template <int L>
+__device__ __forceinline__ int cmp_limbs(const uint32_t* x, const uint32_t* y) {
+  int c = 0;
+#pragma unroll
+  for (int q = L - 1; q >= 0; --q)
+    if (c == 0) c = (x[q] > y[q]) - (x[q] < y[q]);
+  return c;
+}
+
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
+// Non-negative residue of 4Q times 4^-1: the centred residue plus p, in
+// [(p-1)/2, (3p+1)/2], as an integer (the bias 1.5 * 2^23 + p is folded into
+// one add).  |4Q * 4^-1| < 2^22 keeps the float conversions exact.
+__device__ __forceinline__ uint32_t residue_plus_p(int q4, const ModConst& mc) {
+  const float qf = __int_as_float(q4 * mc.inv4 + 0x4B400000) - 12582912.0f;
+  const float r = fmod_c(qf, mc);
+  return (uint32_t)(__float_as_int(r + mc.pbias) - 0x4B400000);
+}
+
 template <int L>
-__global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs,
-                                                                const KPlan* __restrict__ plans,
-                                                                unsigned char* __restrict__ ws) {
+__global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                                    const KPlan* __restrict__ plans,
+                                                                    unsigned char* __restrict__ ws) {
   constexpr int kStages = 3;
+  constexpr int kChunksPerRow = kCrtCols / 16;    // 16-byte cp.async chunks per residue row
   __shared__ uint32_t wpk[8][kMaxProducts / 4];
-  __shared__ __align__(16) uint8_t ring[kStages][kMaxProducts][kCrtThreads];
+  __shared__ __align__(16) uint8_t ring[kStages][kMaxProducts][kCrtCols];
+  __shared__ double xch[8][kCrtCols];            // the four components of each half, for alpha / beta
   const int64_t blk = blockIdx.x;
   const int g = find_split_job(jobs, njobs, blk, 4);
   const SplitJob& sj = jobs[g];
@@ -463,6 +509,7 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
   const KPlan& P = plans[d.plan];
   const int np = sj.np, nw = (np + 3) / 4, nm = sj.nmod;
   const int tid = threadIdx.x;
+  const int col = tid % kCrtCols, half = tid / kCrtCols;   // half 0: M1..M4, half 1: M5..M8
   if (tid < 8 * (kMaxProducts / 4)) {
     const int e = tid / (kMaxProducts / 4), w = tid % (kMaxProducts / 4);
     uint32_t word = 0;
@@ -474,46 +521,33 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
     }
     wpk[e][w] = word;
   }
-  // this block: row i, columns jb*128 .. jb*128+127 of the output
+  // this block: row i, columns jb*kCrtCols .. jb*kCrtCols + kCrtCols - 1 of the output
   const int64_t local = blk - sj.crt_begin;
-  const int colblocks = (d.n + kCrtThreads - 1) / kCrtThreads;
+  const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
   const int i = (int)(local / colblocks);
   const int jb = (int)(local % colblocks);
-  const int j = jb * kCrtThreads + tid;
+  const int j = jb * kCrtCols + col;
   const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
   const int64_t plane = sj.res_plane;
-  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtThreads;
-  const int64_t cavail = (ncols - (int64_t)jb * kCrtThreads) / 16;
-  const int cmax = cavail < kCrtThreads / 16 ? (int)cavail : kCrtThreads / 16;
+  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
+  const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
+  const int cmax = cavail < kChunksPerRow ? (int)cavail : kChunksPerRow;
 
-  // prefetch modulus l's np residue rows (128 bytes each) into ring slot l % 3;
-  // this thread's first two 16-byte chunks (all of them for np <= 32) are fixed,
-  // further ones (larger plans) are computed per modulus
-  constexpr int kMaxChunks = 2;
-  int64_t c_src[kMaxChunks];
-  int c_dst[kMaxChunks];
-  int nchunks = 0;
-#pragma unroll
-  for (int u = 0; u < kMaxChunks; ++u) {
-    const int idx = tid + u * kCrtThreads;
-    const int p = idx / (kCrtThreads / 16), c = idx % (kCrtThreads / 16);
-    c_src[u] = (int64_t)p * plane + c * 16;
-    c_dst[u] = p * kCrtThreads + c * 16;
-    if (idx < np * (kCrtThreads / 16) && c < cmax) nchunks = u + 1;
-  }
+  // prefetch modulus l's np residue rows (kCrtCols bytes each) into ring slot
+  // l % 3: thread tid copies chunk tid (all of them for np <= 32), further
+  // chunks (larger plans) are computed per modulus
+  const int p0 = tid / kChunksPerRow, c0 = tid % kChunksPerRow;
+  const bool has0 = tid < np * kChunksPerRow && c0 < cmax;
+  const int64_t src0 = (int64_t)p0 * plane + c0 * 16;
+  const int dst0 = p0 * kCrtCols + c0 * 16;
   auto issue = [&](int l) {
     if (l < nm) {
       uint8_t* slot = &ring[l % kStages][0][0];
       const unsigned char* src = rowbase + (int64_t)l * np * plane;
-#pragma unroll
-      for (int u = 0; u < kMaxChunks; ++u) {
-        const int idx = tid + u * kCrtThreads;
-        if (u < nchunks && idx < np * (kCrtThreads / 16) && (idx % (kCrtThreads / 16)) < cmax)
-          cp_async16(slot + c_dst[u], src + c_src[u]);
-      }
-      for (int idx = tid + kMaxChunks * kCrtThreads; idx < np * (kCrtThreads / 16); idx += kCrtThreads) {
-        const int p = idx / (kCrtThreads / 16), c = idx % (kCrtThreads / 16);
-        if (c < cmax) cp_async16(slot + p * kCrtThreads + c * 16, src + (int64_t)p * plane + c * 16);
+      if (has0) cp_async16(slot + dst0, src + src0);
+      for (int idx = tid + 2 * kCrtCols; idx < np * kChunksPerRow; idx += 2 * kCrtCols) {
+        const int p = idx / kChunksPerRow, c = idx % kChunksPerRow;
+        if (c < cmax) cp_async16(slot + p * kCrtCols + c * 16, src + (int64_t)p * plane + c * 16);
       }
     }
     cp_async_commit();
@@ -521,9 +555,9 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
   issue(0);
   issue(1);
 
-  unsigned long long acc[8][L];
+  unsigned long long acc[4][L];
 #pragma unroll
-  for (int e = 0; e < 8; ++e)
+  for (int e = 0; e < 4; ++e)
 #pragma unroll
     for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
 
@@ -533,173 +567,166 @@ __global__ void __launch_bounds__(kCrtThreads) split_crt_kernel(const SplitJob* 
     cp_async_wait2();            // modulus l has landed
     __syncthreads();
     const ModConst& mc = c_mod[l];
-    const uint8_t(*slot)[kCrtThreads] = ring[l % kStages];
+    uint32_t cl[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) cl[q] = c_crt[nm][l][q];
+    const uint8_t(*slot)[kCrtCols] = ring[l % kStages];
+    uint32_t ru[4];
     if (structured) {
       // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
       // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
-      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); in 32-bit
-      // integers (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
-      int pre[8], pim[8];
+      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); real parts
+      // in half 0, imaginary parts in half 1, in 32-bit integers
+      // (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
+      int v[8];
+      if (half == 0) {
 #pragma unroll
-      for (int r = 0; r < 8; ++r) {
-        const int t0 = (int8_t)slot[3 * r][tid], t1 = (int8_t)slot[3 * r + 1][tid];
-        const int t2 = (int8_t)slot[3 * r + 2][tid];
-        pre[r] = t0 - t1;
-        pim[r] = t2 - t0 - t1;
+        for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
       }
-      int q4[8];
-      {
-        const int a = pre[4] + pre[5], b = pre[4] - pre[5], c = pre[6] + pre[7], dd = pre[6] - pre[7];
-        q4[0] = 8 * pre[0] - (a + c);
-        q4[1] = -8 * pre[1] + (a - c);
-        q4[2] = -8 * pre[2] + (b + dd);
-        q4[3] = -8 * pre[3] + (b - dd);
-        const int ai = pim[4] + pim[5], bi = pim[4] - pim[5], ci = pim[6] + pim[7], di = pim[6] - pim[7];
-        q4[4] = 8 * pim[0] - (ai + ci);
-        q4[5] = -8 * pim[1] + (ai - ci);
-        q4[6] = -8 * pim[2] + (bi + di);
-        q4[7] = -8 * pim[3] + (bi - di);
-      }
+      const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
+      ru[0] = residue_plus_p(8 * v[0] - (a + c), mc);
+      ru[1] = residue_plus_p(-8 * v[1] + (a - c), mc);
+      ru[2] = residue_plus_p(-8 * v[2] + (b + dd), mc);
+      ru[3] = residue_plus_p(-8 * v[3] + (b - dd), mc);
+    } else {
+      uint32_t tw[kMaxProducts / 4];
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        // |4Q * 4^-1| < 4572 * 255 < 2^21: int -> float through the 1.5 * 2^23 bias is exact
-        const float qf = __int_as_float(q4[e] * mc.inv4 + 0x4B400000) - 12582912.0f;
-        float r = fmod_c(qf, mc);
-        if (r < 0.f) r += mc.pf;
-        const uint32_t ru = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
+      for (int w = 0; w < kMaxProducts / 4; ++w) {
+        uint32_t word = 0;
+        if (w < nw) {
 #pragma unroll
-        for (int qq = 0; qq < L; ++qq) acc[e][qq] += (unsigned long long)ru * c_crt[nm][l][qq];
-      }
-      __syncthreads();           // slot l % 3 is refilled by issue(l + 3)
-      continue;
-    }
-    uint32_t tw[kMaxProducts / 4];
-#pragma unroll
-    for (int w = 0; w < kMaxProducts / 4; ++w) {
-      uint32_t word = 0;
-      if (w < nw) {
-#pragma unroll
-        for (int b = 0; b < 4; ++b) {
-          const int p = 4 * w + b;
-          const uint32_t v = p < np ? (uint32_t)slot[p][tid] : 0u;
-          word |= v << (8 * b);
+          for (int b = 0; b < 4; ++b) {
+            const int p = 4 * w + b;
+            const uint32_t x = p < np ? (uint32_t)slot[p][col] : 0u;
+            word |= x << (8 * b);
+          }
         }
+        tw[w] = word;
       }
-      tw[w] = word;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        int o = 0;
+#pragma unroll
+        for (int w = 0; w < kMaxProducts / 4; ++w)
+          if (w < nw) o = __dp4a((int)wpk[4 * half + e][w], (int)tw[w], o);
+        // |o| <= sum_p |w4[e][p]| * 127 < 2^16 and 4^-1 < 2^8: o * 4^-1 is an exact
+        // float below 2^24 (int -> float through the 1.5 * 2^23 bias, |o| < 2^22)
+        const float of = __int_as_float(o + 0x4B400000) - 12582912.0f;
+        const float r = fmod_c(of * (float)mc.inv4, mc);
+        ru[e] = (uint32_t)(__float_as_int(r + mc.pbias) - 0x4B400000);
+      }
     }
-    const float inv4 = (float)mc.inv4;
 #pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      int o = 0;
+    for (int e = 0; e < 4; ++e)
 #pragma unroll
-      for (int w = 0; w < kMaxProducts / 4; ++w)
-        if (w < nw) o = __dp4a((int)wpk[e][w], (int)tw[w], o);
-      // |o| <= 24 * 8 * 127 < 2^15 and 4^-1 < 2^8: o * 4^-1 is an exact float below 2^23.
-      // int <-> float through the 1.5 * 2^23 bias (exact for |x| < 2^22, no conversion unit)
-      const float of = __int_as_float(o + 0x4B400000) - 12582912.0f;
-      float r = fmod_c(of * inv4, mc);
-      if (r < 0.f) r += mc.pf;
-      const uint32_t ru = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
-#pragma unroll
-      for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru * c_crt[nm][l][q];
-    }
+      for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
     __syncthreads();             // slot l % 3 is refilled by issue(l + 3)
   }
-  if (j >= d.n) return;
 
-  const int s_i = reinterpret_cast<const int32_t*>(ws + sj.off_sexp)[i];
-  const int t_j = reinterpret_cast<const int32_t*>(ws + sj.off_texp)[j];
-  double q8[8];
+  const bool valid = j < d.n;
+  double q4v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (valid) {
+    const int s_i = reinterpret_cast<const int32_t*>(ws + sj.off_sexp)[i];
+    const int t_j = reinterpret_cast<const int32_t*>(ws + sj.off_texp)[j];
 #pragma unroll
-  for (int e = 0; e < 8; ++e) {
-    uint32_t x[L];
-    unsigned long long carry = 0;
-#pragma unroll
-    for (int q = 0; q < L; ++q) {
-      const unsigned long long tq = acc[e][q] + carry;
-      x[q] = (uint32_t)tq;
-      carry = tq >> 32;
-    }
-    // quotient estimate q = floor(S / P) from the leading limbs (S < nmod * 255 * P)
-    const int pb = c_Pbase[nm];
-    float sf = 0.f;
-#pragma unroll
-    for (int q = L - 1; q >= 0; --q)
-      if (q >= pb) sf = sf * 4294967296.f + (float)x[q];
-    int qq = (int)floorf(sf / c_Pf[nm]);
-    if (qq < 0) qq = 0;
-    long long borrow = 0;
-    unsigned long long mulc = 0;
-#pragma unroll
-    for (int q = 0; q < L; ++q) {            // x -= qq * P
-      const unsigned long long prod = (unsigned long long)c_P[nm][q] * (uint32_t)qq + mulc;
-      mulc = prod >> 32;
-      const long long diff = (long long)x[q] - (long long)(uint32_t)prod + borrow;
-      x[q] = (uint32_t)diff;
-      borrow = diff >> 32;
-    }
-    if (borrow < 0) {                        // over-estimate by one: add P back
-      unsigned long long c = 0;
+    for (int e = 0; e < 4; ++e) {
+      uint32_t x[L];
+      unsigned long long carry = 0;
 #pragma unroll
       for (int q = 0; q < L; ++q) {
-        const unsigned long long tq = (unsigned long long)x[q] + c_P[nm][q] + c;
+        const unsigned long long tq = acc[e][q] + carry;
         x[q] = (uint32_t)tq;
-        c = tq >> 32;
+        carry = tq >> 32;
       }
-    } else {                                 // under-estimate by one: subtract P
-      bool ge = true;
+      // quotient estimate q = floor(S / P) from the leading limbs (S < nmod * 383 * P)
+      const int pb = c_Pbase[nm];
+      float sf = 0.f;
 #pragma unroll
-      for (int q = L - 1; q >= 0; --q) {
-        if (x[q] != c_P[nm][q]) { ge = x[q] > c_P[nm][q]; break; }
+      for (int q = L - 1; q >= 0; --q)
+        if (q >= pb) sf = sf * 4294967296.f + (float)x[q];
+      int qq = (int)floorf(sf / c_Pf[nm]);
+      if (qq < 0) qq = 0;
+      long long borrow = 0;
+      unsigned long long mulc = 0;
+#pragma unroll
+      for (int q = 0; q < L; ++q) {            // x -= qq * P
+        const unsigned long long prod = (unsigned long long)c_P[nm][q] * (uint32_t)qq + mulc;
+        mulc = prod >> 32;
+        const long long diff = (long long)x[q] - (long long)(uint32_t)prod + borrow;
+        x[q] = (uint32_t)diff;
+        borrow = diff >> 32;
       }
-      if (ge) {
+      if (borrow < 0) {                        // over-estimate by one: add P back
+        unsigned long long c = 0;
+#pragma unroll
+        for (int q = 0; q < L; ++q) {
+          const unsigned long long tq = (unsigned long long)x[q] + c_P[nm][q] + c;
+          x[q] = (uint32_t)tq;
+          c = tq >> 32;
+        }
+      } else {                                 // under-estimate by one: subtract P
+        if (cmp_limbs<L>(x, c_P[nm]) >= 0) {
+          long long b = 0;
+#pragma unroll
+          for (int q = 0; q < L; ++q) {
+            const long long diff = (long long)x[q] - (long long)c_P[nm][q] + b;
+            x[q] = (uint32_t)diff;
+            b = diff >> 32;
+          }
+        }
+      }
+      int neg = 0;                             // centre: x > P/2 means x - P
+      if (cmp_limbs<L>(x, c_Ph[nm]) > 0) {
         long long b = 0;
 #pragma unroll
         for (int q = 0; q < L; ++q) {
-          const long long diff = (long long)x[q] - (long long)c_P[nm][q] + b;
+          const long long diff = (long long)c_P[nm][q] - (long long)x[q] + b;
           x[q] = (uint32_t)diff;
           b = diff >> 32;
         }
+        neg = 1;
       }
+      q4v[e] = limbs_to_double<L>(x, neg, -(s_i + t_j));
     }
-    bool gt = false;                         // centre: x > P/2 means x - P
-#pragma unroll
-    for (int q = L - 1; q >= 0; --q) {
-      if (x[q] != c_Ph[nm][q]) { gt = x[q] > c_Ph[nm][q]; break; }
-    }
-    int neg = 0;
-    if (gt) {
-      long long b = 0;
-#pragma unroll
-      for (int q = 0; q < L; ++q) {
-        const long long diff = (long long)c_P[nm][q] - (long long)x[q] + b;
-        x[q] = (uint32_t)diff;
-        b = diff >> 32;
-      }
-      neg = 1;
-    }
-    q8[e] = limbs_to_double<L>(x, neg, -(s_i + t_j));
   }
 
   double* cbase = d.C + (int64_t)i * d.ldc + j;
   const bool plain = (d.alpha_re == 1.0 && d.alpha_im == 0.0 && d.beta_re == 0.0 && d.beta_im == 0.0);
-  if (plain) {
+  if (plain) {                                 // block-uniform
+    if (valid) {
 #pragma unroll
-    for (int e = 0; e < 8; ++e) cbase[(int64_t)e * d.sC] = q8[e];
-  } else {
-    const bool use_beta = (d.beta_re != 0.0 || d.beta_im != 0.0);
+      for (int e = 0; e < 4; ++e) cbase[(int64_t)(4 * half + e) * d.sC] = q4v[e];
+    }
+    return;
+  }
+  // complex alpha / beta: this half's component e pairs with the other half's
+  // e; both C values are read before the exchange barrier, written after it
+  const bool use_beta = (d.beta_re != 0.0 || d.beta_im != 0.0);
+  double cown[4] = {0.0, 0.0, 0.0, 0.0}, coth[4] = {0.0, 0.0, 0.0, 0.0};
+  if (valid && use_beta) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      double re = d.alpha_re * q8[e] - d.alpha_im * q8[e + 4];
-      double im = d.alpha_re * q8[e + 4] + d.alpha_im * q8[e];
-      if (use_beta) {
-        const double cr = cbase[(int64_t)e * d.sC], ci = cbase[(int64_t)(e + 4) * d.sC];
-        re += d.beta_re * cr - d.beta_im * ci;
-        im += d.beta_re * ci + d.beta_im * cr;
-      }
-      cbase[(int64_t)e * d.sC] = re;
-      cbase[(int64_t)(e + 4) * d.sC] = im;
+      cown[e] = cbase[(int64_t)(4 * half + e) * d.sC];
+      coth[e] = cbase[(int64_t)(4 * (1 - half) + e) * d.sC];
     }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e) xch[4 * half + e][col] = q4v[e];
+  __syncthreads();
+  if (!valid) return;
+  // half 0: re = a_r Q_e - a_i Q_{e+4} + b_r C_e - b_i C_{e+4}
+  // half 1: im = a_r Q_{e+4} + a_i Q_e + b_r C_{e+4} + b_i C_e
+  const double sgn = half ? 1.0 : -1.0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const double qo = xch[4 * (1 - half) + e][col];
+    double v = d.alpha_re * q4v[e] + sgn * d.alpha_im * qo;
+    if (use_beta) v += d.beta_re * cown[e] + sgn * d.beta_im * coth[e];
+    cbase[(int64_t)(4 * half + e) * d.sC] = v;
   }
 }
 
@@ -724,6 +751,7 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
     for (int x = 1; x < p; ++x)
       if ((4 * x) % p == 1) { inv4 = x; break; }
     m.inv4 = inv4;
+    m.pbias = 12582912.0f + (float)p;
     m.fm = ~0ull / (unsigned long long)p + 1ull;
   }
   cudaError_t e = cudaMemcpyToSymbol(c_mod, mc, sizeof(mc));
@@ -776,9 +804,9 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
                              cudaStream_t s, unsigned char* ws, int max_nmod) {
   if (units <= 0) return cudaSuccess;
-  // 4 limbs hold sum_l r_l c_l while nmod * 255 * P < 2^128 (nmod <= 14)
-  if (max_nmod <= 14) split_crt_kernel<4><<<(unsigned)units, kCrtThreads, 0, s>>>(d_jobs, njobs, d_plans, ws);
-  else split_crt_kernel<kLimbs><<<(unsigned)units, kCrtThreads, 0, s>>>(d_jobs, njobs, d_plans, ws);
+  // 4 limbs hold sum_l (r_l + p_l) c_l < nmod * 383 * P below 2^128 (nmod <= 14)
+  if (max_nmod <= 14) split_crt_kernel<4><<<(unsigned)units, 2 * kCrtCols, 0, s>>>(d_jobs, njobs, d_plans, ws);
+  else split_crt_kernel<kLimbs><<<(unsigned)units, 2 * kCrtCols, 0, s>>>(d_jobs, njobs, d_plans, ws);
   return cudaGetLastError();
 }
 
