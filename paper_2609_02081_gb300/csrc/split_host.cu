@@ -34,7 +34,9 @@ hmat_status split_params(int64_t k, double tol, SplitParams* out) {
   if (want + 2 > 52) return HMAT_STATUS_TOLERANCE_UNREACHABLE;
   int bits = std::max(10, std::min(52, want + kBitsMargin));
   // the exact integer result of one output component is a sum of at most 8 real
-  // products over k of b-bit integers: |Q| <= 8 k 2^(2b); CRT needs P > 2 |Q|
+  // products over k of b-bit integers: |Q| <= 8 k 2^(2b); CRT needs P > 2 |Q|,
+  // and the extra 2^0.25 (|Q| < 0.42 P) lets the CRT kernel take the quotient
+  // as the nearest integer to a float estimate of S / P, with no correction
   const double need = 2.0 * bits + std::log2((double)std::max<int64_t>(k, 1)) + 4.0 + 0.25;
   double acc = 0.0;
   int n = 0;

@@ -22,15 +22,15 @@ struct ModConst {
   float c36;    // 2^36 mod p, centred
   float c23;    // 2^23 mod p, in [0, p)
   int inv4;     // 4^-1 mod p
-  float pbias;  // p + 1.5 * 2^23 (residue + p to integer in one add)
+  int kp;       // p ceil(2^21 / p): makes 4Q 4^-1 non-negative
+  uint32_t magic;  // ceil(2^32 / p)
   unsigned long long fm;  // floor(2^64 / p) + 1 (fast exact 32-bit mod)
 };
 
 __constant__ ModConst c_mod[kModTable];
 __constant__ uint32_t c_crt[kMaxModuli + 1][kMaxModuli][kLimbs];  // [nmod][l] CRT basis (P/p_l)*inv_l
 __constant__ uint32_t c_P[kMaxModuli + 1][kLimbs];                // product of the first nmod moduli
-__constant__ uint32_t c_Ph[kMaxModuli + 1][kLimbs];               // floor(P/2)
-__constant__ float c_Pf[kMaxModuli + 1];                          // P / 2^(32 Pbase) as float
+__constant__ float c_Pinv[kMaxModuli + 1];                        // 2^(32 Pbase) / P as float
 __constant__ int c_Pbase[kMaxModuli + 1];                         // limb index one below P's top limb
 
 // ------------------------------------------------------------------ small exact modular helpers
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
     if (sign[c] < 0) X = -X;
     if (LIMBS == 2) {
       xs[c][kk][rr][0] = (float)(int)(X & 0x7FFFFF);
-      xs[c][kk][rr][LIMBS - 1] = (float)(long long)(X >> 23);
+      xs[c][kk][rr][LIMBS - 1] = (float)(int)(X >> 23);   // |X| <= 2^47: a 32-bit conversion
     } else {
       xs[c][kk][rr][0] = (float)(int)(X & 0x3FFFF);
       xs[c][kk][rr][1] = (float)(int)((X >> 18) & 0x3FFFF);
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
 // element: threads [0, kCrtCols) form the four real-part components
 // (M1..M4 of the storage order), threads [kCrtCols, 2 kCrtCols) the four
 // imaginary-part ones (M5..M8); the split is warp-uniform.  The np residue
-// rows of each modulus are prefetched into a three-slot shared-memory ring
+// rows of each modulus are prefetched into a four-slot shared-memory ring
 // with cp.async two moduli ahead.  Per modulus the output residues
 // sum_p w4[e][p] T_p are formed (the paper's recombination for the bilinear
 // plan, __dp4a against the packed weights otherwise), times 4^-1 mod p gives
@@ -462,20 +462,21 @@ __device__ __forceinline__ double limbs_to_double(const uint32_t* xin, int neg, 
     lo <<= lz;
   }
   if (lo != 0 || sticky != 0) hi |= 1ull;         // sticky bit: one correct rounding below
-  const double v = __ull2double_rn(hi);
-  // value = W 2^(32(h-2)) with W ~ hi 2^(32 - lz)
-  const double r = scalbn(v, 32 * (h - 1) - lz + scale_exp);
+  // value = W 2^(32(h-2)) with W ~ hi 2^(32 - lz): hi 2^E, hi in [2^63, 2^64)
+  const int E = 32 * (h - 1) - lz + scale_exp;
+  const int bexp = E + 1086;                      // IEEE biased exponent of hi 2^E
+  if (bexp >= 1 && bexp <= 2046) {
+    // normal result: round hi to 53 bits (nearest, ties to even) and assemble
+    // the bits with integer operations; a mantissa carry bumps the exponent
+    const unsigned long long mant = hi >> 11;
+    const uint32_t rem = (uint32_t)hi & 0x7FFu;
+    const unsigned long long up = (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+    const unsigned long long bits = ((unsigned long long)(bexp - 1) << 52) + mant + up;
+    return __longlong_as_double((long long)(bits | ((unsigned long long)neg << 63)));
+  }
+  const double v = __ull2double_rn(hi);           // subnormal or overflowing result
+  const double r = scalbn(v, E);
   return neg ? -r : r;
-}
-
-// Sign of x - y for L-limb unsigned integers (most significant limb last).
-template <int L>
-__device__ __forceinline__ int cmp_limbs(const uint32_t* x, const uint32_t* y) {
-  int c = 0;
-#pragma unroll
-  for (int q = L - 1; q >= 0; --q)
-    if (c == 0) c = (x[q] > y[q]) - (x[q] < y[q]);
-  return c;
 }
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -484,20 +485,23 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
-// Non-negative residue of 4Q times 4^-1: the centred residue plus p, in
-// [(p-1)/2, (3p+1)/2], as an integer (the bias 1.5 * 2^23 + p is folded into
-// one add).  |4Q * 4^-1| < 2^22 keeps the float conversions exact.
-__device__ __forceinline__ uint32_t residue_plus_p(int q4, const ModConst& mc) {
-  const float qf = __int_as_float(q4 * mc.inv4 + 0x4B400000) - 12582912.0f;
-  const float r = fmod_c(qf, mc);
-  return (uint32_t)(__float_as_int(r + mc.pbias) - 0x4B400000);
+// Residue in [0, p) of 4Q times 4^-1 for |4Q| <= 4572: x = 4Q 4^-1 + K p lies
+// in [0, 2^23) (K p >= 2^21 > 4572 * 254), and with M = ceil(2^32 / p) the
+// quotient floor(x M / 2^32) is exact while x (M p - 2^32) < 2^32, i.e. for
+// x < 2^32 / p (Granlund and Montgomery, division by invariant integers).
+__device__ __forceinline__ uint32_t residue_q4(int q4, const ModConst& mc) {
+  const uint32_t x = (uint32_t)(q4 * mc.inv4 + mc.kp);
+  return x - __umulhi(x, mc.magic) * (uint32_t)mc.p;
 }
 
 template <int L>
 __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs,
                                                                     const KPlan* __restrict__ plans,
                                                                     unsigned char* __restrict__ ws) {
-  constexpr int kStages = 3;
+  // four ring slots, prefetch distance two: the slot refilled at modulus l
+  // was read at l - 2, which every thread has finished once it passes the
+  // barrier of l - 1, so one barrier per modulus suffices
+  constexpr int kStages = 4;
   constexpr int kChunksPerRow = kCrtCols / 16;    // 16-byte cp.async chunks per residue row
   __shared__ uint32_t wpk[8][kMaxProducts / 4];
   __shared__ __align__(16) uint8_t ring[kStages][kMaxProducts][kCrtCols];
@@ -534,7 +538,7 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
   const int cmax = cavail < kChunksPerRow ? (int)cavail : kChunksPerRow;
 
   // prefetch modulus l's np residue rows (kCrtCols bytes each) into ring slot
-  // l % 3: thread tid copies chunk tid (all of them for np <= 32), further
+  // l % 4: thread tid copies chunk tid (all of them for np <= 32), further
   // chunks (larger plans) are computed per modulus
   const int p0 = tid / kChunksPerRow, c0 = tid % kChunksPerRow;
   const bool has0 = tid < np * kChunksPerRow && c0 < cmax;
@@ -588,10 +592,10 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
           v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
       }
       const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
-      ru[0] = residue_plus_p(8 * v[0] - (a + c), mc);
-      ru[1] = residue_plus_p(-8 * v[1] + (a - c), mc);
-      ru[2] = residue_plus_p(-8 * v[2] + (b + dd), mc);
-      ru[3] = residue_plus_p(-8 * v[3] + (b - dd), mc);
+      ru[0] = residue_q4(8 * v[0] - (a + c), mc);
+      ru[1] = residue_q4(-8 * v[1] + (a - c), mc);
+      ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
+      ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
     } else {
       uint32_t tw[kMaxProducts / 4];
 #pragma unroll
@@ -616,15 +620,15 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
         // |o| <= sum_p |w4[e][p]| * 127 < 2^16 and 4^-1 < 2^8: o * 4^-1 is an exact
         // float below 2^24 (int -> float through the 1.5 * 2^23 bias, |o| < 2^22)
         const float of = __int_as_float(o + 0x4B400000) - 12582912.0f;
-        const float r = fmod_c(of * (float)mc.inv4, mc);
-        ru[e] = (uint32_t)(__float_as_int(r + mc.pbias) - 0x4B400000);
+        float r = fmod_c(of * (float)mc.inv4, mc);
+        if (r < 0.f) r += mc.pf;
+        ru[e] = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
       }
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
 #pragma unroll
       for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
-    __syncthreads();             // slot l % 3 is refilled by issue(l + 3)
   }
 
   const bool valid = j < d.n;
@@ -642,53 +646,36 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
         x[q] = (uint32_t)tq;
         carry = tq >> 32;
       }
-      // quotient estimate q = floor(S / P) from the leading limbs (S < nmod * 383 * P)
+      // S = sum_l r_l c_l is congruent to the output X mod P, and the modulus
+      // count leaves |X| < 2^-1.25 P, so S / P lies within 0.42 of the integer
+      // q = (S - X) / P.  The float estimate of S / P from the leading limbs
+      // (S < nmod * 255 * P: relative error ~2^-22, absolute below 10^-3)
+      // rounds to q, and S - q P is X itself, no correction step.
       const int pb = c_Pbase[nm];
       float sf = 0.f;
 #pragma unroll
       for (int q = L - 1; q >= 0; --q)
         if (q >= pb) sf = sf * 4294967296.f + (float)x[q];
-      int qq = (int)floorf(sf / c_Pf[nm]);
-      if (qq < 0) qq = 0;
+      const uint32_t qq = (uint32_t)__float2int_rn(sf * c_Pinv[nm]);
       long long borrow = 0;
       unsigned long long mulc = 0;
 #pragma unroll
-      for (int q = 0; q < L; ++q) {            // x -= qq * P
-        const unsigned long long prod = (unsigned long long)c_P[nm][q] * (uint32_t)qq + mulc;
+      for (int q = 0; q < L; ++q) {            // x = S - qq P modulo 2^(32 L): X in two's complement
+        const unsigned long long prod = (unsigned long long)c_P[nm][q] * qq + mulc;
         mulc = prod >> 32;
         const long long diff = (long long)x[q] - (long long)(uint32_t)prod + borrow;
         x[q] = (uint32_t)diff;
         borrow = diff >> 32;
       }
-      if (borrow < 0) {                        // over-estimate by one: add P back
-        unsigned long long c = 0;
+      const int neg = (int)(x[L - 1] >> 31);
+      if (neg) {                               // |X| = ~x + 1
+        unsigned long long c = 1;
 #pragma unroll
         for (int q = 0; q < L; ++q) {
-          const unsigned long long tq = (unsigned long long)x[q] + c_P[nm][q] + c;
+          const unsigned long long tq = (unsigned long long)(~x[q]) + c;
           x[q] = (uint32_t)tq;
           c = tq >> 32;
         }
-      } else {                                 // under-estimate by one: subtract P
-        if (cmp_limbs<L>(x, c_P[nm]) >= 0) {
-          long long b = 0;
-#pragma unroll
-          for (int q = 0; q < L; ++q) {
-            const long long diff = (long long)x[q] - (long long)c_P[nm][q] + b;
-            x[q] = (uint32_t)diff;
-            b = diff >> 32;
-          }
-        }
-      }
-      int neg = 0;                             // centre: x > P/2 means x - P
-      if (cmp_limbs<L>(x, c_Ph[nm]) > 0) {
-        long long b = 0;
-#pragma unroll
-        for (int q = 0; q < L; ++q) {
-          const long long diff = (long long)c_P[nm][q] - (long long)x[q] + b;
-          x[q] = (uint32_t)diff;
-          b = diff >> 32;
-        }
-        neg = 1;
       }
       q4v[e] = limbs_to_double<L>(x, neg, -(s_i + t_j));
     }
@@ -751,7 +738,8 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
     for (int x = 1; x < p; ++x)
       if ((4 * x) % p == 1) { inv4 = x; break; }
     m.inv4 = inv4;
-    m.pbias = 12582912.0f + (float)p;
+    m.kp = p * (((1 << 21) + p - 1) / p);
+    m.magic = (uint32_t)((1ull << 32) / (unsigned long long)p + 1ull);
     m.fm = ~0ull / (unsigned long long)p + 1ull;
   }
   cudaError_t e = cudaMemcpyToSymbol(c_mod, mc, sizeof(mc));
@@ -760,29 +748,21 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_P, crt_P, sizeof(uint32_t) * (kMaxModuli + 1) * kLimbs);
   if (e != cudaSuccess) return e;
-  uint32_t ph[kMaxModuli + 1][kLimbs];
-  float pf[kMaxModuli + 1];
+  float pinv[kMaxModuli + 1];
   int pb[kMaxModuli + 1];
   for (int n = 0; n <= kMaxModuli; ++n) {
     const uint32_t* P = crt_P + n * kLimbs;
-    uint32_t carry = 0;
-    for (int q = kLimbs - 1; q >= 0; --q) {
-      ph[n][q] = (P[q] >> 1) | (carry << 31);
-      carry = P[q] & 1u;
-    }
     int top = 0;
     for (int q = 0; q < kLimbs; ++q)
       if (P[q]) top = q;
     pb[n] = top > 0 ? top - 1 : 0;
-    float f = 0.f;
-    for (int q = kLimbs - 1; q >= pb[n]; --q) f = f * 4294967296.f + (float)P[q];
-    pf[n] = f > 0.f ? f : 1.f;
+    double f = 0.0;                    // P / 2^(32 pb), then its float reciprocal
+    for (int q = kLimbs - 1; q >= pb[n]; --q) f = f * 4294967296.0 + (double)P[q];
+    pinv[n] = f > 0.0 ? (float)(1.0 / f) : 1.f;
   }
-  e = cudaMemcpyToSymbol(c_Ph, ph, sizeof(ph));
-  if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_Pbase, pb, sizeof(pb));
   if (e != cudaSuccess) return e;
-  return cudaMemcpyToSymbol(c_Pf, pf, sizeof(pf));
+  return cudaMemcpyToSymbol(c_Pinv, pinv, sizeof(pinv));
 }
 
 cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t units, int64_t first_unit,
@@ -804,7 +784,7 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
                              cudaStream_t s, unsigned char* ws, int max_nmod) {
   if (units <= 0) return cudaSuccess;
-  // 4 limbs hold sum_l (r_l + p_l) c_l < nmod * 383 * P below 2^128 (nmod <= 14)
+  // 4 limbs hold sum_l r_l c_l < nmod * 255 * P below 2^128 (nmod <= 14)
   if (max_nmod <= 14) split_crt_kernel<4><<<(unsigned)units, 2 * kCrtCols, 0, s>>>(d_jobs, njobs, d_plans, ws);
   else split_crt_kernel<kLimbs><<<(unsigned)units, 2 * kCrtCols, 0, s>>>(d_jobs, njobs, d_plans, ws);
   return cudaGetLastError();

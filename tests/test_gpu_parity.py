@@ -130,6 +130,59 @@ def test_beta_zero_ignores_nan_and_k_zero_scales(handle, mode):
     np.testing.assert_array_equal(got, want)
 
 
+def _product_tensor():
+    """T[e, c, d]: output component e of the product of storage basis elements c and d (oracle)."""
+    T = np.zeros((8, 8, 8))
+    for c in range(8):
+        for d in range(8):
+            a = np.zeros((8, 1, 1))
+            b = np.zeros((8, 1, 1))
+            a[c] = 1.0
+            b[d] = 1.0
+            T[:, c, d] = oracle.bq_gemm(a, b)[:, 0, 0]
+    return T
+
+
+@pytest.mark.parametrize("tol,k", [(1e-12, 11776), (1e-13, 8900)])
+def test_split_crt_worst_case_magnitude(handle, tol, k):
+    """Outputs at the top of the integer range the modulus count allows.
+
+    Every entry of op(A) is one biquaternion a and every entry of B one b, all
+    eight storage values +-c with c = 2 - 2^-40 (scaled integer 2^b - 2^(b-41)),
+    signs chosen so that all eight real products of one output component add
+    up: |Q| = 8 k (2^b - 2^(b-41))^2.  Each k puts 8 k 2^(2b) just below
+    P / 2^1.25 for the moduli it needs (b = 46 with 14 moduli, 4-limb CRT;
+    b = 50 with 15 moduli, 5 limbs and 3-limb encoding), the least margin the
+    modulus count leaves (|Q| / P = 0.418 and 0.419).  Every output is
+    k N_e c^2 with an integer N_e, and split mode rounds the exact integer
+    once: bit-exact against the rational value.
+    """
+    from fractions import Fraction
+    moduli, bits = hm.split_info(k, tol)
+    P = 1
+    for p in moduli:
+        P *= p
+    assert (len(moduli), bits) == ((14, 46) if tol == 1e-12 else (15, 50))
+    assert 0.41 < 8 * k * (2 ** bits - 2 ** (bits - 41)) ** 2 / P < 0.42
+    T = _product_tensor()
+    signs = np.array([[1.0 if (v >> c) & 1 else -1.0 for c in range(8)] for v in range(256)])
+    Q = np.einsum("sc,ecd,td->est", signs, T, signs)          # [e, sign pattern of a, of b]
+    e_best, sa, sb = np.unravel_index(np.argmax(np.abs(Q)), Q.shape)
+    N = Q[:, sa, sb]
+    assert abs(N[e_best]) == 8.0
+    c = 2.0 - 2.0 ** -40
+    m, n = 3, 5
+    dev = torch.device("cuda")
+    A = torch.from_numpy(np.broadcast_to((signs[sa] * c)[:, None, None], (8, m, k)).copy()).to(dev)
+    B = torch.from_numpy(np.broadcast_to((signs[sb] * c)[:, None, None], (8, k, n)).copy()).to(dev)
+    want = np.array([float(Fraction(int(N[e]) * k) * Fraction(c) ** 2) for e in range(8)])
+    for sign in (1.0, -1.0):            # both signs of the extreme component
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        hm.hmat_bq_gemm(handle, sign * A, B, C, mode="split", tol=tol)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(C.cpu().numpy(), np.broadcast_to((sign * want)[:, None, None], (8, m, n)))
+
+
 def test_strided_views(handle):
     """ld > columns and component strides larger than rows * ld."""
     dev = torch.device("cuda")
