@@ -381,12 +381,13 @@ def ours(args, rank, world, local):
         serial = {"h2d": ev[0].elapsed_time(ev[1]), "product": ev[1].elapsed_time(ev[2]),
                   "d2h": ev[2].elapsed_time(ev[3])}
         serial["total"] = sum(serial.values())
-        # The public call for host-resident operands: hmat_bq_gemm_streamed moves column panels of B and C
-        # behind the products (A copied and encoded once), within a device budget.
+        # The public call for host-resident operands: hmat_bq_gemm_streamed copies blocks of A and B in and
+        # blocks of C out behind the products, within a device budget; the bytes it copies per call come
+        # from the library's plan (hmat_streamed_traffic).
         del ws
         torch.cuda.empty_cache()
         budget = int(args.e2e_budget_gb * (1 << 30))
-        mb, nb, kb, _ = hm.streamed_plan(n, n, n, args.opA, "N", fa, fb, args.mode, args.tol, budget)
+        mb, nb, kb, _ = hm.streamed_plan(n, n, n, args.opA, "N", fa, fb, args.mode, args.tol, budget, handle=h)
         ws_e2e = torch.empty(budget, dtype=torch.uint8, device=dev)
 
         def e2e_step():
@@ -403,9 +404,7 @@ def ours(args, rank, world, local):
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / args.e2e_steps
         got_e2e = Ch.numpy()[:, rows, :]
-        blocks_i = -(-n // mb)
-        h2d = 8 * 8 * n * n * (1 + blocks_i)            # A once, B once per block row
-        d2h = 8 * 8 * n * n
+        h2d, d2h = hm.streamed_traffic(n, n, n, args.opA, "N", fa, fb, args.mode, args.tol, budget, handle=h)
         info["e2e"] = {"value": flops64 / (ems * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": ems,
                        "api": "hmat_bq_gemm_streamed (pinned host A, B, C)", "blocks": [mb, nb, kb],
@@ -682,9 +681,7 @@ def streamed_arm(args, rank, world, local):
         want, t_or, threads = oracle_rows(A.numpy(), B.numpy(), rows)
         got = C.numpy()[:, rows, :]
         err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
-        blocks_i, blocks_j = -(-n // mb), -(-n // nb)
-        h2d = 8 * 8 * n * n * (1 + blocks_i)          # A once per block row, B once per block
-        d2h = 8 * 8 * n * n
+        h2d, d2h = hm.streamed_traffic(n, n, n, mode=args.mode, tol=args.tol, budget=budget, handle=h)
         mods, bits = hm.split_info(kb, args.tol)
         P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ)[0]
         gl, gms = kernels["split_residue_gemm"]

@@ -333,6 +333,19 @@ hmat_status hmat_streamed_plan(hmat_handle handle, int32_t opA, int32_t opB, uin
                                int32_t a_on_host, int32_t b_on_host, int32_t c_on_host,
                                int64_t *mb, int64_t *nb, int64_t *kb, size_t *bytes);
 
+/* Host <-> device bytes the streamed product of these arguments copies per
+ * call, under the plan hmat_streamed_plan gives for the same arguments (the
+ * same handle, budget and residence): *h2d_bytes counts the blocks of
+ * host-resident A and B (present components; A once when kb = k, else once
+ * per column block; B once with the column-block cache of encoded B sides,
+ * else once per block row) and of C when beta_nonzero; *d2h_bytes counts C
+ * (all eight components).  Host-only; handle may be NULL.
+ * Errors: as hmat_streamed_plan. */
+hmat_status hmat_streamed_traffic(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+                                  int64_t m, int64_t n, int64_t k, int32_t mode, double tol, size_t budget,
+                                  int32_t a_on_host, int32_t b_on_host, int32_t c_on_host, int32_t beta_nonzero,
+                                  size_t *h2d_bytes, size_t *d2h_bytes);
+
 /* C <- alpha op(A) op(B) + beta C with A, B, C each in host memory (pinned
  * for copy / compute overlap; pageable works but serialises) or device
  * memory; arguments and layout as hmat_bq_gemm.  `workspace` (device, 256-byte

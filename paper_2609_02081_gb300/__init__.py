@@ -96,6 +96,8 @@ SIGNATURES = {
     "hmat_streamed_plan": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _i32, _dbl, _sz, _i32,
                                           _i32, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_i64),
                                           ctypes.POINTER(_i64), ctypes.POINTER(_sz)]),
+    "hmat_streamed_traffic": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _i32, _dbl, _sz,
+                                             _i32, _i32, _i32, _i32, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "hmat_bq_gemm_streamed": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _dbl, _dbl,
                                              _ptr, _i64, _i64, _ptr, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
                                              _i32, _dbl, _ptr, _sz, _ptr]),
@@ -399,6 +401,18 @@ def streamed_plan(m, n, k, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, mod
     return mb.value, nb.value, kb.value, nbytes.value
 
 
+def streamed_traffic(m, n, k, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, mode="split", tol=0.0,
+                     budget=8 << 30, on_host=(True, True, True), beta_nonzero=False, handle=None):
+    """(host-to-device, device-to-host) bytes one streamed product copies under that plan
+    (hmat_streamed_traffic)."""
+    h2d, d2h = _sz(), _sz()
+    _check(lib().hmat_streamed_traffic(handle.value if handle is not None else None, _op(opA), _op(opB), int(flagsA),
+                                       int(flagsB), int(m), int(n), int(k), _mode(mode), float(tol), int(budget),
+                                       int(on_host[0]), int(on_host[1]), int(on_host[2]), int(bool(beta_nonzero)),
+                                       ctypes.byref(h2d), ctypes.byref(d2h)), "hmat_streamed_traffic")
+    return h2d.value, d2h.value
+
+
 def hmat_bq_gemm_streamed(handle: Handle, A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, alpha=1.0,
                           beta=0.0, mode="split", tol=0.0, budget=None, workspace=None, stream=None):
     """C <- alpha op(A) op(B) + beta C with host (pinned) or device tensors, computed block by block within a
@@ -540,7 +554,7 @@ def hmat_bq_hadamard_block(handle: Handle, X, alpha, flags=0xCC, Z=None, offdiag
 
 
 __all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gemm_grouped", "hmat_workspace_size",
-           "hmat_bq_gemm_split_noalloc", "hmat_bq_gemm_streamed", "streamed_plan", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
+           "hmat_bq_gemm_split_noalloc", "hmat_bq_gemm_streamed", "streamed_plan", "streamed_traffic", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
            "hmat_complex_to_bq", "hmat_bq_hermiticity", "hmat_bq_hadamard_block",
            "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",
            "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]

@@ -18,8 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhmat.so")
-UNITS = ["hmat_capi.cu", "fp64_bilinear.cu", "split_host.cu", "split_kernels.cu", "split_gemm.cu",
-         "isomorph.cu", "elementwise.cu"]
+UNITS = ["hmat_capi.cu", "capi_elementwise.cu", "capi_streamed.cu", "fp64_bilinear.cu", "split_host.cu",
+         "split_kernels.cu", "split_gemm.cu", "isomorph.cu", "elementwise.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

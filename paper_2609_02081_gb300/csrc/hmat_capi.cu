@@ -1,5 +1,7 @@
-// hmat_capi.cu — the C ABI (include/hmat.h): validation, plans, job upload,
-// kernel dispatch, profiling and the device error word.
+// hmat_capi.cu — the C ABI (include/hmat.h) of handles and products:
+// validation, plans, job upload, kernel dispatch, profiling and the device
+// error word.  The element-wise operations are in capi_elementwise.cu, the
+// streamed products in capi_streamed.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,10 +14,7 @@
 #include <new>
 #include <vector>
 
-#include "../../include/hmat.h"
-#include "common.cuh"
-#include "ops.hpp"
-#include "split.hpp"
+#include "capi.hpp"
 
 namespace hmat {
 
@@ -79,66 +78,12 @@ int fp64_max_products();
 cudaError_t launch_iso_map_in(const IsoMapIn& p, cudaStream_t s);
 cudaError_t launch_iso_map_out(const IsoMapOut& p, cudaStream_t s);
 
-constexpr int kPlanSlots = 256;
-constexpr int kStageSlots = 8;
-constexpr int kKernelIds = 14;
-constexpr size_t kGraphCache = 8;
-
 }  // namespace hmat
 
 using namespace hmat;
 
-struct hmat_context {
-  int device = 0;
-  int sm_count = 0;
-  std::mutex mu;
-  // product plans: host pinned copy (immutable once filled) and device table
-  KPlan* h_plans = nullptr;
-  KPlan* d_plans = nullptr;
-  uint32_t plan_key[kPlanSlots];
-  int n_plans = 0;
-  // job-descriptor staging ring
-  struct Slot {
-    JobDesc* h = nullptr;
-    JobDesc* d = nullptr;
-    size_t cap = 0;
-    cudaEvent_t done = nullptr;
-    bool used = false;
-  } slots[kStageSlots];
-  int next_slot = 0;
-  // profiling
-  bool profiling = false;
-  struct Rec { int kernel; cudaEvent_t a, b; };
-  std::vector<Rec> pending;
-  std::vector<cudaEvent_t> event_pool;
-  int64_t launches[kKernelIds] = {0};
-  double total_ms[kKernelIds] = {0};
-  int32_t last_bad = -1;
-  SplitState split;
-  // CUDA graphs of grouped calls (use_graph), keyed by the call arguments
-  struct GraphEntry {
-    std::vector<unsigned char> key;
-    cudaGraphExec_t exec = nullptr;
-    std::vector<JobDesc*> d_fp64;   // one job table per FP64 launch group
-    SplitJob* d_split = nullptr;
-    void release() {
-      if (exec) cudaGraphExecDestroy(exec);
-      for (JobDesc* d : d_fp64)
-        if (d) cudaFree(d);
-      if (d_split) cudaFree(d_split);
-      exec = nullptr; d_fp64.clear(); d_split = nullptr;
-    }
-  };
-  int32_t algo = HMAT_ALGO_BILINEAR;
-  std::vector<GraphEntry> graphs;
-  // streamed products: copy-in / copy-out streams and the slot events, created on first use
-  cudaStream_t s_in = nullptr, s_out = nullptr;
-  static constexpr int kStreamEvents = 16;
-  cudaEvent_t sev[kStreamEvents] = {};
-  bool log = false;                    // HMAT_LOG: one stderr line per product call
-};
 
-namespace {
+namespace hmat {
 
 thread_local char g_last_cuda_error[256] = "";
 
@@ -298,7 +243,7 @@ hmat_status finish_slot(hmat_context* h, int si, cudaStream_t stream) {
   return HMAT_STATUS_SUCCESS;
 }
 
-}  // namespace
+}  // namespace hmat
 
 // ----------------------------------------------------------------- profiling hooks
 namespace hmat {
@@ -324,7 +269,7 @@ SplitState& handle_split(hmat_context* h) { return h->split; }
 }  // namespace hmat
 
 // ----------------------------------------------------------------- dispatch
-namespace {
+namespace hmat {
 
 const int8_t* split_table(hmat_context* h) { return h->split.has_table ? h->split.tile_table : nullptr; }
 
@@ -480,20 +425,8 @@ hmat_status launch_iso_out(hmat_context* h, const Prepared& pr, cudaStream_t str
   return HMAT_STATUS_SUCCESS;
 }
 
-// Split-mode data a streamed product shares between calls (one product per
-// call, never the isomorph route).  a: the workspace still holds the A side
-// (exponents, encoded factor tiles) of the previous call, made from the same A
-// block with the same shape.  b_offset >= 0: the B side lives at that byte
-// offset of the workspace instead of its own layout slot; b_cached: it already
-// holds this B block's data from an earlier call with the same shape.
-struct SplitReuse {
-  bool a = false;
-  int64_t b_offset = -1;
-  bool b_cached = false;
-};
-
 hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse = SplitReuse{}) {
+                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
   std::lock_guard<std::mutex> lock(h->mu);
@@ -615,7 +548,7 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
   return cuda_status(cudaGraphLaunch(h->graphs.back().exec, stream));
 }
 
-}  // namespace
+}  // namespace hmat
 
 // ----------------------------------------------------------------- C ABI
 extern "C" {
@@ -640,7 +573,9 @@ const char* hmat_status_string(hmat_status s) {
   return "unknown status";
 }
 
-namespace {
+}  // extern "C"
+
+namespace hmat {
 
 // Kernel attributes and the constant tables (moduli, CRT basis) are per
 // device and the same for every handle: set once per device and process.
@@ -717,7 +652,9 @@ void log_call(const hmat_context* h, const char* fn, const hmat_gemm_desc& d, in
                (h->algo >= 0 && h->algo <= 2) ? kAlgoNames[h->algo] : "?", hmat_status_string(st));
 }
 
-}  // namespace
+}  // namespace hmat
+
+extern "C" {
 
 hmat_status hmat_create(hmat_handle* handle) {
   if (!handle) return HMAT_STATUS_INVALID_VALUE;
@@ -764,7 +701,9 @@ hmat_status hmat_destroy(hmat_handle h) {
   return HMAT_STATUS_SUCCESS;
 }
 
-namespace {
+}  // extern "C"
+
+namespace hmat {
 
 // Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule).
 hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
@@ -801,7 +740,9 @@ hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const 
   return HMAT_STATUS_SUCCESS;
 }
 
-}  // namespace
+}  // namespace hmat
+
+extern "C" {
 
 hmat_status hmat_workspace_size(hmat_handle h, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
                                 double tol, size_t* bytes) {
@@ -1015,534 +956,5 @@ hmat_status hmat_reset_profile(hmat_handle h) {
   for (int i = 0; i < kKernelIds; ++i) { h->launches[i] = 0; h->total_ms[i] = 0; }
   return st;
 }
-
-// ----------------------------------------------------------------- element-wise and mapping operations
-namespace {
-
-bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
-
-hmat_status on_device(hmat_context* h) {
-  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
-  int cur = -1;
-  if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) return HMAT_STATUS_INVALID_VALUE;
-  return HMAT_STATUS_SUCCESS;
-}
-
-// op(X) is rows x cols; fills v.  X may be null when flags == 0 or the matrix is empty.
-hmat_status make_view(int32_t op, uint32_t flags, int64_t rows, int64_t cols, const double* X, int64_t ld,
-                      int64_t stride, BqView* v) {
-  if (op < 0 || op > 4 || flags > 0xFFu || rows < 0 || cols < 0) return HMAT_STATUS_INVALID_VALUE;
-  const bool tr = op_transposes(op);
-  v->X = X; v->ld = ld; v->cs = stride; v->trans = tr ? 1 : 0; v->flags = flags;
-  for (int c = 0; c < 8; ++c) v->sign[c] = (int8_t)op_sign(op, c);
-  if (rows == 0 || cols == 0 || flags == 0) return HMAT_STATUS_SUCCESS;
-  if (!X) return HMAT_STATUS_INVALID_VALUE;
-  if (ld < std::max<int64_t>(1, tr ? rows : cols) || stride < 0) return HMAT_STATUS_INVALID_VALUE;
-  if (!aligned(X, 8)) return HMAT_STATUS_MISALIGNED;
-  return HMAT_STATUS_SUCCESS;
-}
-
-hmat_status check_out(const double* Y, int64_t ld, int64_t need_ld, int64_t stride, uintptr_t align) {
-  if (!Y || ld < std::max<int64_t>(1, need_ld) || stride < 0) return HMAT_STATUS_INVALID_VALUE;
-  if (!aligned(Y, align)) return HMAT_STATUS_MISALIGNED;
-  return HMAT_STATUS_SUCCESS;
-}
-
-bool tiles_fit(int64_t m, int64_t n) {
-  const int64_t kLim = (int64_t)1 << 30;
-  if (m > kLim || n > kLim) return false;
-  return ((m + 31) / 32) * ((n + 31) / 32) <= 0x7FFFFFFFLL;
-}
-
-}  // namespace
-
-hmat_status hmat_bq_add(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
-                        int64_t n, double alpha_re, double alpha_im, const double* A, int64_t lda, int64_t strideA,
-                        double beta_re, double beta_im, const double* B, int64_t ldb, int64_t strideB, double* C,
-                        int64_t ldc, int64_t strideC, void* stream) {
-  hmat_status st = on_device(h);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  if (!std::isfinite(alpha_re) || !std::isfinite(alpha_im) || !std::isfinite(beta_re) || !std::isfinite(beta_im))
-    return HMAT_STATUS_INVALID_VALUE;
-  AxpbyParams p;
-  std::memset(&p, 0, sizeof(p));
-  if ((st = make_view(opA, flagsA, m, n, A, lda, strideA, &p.a)) != HMAT_STATUS_SUCCESS) return st;
-  if ((st = make_view(opB, flagsB, m, n, B, ldb, strideB, &p.b)) != HMAT_STATUS_SUCCESS) return st;
-  if (m == 0 || n == 0) return HMAT_STATUS_SUCCESS;
-  if (!tiles_fit(m, n)) return HMAT_STATUS_UNSUPPORTED;
-  if ((st = check_out(C, ldc, n, strideC, 8)) != HMAT_STATUS_SUCCESS) return st;
-  // in place is allowed only where each tile is read before it is written
-  if ((C == A && p.a.trans) || (C == B && p.b.trans)) return HMAT_STATUS_INVALID_VALUE;
-  if (!B || flagsB == 0) { p.b.X = nullptr; p.b.flags = 0; }
-  if (!p.b.X) { beta_re = 0.0; beta_im = 0.0; }
-  if (flagsA == 0) p.a.X = nullptr;
-  if (!p.a.X) p.a.flags = 0;
-  p.alpha_re = alpha_re; p.alpha_im = alpha_im; p.beta_re = beta_re; p.beta_im = beta_im;
-  p.kind_a = scalar_kind(alpha_re, alpha_im);
-  p.kind_b = p.b.X ? scalar_kind(beta_re, beta_im) : kScalarZero;
-  p.C = C; p.ldc = ldc; p.sC = strideC; p.m = (int32_t)m; p.n = (int32_t)n;
-  std::lock_guard<std::mutex> lock(h->mu);
-  ProfScope ps(h, 8, static_cast<cudaStream_t>(stream));
-  return cuda_status(launch_axpby(p, static_cast<cudaStream_t>(stream)));
-}
-
-hmat_status hmat_bq_scale(hmat_handle h, int32_t op, uint32_t flags, int64_t m, int64_t n, double alpha_re,
-                          double alpha_im, const double* X, int64_t ldx, int64_t strideX, double* Y, int64_t ldy,
-                          int64_t strideY, void* stream) {
-  return hmat_bq_add(h, op, HMAT_OP_N, flags, 0u, m, n, alpha_re, alpha_im, X, ldx, strideX, 0.0, 0.0, nullptr, 1,
-                     0, Y, ldy, strideY, stream);
-}
-
-hmat_status hmat_bq_trace(hmat_handle h, int32_t op, uint32_t flags, int64_t n, const double* X, int64_t ldx,
-                          int64_t strideX, double* result, void* stream) {
-  hmat_status st = on_device(h);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  TraceParams p;
-  std::memset(&p, 0, sizeof(p));
-  if ((st = make_view(op, flags, n, n, X, ldx, strideX, &p.x)) != HMAT_STATUS_SUCCESS) return st;
-  if (n > ((int64_t)1 << 30)) return HMAT_STATUS_UNSUPPORTED;
-  if (!result) return HMAT_STATUS_INVALID_VALUE;
-  if (!aligned(result, 8)) return HMAT_STATUS_MISALIGNED;
-  if (!X) p.x.flags = 0;
-  p.n = (int32_t)n;
-  p.result = result;
-  std::lock_guard<std::mutex> lock(h->mu);
-  ProfScope ps(h, 11, static_cast<cudaStream_t>(stream));
-  return cuda_status(launch_trace(p, static_cast<cudaStream_t>(stream)));
-}
-
-hmat_status hmat_bq_to_complex(hmat_handle h, int32_t op, uint32_t flags, int64_t m, int64_t n, const double* X,
-                               int64_t ldx, int64_t strideX, double* Z, int64_t ldz, void* stream) {
-  hmat_status st = on_device(h);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  ToComplexParams p;
-  std::memset(&p, 0, sizeof(p));
-  if ((st = make_view(op, flags, m, n, X, ldx, strideX, &p.x)) != HMAT_STATUS_SUCCESS) return st;
-  if (m == 0 || n == 0) return HMAT_STATUS_SUCCESS;
-  if (!tiles_fit(m, n)) return HMAT_STATUS_UNSUPPORTED;
-  if ((st = check_out(Z, ldz, 2 * n, 0, 16)) != HMAT_STATUS_SUCCESS) return st;
-  if (!X) p.x.flags = 0;
-  p.Z = Z; p.ldz = ldz; p.m = (int32_t)m; p.n = (int32_t)n;
-  std::lock_guard<std::mutex> lock(h->mu);
-  ProfScope ps(h, 9, static_cast<cudaStream_t>(stream));
-  return cuda_status(launch_to_complex(p, static_cast<cudaStream_t>(stream)));
-}
-
-hmat_status hmat_complex_to_bq(hmat_handle h, int64_t m, int64_t n, const double* Z, int64_t ldz, double* Y,
-                               int64_t ldy, int64_t strideY, void* stream) {
-  hmat_status st = on_device(h);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  if (m < 0 || n < 0) return HMAT_STATUS_INVALID_VALUE;
-  if (m == 0 || n == 0) return HMAT_STATUS_SUCCESS;
-  if (!tiles_fit(m, n)) return HMAT_STATUS_UNSUPPORTED;
-  if (!Z || ldz < 2 * n) return HMAT_STATUS_INVALID_VALUE;
-  if (!aligned(Z, 16)) return HMAT_STATUS_MISALIGNED;
-  if ((st = check_out(Y, ldy, n, strideY, 8)) != HMAT_STATUS_SUCCESS) return st;
-  FromComplexParams p{Z, ldz, Y, ldy, strideY, (int32_t)m, (int32_t)n};
-  std::lock_guard<std::mutex> lock(h->mu);
-  ProfScope ps(h, 10, static_cast<cudaStream_t>(stream));
-  return cuda_status(launch_from_complex(p, static_cast<cudaStream_t>(stream)));
-}
-
-hmat_status hmat_bq_hermiticity(hmat_handle h, uint32_t flags, int64_t n, const double* X, int64_t ldx,
-                                int64_t strideX, double* result, void* stream) {
-  hmat_status st = on_device(h);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  HermParams p;
-  std::memset(&p, 0, sizeof(p));
-  if ((st = make_view(HMAT_OP_H, flags, n, n, X, ldx, strideX, &p.x)) != HMAT_STATUS_SUCCESS) return st;
-  if (!tiles_fit(n, n)) return HMAT_STATUS_UNSUPPORTED;
-  if (!result) return HMAT_STATUS_INVALID_VALUE;
-  if (!aligned(result, 8)) return HMAT_STATUS_MISALIGNED;
-  if (!X) p.x.flags = 0;
-  p.n = (int32_t)n;
-  p.result = reinterpret_cast<unsigned long long*>(result);
-  std::lock_guard<std::mutex> lock(h->mu);
-  ProfScope ps(h, 12, static_cast<cudaStream_t>(stream));
-  return cuda_status(launch_hermiticity(p, static_cast<cudaStream_t>(stream)));
-}
-
-hmat_status hmat_bq_hadamard_block(hmat_handle h, uint32_t flags, int64_t n, double alpha_re, double alpha_im,
-                                   const double* X, int64_t ldx, int64_t strideX, double* Z, int64_t ldz,
-                                   double* offdiag, void* stream) {
-  hmat_status st = on_device(h);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  if (flags & 0x33u) return HMAT_STATUS_UNSUPPORTED;     // E or G present: the image is not block anti-diagonal
-  if (!std::isfinite(alpha_re) || !std::isfinite(alpha_im) ||
-      std::fabs(alpha_re * alpha_re + alpha_im * alpha_im - 1.0) > 1e-12)
-    return HMAT_STATUS_INVALID_VALUE;
-  HadamardParams p;
-  std::memset(&p, 0, sizeof(p));
-  if ((st = make_view(HMAT_OP_N, flags, n, n, X, ldx, strideX, &p.x)) != HMAT_STATUS_SUCCESS) return st;
-  if (!tiles_fit(n, n)) return HMAT_STATUS_UNSUPPORTED;
-  if (offdiag && !aligned(offdiag, 8)) return HMAT_STATUS_MISALIGNED;
-  if (n > 0 && (st = check_out(Z, ldz, n, 0, 16)) != HMAT_STATUS_SUCCESS) return st;
-  if (!X) p.x.flags = 0;
-  p.alpha_re = alpha_re; p.alpha_im = alpha_im;
-  p.kind = scalar_kind(alpha_re, alpha_im);
-  p.Z = Z; p.ldz = ldz; p.n = (int32_t)n;
-  p.offdiag = reinterpret_cast<unsigned long long*>(offdiag);
-  std::lock_guard<std::mutex> lock(h->mu);
-  ProfScope ps(h, 13, static_cast<cudaStream_t>(stream));
-  return cuda_status(launch_hadamard(p, static_cast<cudaStream_t>(stream)));
-}
-
-// ----------------------------------------------------------------- streamed (out-of-core) products
-namespace {
-
-bool on_host(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    (void)cudaGetLastError();
-    return true;                        // unknown to CUDA: pageable host memory
-  }
-  return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
-}
-
-int64_t blk_bytes(int64_t rows, int64_t cols) { return align_up256(8 * 8 * rows * cols); }
-
-struct StreamedPlan {
-  int64_t mb = 0, nb = 0, kb = 0;
-  int64_t a_blk = 0, b_blk = 0, c_blk = 0;   // bytes of one device slot (0: operand read in place)
-  int64_t ws = 0;                            // product workspace of the largest block
-  int64_t b_region = 0;                      // split mode with a B cache: bytes per column block
-  int64_t n_jblocks = 0;                     // (0: no cache)
-  int64_t total = 0;
-};
-
-hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d, int32_t mode, double tol,
-                          size_t budget, bool a_host, bool b_host, bool c_host, StreamedPlan* out) {
-  if (d.m <= 0 || d.n <= 0) { *out = StreamedPlan{}; return HMAT_STATUS_SUCCESS; }
-  const int64_t m = d.m, n = d.n, k = std::max<int64_t>(d.k, 1);
-  auto round_up = [](int64_t x, int64_t q) { return (x + q - 1) / q * q; };
-  std::vector<int64_t> kbs;
-  for (int64_t kb = k;; kb = round_up((kb + 1) / 2, 64)) {
-    kbs.push_back(kb);
-    if (kb <= 1024) break;
-  }
-  // candidate block shapes in order of preference: with a host-resident
-  // operand first column panels (all rows of C, n split in 4 then 2), which
-  // copy and encode A once and stream B and C panels behind the products;
-  // then square blocks from the whole matrix down to 128
-  std::vector<std::pair<int64_t, int64_t>> shapes;
-  if ((a_host || b_host || c_host) && n >= 512) {
-    shapes.push_back({m, round_up((n + 3) / 4, 128)});
-    shapes.push_back({m, round_up((n + 1) / 2, 128)});
-  }
-  const int64_t top = std::max(m, n);
-  for (int64_t b = round_up(top, 128); b >= 128; b = round_up(b / 2, 128)) {
-    shapes.push_back({b, b});
-    if (b == 128) break;
-  }
-  // Split mode with a host-resident operand and the whole k: first try square
-  // blocks of about a quarter of m and n with every column block's B side
-  // (exponents and encoded tiles) kept in the budget.  Each A block row and
-  // each B column block is then copied and encoded once, and only the first
-  // A and B blocks are copied before the first product.
-  // (Only under the built-in tile rule, whose width depends on n alone: a tuned
-  // table could give a ragged last block row another width than the cached B.)
-  if (mode == HMAT_MODE_SPLIT && algo != HMAT_ALGO_ISOMORPH && (a_host || b_host || c_host) && d.k > 0 &&
-      std::min(m, n) >= 512 && table == nullptr) {
-    KPlan kp;
-    if (!build_plan(d.flagsA, d.flagsB, &kp, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
-      return HMAT_STATUS_INTERNAL;
-    for (int64_t b = round_up((std::min(m, n) + 3) / 4, 128); b >= 256 && kp.np > 0; b = round_up(b / 2, 128)) {
-      StreamedPlan p;
-      p.mb = std::min(m, b);
-      p.nb = std::min(n, b);
-      p.kb = k;
-      p.a_blk = a_host ? blk_bytes(p.mb, p.kb) : 0;
-      p.b_blk = b_host ? blk_bytes(p.kb, p.nb) : 0;
-      p.c_blk = c_host ? blk_bytes(p.mb, p.nb) : 0;
-      hmat_gemm_desc bd = d;
-      bd.m = p.mb; bd.n = p.nb; bd.k = p.kb;
-      size_t ws = 0;
-      hmat_status st = workspace_bytes(algo, table, 1, &bd, mode, tol, &ws);
-      if (st == HMAT_STATUS_UNSUPPORTED) continue;
-      if (st != HMAT_STATUS_SUCCESS) return st;
-      int64_t region = 0;
-      st = split_b_region_bytes(SplitShape{p.mb, p.nb, p.kb, kp.np, kp.nlf, kp.nrf}, tol, table, &region);
-      if (st != HMAT_STATUS_SUCCESS) return st;
-      p.ws = align_up256((int64_t)ws);
-      p.b_region = align_up256(region);
-      p.n_jblocks = (n + p.nb - 1) / p.nb;
-      p.total = 2 * (p.a_blk + p.b_blk + p.c_blk) + p.ws + p.n_jblocks * p.b_region;
-      if ((size_t)p.total <= budget) { *out = p; return HMAT_STATUS_SUCCESS; }
-    }
-  }
-  for (int64_t kb : kbs) {
-    for (const auto& sh : shapes) {
-      StreamedPlan p;
-      p.mb = std::min(m, sh.first);
-      p.nb = std::min(n, sh.second);
-      p.kb = std::min(k, kb);
-      p.a_blk = a_host ? blk_bytes(p.mb, p.kb) : 0;
-      p.b_blk = b_host ? blk_bytes(p.kb, p.nb) : 0;
-      p.c_blk = c_host ? blk_bytes(p.mb, p.nb) : 0;
-      hmat_gemm_desc bd = d;
-      bd.m = p.mb; bd.n = p.nb; bd.k = d.k > 0 ? p.kb : 0;
-      size_t ws = 0;
-      hmat_status st = workspace_bytes(algo, table, 1, &bd, mode, tol, &ws);
-      if (st == HMAT_STATUS_UNSUPPORTED) continue;    // a block too large for one split product
-      if (st != HMAT_STATUS_SUCCESS) return st;
-      p.ws = align_up256((int64_t)ws);
-      p.total = 2 * (p.a_blk + p.b_blk + p.c_blk) + p.ws;
-      if ((size_t)p.total <= budget) { *out = p; return HMAT_STATUS_SUCCESS; }
-    }
-  }
-  return HMAT_STATUS_WORKSPACE_TOO_SMALL;
-}
-
-// Copy an 8-component rows x cols block (present components only) between a
-// strided host matrix and a dense device slot (ld = cols, component stride rows * cols).
-cudaError_t copy_block(const double* src, int64_t sld, int64_t sstride, double* dst, int64_t dld, int64_t dstride,
-                       int64_t rows, int64_t cols, uint32_t flags, cudaMemcpyKind kind, cudaStream_t s) {
-  for (int c = 0; c < 8; ++c) {
-    if (!((flags >> c) & 1u)) continue;
-    cudaError_t e = cudaMemcpy2DAsync(dst + (int64_t)c * dstride, (size_t)dld * 8, src + (int64_t)c * sstride,
-                                      (size_t)sld * 8, (size_t)cols * 8, (size_t)rows, kind, s);
-    if (e != cudaSuccess) return e;
-  }
-  return cudaSuccess;
-}
-
-hmat_status ensure_copy_streams(hmat_context* h) {
-  std::lock_guard<std::mutex> lock(h->mu);
-  cudaError_t e = cudaSuccess;
-  if (!h->s_in) e = cudaStreamCreateWithFlags(&h->s_in, cudaStreamNonBlocking);
-  if (e == cudaSuccess && !h->s_out) e = cudaStreamCreateWithFlags(&h->s_out, cudaStreamNonBlocking);
-  for (int i = 0; e == cudaSuccess && i < hmat_context::kStreamEvents; ++i)
-    if (!h->sev[i]) e = cudaEventCreateWithFlags(&h->sev[i], cudaEventDisableTiming);
-  return cuda_status(e);
-}
-
-}  // namespace
-
-hmat_status hmat_streamed_plan(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
-                               int64_t n, int64_t k, int32_t mode, double tol, size_t budget, int32_t a_on_host,
-                               int32_t b_on_host, int32_t c_on_host, int64_t* mb, int64_t* nb, int64_t* kb,
-                               size_t* bytes) {
-  if (!mb || !nb || !kb || !bytes) return HMAT_STATUS_INVALID_VALUE;
-  if (opA < 0 || opA > 4 || opB < 0 || opB > 4 || m < 0 || n < 0 || k < 0) return HMAT_STATUS_INVALID_VALUE;
-  hmat_gemm_desc d;
-  std::memset(&d, 0, sizeof(d));
-  d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB; d.m = m; d.n = n; d.k = k;
-  StreamedPlan p;
-  hmat_status st = plan_streamed(h ? h->algo : HMAT_ALGO_BILINEAR, h ? split_table(h) : nullptr, d, mode, tol,
-                                 budget, a_on_host != 0, b_on_host != 0, c_on_host != 0, &p);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  *mb = p.mb; *nb = p.nb; *kb = p.kb; *bytes = (size_t)p.total;
-  return HMAT_STATUS_SUCCESS;
-}
-
-namespace {
-hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
-                          int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A, int64_t lda,
-                          int64_t strideA, const double* B, int64_t ldb, int64_t strideB, double beta_re,
-                          double beta_im, double* C, int64_t ldc, int64_t strideC, int32_t mode, double tol,
-                          void* workspace, size_t workspace_bytes, void* stream);
-}  // namespace
-
-hmat_status hmat_bq_gemm_streamed(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
-                                  int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A,
-                                  int64_t lda, int64_t strideA, const double* B, int64_t ldb, int64_t strideB,
-                                  double beta_re, double beta_im, double* C, int64_t ldc, int64_t strideC,
-                                  int32_t mode, double tol, void* workspace, size_t workspace_bytes, void* stream) {
-  const hmat_status st = streamed_impl(h, opA, opB, flagsA, flagsB, m, n, k, alpha_re, alpha_im, A, lda, strideA, B,
-                                       ldb, strideB, beta_re, beta_im, C, ldc, strideC, mode, tol, workspace,
-                                       workspace_bytes, stream);
-  if (st != HMAT_STATUS_SUCCESS && h && h->s_in && h->s_out) {
-    // copies queued before the failure may still touch the host buffers: the
-    // caller's stream completes only after them
-    cudaStream_t cs = static_cast<cudaStream_t>(stream);
-    if (cudaEventRecord(h->sev[15], h->s_in) == cudaSuccess) (void)cudaStreamWaitEvent(cs, h->sev[15], 0);
-    if (cudaEventRecord(h->sev[14], h->s_out) == cudaSuccess) (void)cudaStreamWaitEvent(cs, h->sev[14], 0);
-    (void)cudaGetLastError();
-  }
-  if (h && h->log) {
-    hmat_gemm_desc d;
-    std::memset(&d, 0, sizeof(d));
-    d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB; d.m = m; d.n = n; d.k = k;
-    log_call(h, "hmat_bq_gemm_streamed", d, mode, st);
-  }
-  return st;
-}
-
-namespace {
-hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
-                          int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A, int64_t lda,
-                          int64_t strideA, const double* B, int64_t ldb, int64_t strideB, double beta_re,
-                          double beta_im, double* C, int64_t ldc, int64_t strideC, int32_t mode, double tol,
-                          void* workspace, size_t workspace_bytes, void* stream) {
-  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
-  hmat_gemm_desc d;
-  d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB;
-  d.m = m; d.n = n; d.k = k;
-  d.alpha_re = alpha_re; d.alpha_im = alpha_im; d.beta_re = beta_re; d.beta_im = beta_im;
-  d.A = A; d.lda = lda; d.strideA = strideA;
-  d.B = B; d.ldb = ldb; d.strideB = strideB;
-  d.C = C; d.ldc = ldc; d.strideC = strideC;
-  JobDesc chk;
-  hmat_status st = validate(d, &chk);           // argument checks of the whole product
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
-  if (m == 0 || n == 0) return HMAT_STATUS_SUCCESS;
-  if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
-  const bool need_ab = k > 0;
-  const bool a_host = need_ab && flagsA && on_host(A);
-  const bool b_host = need_ab && flagsB && on_host(B);
-  const bool c_host = on_host(C);
-  StreamedPlan p;
-  st = plan_streamed(h->algo, split_table(h), d, mode, tol, workspace_bytes, a_host, b_host, c_host, &p);
-  if (st != HMAT_STATUS_SUCCESS) return st;
-  if (!workspace) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
-  if ((st = ensure_copy_streams(h)) != HMAT_STATUS_SUCCESS) return st;
-  cudaStream_t cs = static_cast<cudaStream_t>(stream), sin = h->s_in, sout = h->s_out;
-  // device layout: [A slot 0, A slot 1][B slots][C slots][product workspace]
-  unsigned char* base = static_cast<unsigned char*>(workspace);
-  double* a_slot[2] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + p.a_blk)};
-  base += 2 * p.a_blk;
-  double* b_slot[2] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + p.b_blk)};
-  base += 2 * p.b_blk;
-  double* c_slot[2] = {reinterpret_cast<double*>(base), reinterpret_cast<double*>(base + p.c_blk)};
-  base += 2 * p.c_blk;
-  void* ws = base;
-  const bool b_cache = p.n_jblocks > 0;      // B sides of the column blocks at ws + p.ws + J * p.b_region
-  // events: A ready/free, B ready/free, C ready/computed/stored (two slots each) + final
-  cudaEvent_t* ev = h->sev;
-  cudaEvent_t a_ready[2] = {ev[0], ev[1]}, a_free[2] = {ev[2], ev[3]};
-  cudaEvent_t b_ready[2] = {ev[4], ev[5]}, b_free[2] = {ev[6], ev[7]};
-  cudaEvent_t c_ready[2] = {ev[8], ev[9]}, c_done[2] = {ev[10], ev[11]}, c_stored[2] = {ev[12], ev[13]};
-  cudaEvent_t start = ev[14], fin = ev[15];
-  const bool ta = op_transposes(opA), tb = op_transposes(opB);
-  const bool beta_zero = beta_re == 0.0 && beta_im == 0.0;
-  cudaError_t e = cudaEventRecord(start, cs);   // copies wait for work already queued on the caller's stream
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(sin, start, 0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, start, 0);
-  if (e != cudaSuccess) return cuda_status(e);
-  bool a_used[2] = {false, false}, b_used[2] = {false, false}, c_used[2] = {false, false};
-  int a_next = 0, b_next = 0, c_next = 0;
-  int64_t a_tag_i = -1, a_tag_k = -1;
-  int a_cur = 0;
-  // shape and A block of the previous product: in split mode an equal pair lets
-  // the next product reuse A's encoding left in the workspace
-  int64_t prev[5] = {-1, -1, -1, -1, -1};
-  const int64_t kk = std::max<int64_t>(k, 1);
-  const int64_t nk = need_ab ? (kk + p.kb - 1) / p.kb : 1;
-  for (int64_t i0 = 0; i0 < m; i0 += p.mb) {
-    const int64_t mb = std::min(p.mb, m - i0);
-    for (int64_t j0 = 0; j0 < n; j0 += p.nb) {
-      const int64_t nb = std::min(p.nb, n - j0);
-      // C block: a device slot (host C) or C itself
-      const int cslot = c_next;
-      double* dC = C + i0 * ldc + j0;
-      int64_t dldc = ldc, dsC = strideC;
-      if (c_host) {
-        c_next ^= 1;
-        dC = c_slot[cslot]; dldc = p.nb; dsC = p.mb * p.nb;
-        if (c_used[cslot]) {
-          if (!beta_zero) e = cudaStreamWaitEvent(sin, c_stored[cslot], 0);
-          else e = cudaStreamWaitEvent(cs, c_stored[cslot], 0);
-          if (e != cudaSuccess) return cuda_status(e);
-        }
-        if (!beta_zero) {
-          e = copy_block(C + i0 * ldc + j0, ldc, strideC, dC, dldc, dsC, mb, nb, 0xFFu, cudaMemcpyHostToDevice, sin);
-          if (e == cudaSuccess) e = cudaEventRecord(c_ready[cslot], sin);
-          if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, c_ready[cslot], 0);
-          if (e != cudaSuccess) return cuda_status(e);
-        }
-        c_used[cslot] = true;
-      }
-      for (int64_t kc = 0; kc < nk; ++kc) {
-        const int64_t k0 = kc * p.kb, kb = need_ab ? std::min(p.kb, kk - k0) : 0;
-        hmat_gemm_desc bd = d;
-        bd.m = mb; bd.n = nb; bd.k = kb;
-        bd.C = dC; bd.ldc = dldc; bd.strideC = dsC;
-        if (kc > 0) { bd.beta_re = 1.0; bd.beta_im = 0.0; }
-        // A block (rows i0.. of op(A), inner k0..): reused while i0 and k0 stay the same
-        if (need_ab && flagsA) {
-          const int64_t sr = ta ? kb : mb, sc = ta ? mb : kb;   // stored block shape
-          const double* src = ta ? A + k0 * lda + i0 : A + i0 * lda + k0;
-          if (a_host) {
-            if (a_tag_i != i0 || a_tag_k != k0) {
-              a_cur = a_next;
-              a_next ^= 1;
-              if (a_used[a_cur]) e = cudaStreamWaitEvent(sin, a_free[a_cur], 0);
-              if (e == cudaSuccess)
-                e = copy_block(src, lda, strideA, a_slot[a_cur], sc, sr * sc, sr, sc, flagsA, cudaMemcpyHostToDevice,
-                               sin);
-              if (e == cudaSuccess) e = cudaEventRecord(a_ready[a_cur], sin);
-              if (e != cudaSuccess) return cuda_status(e);
-              a_used[a_cur] = true;
-              a_tag_i = i0; a_tag_k = k0;
-            }
-            e = cudaStreamWaitEvent(cs, a_ready[a_cur], 0);
-            if (e != cudaSuccess) return cuda_status(e);
-            bd.A = a_slot[a_cur]; bd.lda = sc; bd.strideA = sr * sc;
-          } else {
-            bd.A = src;
-          }
-        }
-        int bcur = -1;
-        const bool b_reused = b_cache && i0 > 0;  // encoded by the first block row
-        if (need_ab && flagsB && b_reused) {
-          bd.B = b_host ? b_slot[0] : (tb ? B + j0 * ldb + k0 : B + k0 * ldb + j0);   // not read
-          if (b_host) { bd.ldb = tb ? kb : nb; bd.strideB = (tb ? nb : kb) * (tb ? kb : nb); }
-        } else if (need_ab && flagsB) {
-          const int64_t sr = tb ? nb : kb, sc = tb ? kb : nb;
-          const double* src = tb ? B + j0 * ldb + k0 : B + k0 * ldb + j0;
-          if (b_host) {
-            bcur = b_next;
-            b_next ^= 1;
-            if (b_used[bcur]) e = cudaStreamWaitEvent(sin, b_free[bcur], 0);
-            if (e == cudaSuccess)
-              e = copy_block(src, ldb, strideB, b_slot[bcur], sc, sr * sc, sr, sc, flagsB, cudaMemcpyHostToDevice,
-                             sin);
-            if (e == cudaSuccess) e = cudaEventRecord(b_ready[bcur], sin);
-            if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, b_ready[bcur], 0);
-            if (e != cudaSuccess) return cuda_status(e);
-            b_used[bcur] = true;
-            bd.B = b_slot[bcur]; bd.ldb = sc; bd.strideB = sr * sc;
-          } else {
-            bd.B = src;
-          }
-        }
-        const int64_t key[5] = {i0, k0, mb, nb, kb};
-        SplitReuse reuse;
-        reuse.a = mode == HMAT_MODE_SPLIT && need_ab && flagsA && std::equal(key, key + 5, prev);
-        if (b_cache) {
-          reuse.b_offset = p.ws + (j0 / p.nb) * p.b_region;
-          reuse.b_cached = b_reused;
-        }
-        st = run(h, 1, &bd, mode, tol, ws, (size_t)(p.ws + p.n_jblocks * p.b_region), stream, reuse);
-        if (st != HMAT_STATUS_SUCCESS) return st;
-        std::copy(key, key + 5, prev);
-        if (a_host && need_ab && flagsA) {
-          e = cudaEventRecord(a_free[a_cur], cs);
-          if (e != cudaSuccess) return cuda_status(e);
-        }
-        if (bcur >= 0) {
-          e = cudaEventRecord(b_free[bcur], cs);
-          if (e != cudaSuccess) return cuda_status(e);
-        }
-      }
-      if (c_host) {
-        e = cudaEventRecord(c_done[cslot], cs);
-        if (e == cudaSuccess) e = cudaStreamWaitEvent(sout, c_done[cslot], 0);
-        if (e == cudaSuccess)
-          e = copy_block(dC, dldc, dsC, C + i0 * ldc + j0, ldc, strideC, mb, nb, 0xFFu, cudaMemcpyDeviceToHost, sout);
-        if (e == cudaSuccess) e = cudaEventRecord(c_stored[cslot], sout);
-        if (e != cudaSuccess) return cuda_status(e);
-      }
-    }
-  }
-  // the caller's stream completes after the last copy out (and the copy-in stream is idle)
-  e = cudaEventRecord(fin, sout);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fin, 0);
-  if (e == cudaSuccess) e = cudaEventRecord(fin, sin);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(cs, fin, 0);
-  return cuda_status(e);
-}
-}  // namespace
 
 }  // extern "C"

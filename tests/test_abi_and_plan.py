@@ -195,6 +195,34 @@ def test_streamed_plan_fits_budget_and_prefers_whole_k():
     assert ei.value.status == 4
 
 
+def test_streamed_traffic_counts_each_copy():
+    """Bytes one streamed product copies (host-only), for each kind of plan."""
+    m = n = k = 4096
+    X = 64 * m * k                     # one full operand: 8 components of 8 bytes
+    # split mode, quarter blocks with the column-block cache of encoded B: A and B once,
+    # C out once and in once more when beta != 0
+    assert hm.streamed_traffic(m, n, k, mode="split", tol=1e-12, budget=1 << 40) == (2 * X, X)
+    assert hm.streamed_traffic(m, n, k, mode="split", tol=1e-12, budget=1 << 40, beta_nonzero=True) == (3 * X, X)
+    # FP64 column panels (mb = m): one block row, so A and B once
+    assert hm.streamed_traffic(m, n, k, mode="fp64", budget=1 << 40) == (2 * X, X)
+    # present components only; device-resident operands are not copied
+    assert hm.streamed_traffic(m, n, k, flagsA=bi.TRS, mode="fp64", budget=1 << 40)[0] == X // 2 + X
+    assert hm.streamed_traffic(m, n, k, mode="fp64", budget=1 << 40, on_host=(False, False, True)) == (0, X)
+    assert hm.streamed_traffic(m, n, k, mode="fp64", budget=1 << 40, on_host=(False, False, False)) == (0, 0)
+    # whole k without the cache (small budget): B again for every block row
+    mb, nb, kb, _ = hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 30)
+    assert kb == k and mb < m
+    assert hm.streamed_traffic(m, n, k, mode="split", tol=1e-12, budget=1 << 30) == (X + X * (m // mb), X)
+    # k in chunks: A again for every column block as well
+    m = n = 1024
+    k = 65536
+    mb, nb, kb, _ = hm.streamed_plan(m, n, k, mode="split", tol=1e-12, budget=1 << 30)
+    assert kb < k
+    XA, XB = 64 * m * k, 64 * k * n
+    assert hm.streamed_traffic(m, n, k, mode="split", tol=1e-12, budget=1 << 30) == (
+        XA * (n // nb) + XB * (m // mb), 64 * m * n)
+
+
 def test_bench_results_file_resume(tmp_path):
     """bench.py --results: a configuration already in the file is not run again."""
     import json
