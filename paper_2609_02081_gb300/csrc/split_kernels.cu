@@ -566,6 +566,19 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
     for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
 
   const bool structured = P.bilinear_full != 0;
+  // outputs of this half with a nonzero weight (a subalgebra plan leaves some
+  // components identically zero: they skip the sums and convert to +0)
+  uint32_t emask = 0xFu;          // the full plan weights every output
+  if (!structured) {
+    __syncthreads();               // wpk filled
+    emask = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t any = 0;
+      for (int w = 0; w < nw; ++w) any |= wpk[4 * half + e][w];
+      emask |= (any != 0u ? 1u : 0u) << e;
+    }
+  }
   for (int l = 0; l < nm; ++l) {
     issue(l + 2);
     cp_async_wait2();            // modulus l has landed
@@ -597,29 +610,24 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
       ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
       ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
     } else {
-      uint32_t tw[kMaxProducts / 4];
-#pragma unroll
-      for (int w = 0; w < kMaxProducts / 4; ++w) {
+      // np residues packed four to a word, dotted with the packed weights of
+      // this half's outputs; only the plan's words, only outputs with weights
+      int o[4] = {0, 0, 0, 0};
+#pragma unroll 2
+      for (int w = 0; emask != 0u && w < nw; ++w) {
         uint32_t word = 0;
-        if (w < nw) {
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
-            const int p = 4 * w + b;
-            const uint32_t x = p < np ? (uint32_t)slot[p][col] : 0u;
-            word |= x << (8 * b);
-          }
-        }
-        tw[w] = word;
+        for (int b = 0; b < 4; ++b)
+          if (4 * w + b < np) word |= (uint32_t)slot[4 * w + b][col] << (8 * b);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        int o = 0;
-#pragma unroll
-        for (int w = 0; w < kMaxProducts / 4; ++w)
-          if (w < nw) o = __dp4a((int)wpk[4 * half + e][w], (int)tw[w], o);
         // |o| <= sum_p |w4[e][p]| * 127 < 2^16 and 4^-1 < 2^8: o * 4^-1 is an exact
         // float below 2^24 (int -> float through the 1.5 * 2^23 bias, |o| < 2^22)
-        const float of = __int_as_float(o + 0x4B400000) - 12582912.0f;
+        const float of = __int_as_float(o[e] + 0x4B400000) - 12582912.0f;
         float r = fmod_c(of * (float)mc.inv4, mc);
         if (r < 0.f) r += mc.pf;
         ru[e] = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
@@ -627,8 +635,10 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
+      if ((emask >> e) & 1u) {
 #pragma unroll
-      for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
+        for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
+      }
   }
 
   const bool valid = j < d.n;
@@ -638,6 +648,7 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
     const int t_j = reinterpret_cast<const int32_t*>(ws + sj.off_texp)[j];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
+      if (!((emask >> e) & 1u)) continue;      // identically zero: +0
       uint32_t x[L];
       unsigned long long carry = 0;
 #pragma unroll
