@@ -1,8 +1,9 @@
-"""Full-size configurations, checked on sampled output elements against the oracle.
+"""Full-size configurations, checked on sampled output elements against the oracle
+and over the whole matrix by a random-vector (Freivalds) check.
 
 The oracle computes C[rows, cols] directly from A's rows and B's columns (the
 plain definition restricted to those elements), so only a small sample has to
-leave the GPU.
+leave the GPU; the Freivalds check compares C x with op(A) (op(B) x).
 """
 import os
 
@@ -40,6 +41,35 @@ def sampled_check(A, B, C, opA, opB, rows, cols):
     return float(np.linalg.norm(got - want) / np.linalg.norm(want))
 
 
+def freivalds(A, B, C, opA, opB, seed):
+    """Whole-matrix check of C = op(A) op(B) (Freivalds): for a random
+    biquaternion vector x, ||C x - op(A) (op(B) x)|| / (||C||_F ||x||), with
+    both sides computed by the oracle on the host.  ||C - C*||_F <= tol ||C*||_F
+    bounds it by tol plus the rounding of the FP64 matrix-vector products."""
+    k = C.shape[2]
+    x = bi.uniform(seed, k, 1).numpy()
+    An, Bn, Cn = A.cpu().numpy(), B.cpu().numpy(), C.cpu().numpy()
+    y1 = oracle.bq_gemm(Cn, x)
+    y2 = oracle.bq_gemm(An, oracle.bq_gemm(Bn, x, opB, "N"), opA, "N")
+    return float(np.linalg.norm(y1 - y2) / (np.linalg.norm(Cn) * np.linalg.norm(x)))
+
+
+def freivalds_gpu(handle, A, B, C, seed):
+    """The same check with the matrix-vector products on the GPU through the
+    library's FP64 mode (n = 1), for operands too large to copy to the host.
+    Those products are compared with the oracle by the other tests, and a wrong
+    tile of C cannot cancel out of both sides."""
+    dev = C.device
+    x = bi.uniform(seed, C.shape[2], 1, device=dev)
+    y1 = torch.empty((8, C.shape[1], 1), dtype=torch.float64, device=dev)
+    t = torch.empty((8, B.shape[1], 1), dtype=torch.float64, device=dev)
+    y2 = torch.empty_like(y1)
+    hm.hmat_bq_gemm(handle, C, x, y1, mode="fp64")
+    hm.hmat_bq_gemm(handle, B, x, t, mode="fp64")
+    hm.hmat_bq_gemm(handle, A, t, y2, mode="fp64")
+    return float(torch.linalg.norm(y1 - y2) / (torch.linalg.norm(C) * torch.linalg.norm(x)))
+
+
 CASES_4096 = [("BQ x BQ, op N,N", bi.BQ, bi.BQ, "N", "N"),
               ("TRS x TRA, op N,N", bi.TRS, bi.TRA, "N", "N"),
               ("BQ x BQ, op(A) = H", bi.BQ, bi.BQ, "H", "N")]
@@ -62,6 +92,30 @@ def test_config_n4096_fock_like(handle, mode, name, fa, fb, opA, opB):
     err = sampled_check(A, B, C, opA, opB, rows, cols)
     assert err <= (1e-14 if mode == "fp64" else TOL), err
     assert torch.isfinite(C).all()
+    fv = freivalds(A, B, C, opA, opB, 7)
+    assert fv <= (1e-14 if mode == "fp64" else TOL + 1e-14), fv
+
+
+def test_config_n8192_split_whole_matrix(handle):
+    """The n = 8192 precision workload (Fock-like, rows scaled over six
+    decades) in split mode: every output element enters a Freivalds check
+    against the oracle, and a 64 x 64 sampled block is compared directly."""
+    dev = torch.device("cuda")
+    n = 8192
+    A = bi.fock_like(103, n, n, row_scale=True, device=dev)
+    B = bi.fock_like(104, n, n, row_scale=True, device=dev)
+    C = torch.full((8, n, n), float("nan"), dtype=torch.float64, device=dev)
+    hm.hmat_bq_gemm(handle, A, B, C, mode="split", tol=TOL)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(n, 64, replace=False))
+    cols = np.sort(rng.choice(n, 64, replace=False))
+    err = sampled_check(A, B, C, "N", "N", rows, cols)
+    assert err <= TOL, err
+    fv = freivalds(A, B, C, "N", "N", 13)
+    assert fv <= TOL + 1e-14, fv
+    fg = freivalds_gpu(handle, A, B, C, 13)       # the form the n = 24576 check uses
+    assert abs(fg - fv) <= 1e-14, (fg, fv)
 
 
 @pytest.mark.skipif(os.environ.get("HMAT_RUN_LARGE") != "1",
@@ -84,9 +138,12 @@ def test_config_n24576_fp64(handle):
     rows = np.sort(rng.choice(n, 64, replace=False))
     cols = np.sort(rng.choice(n, 64, replace=False))
     err = sampled_check(A, B, C, "N", "N", rows, cols)
+    # whole matrix: C x against A (B x); three 39 GB operands stay on the GPU
+    fv = freivalds_gpu(handle, A, B, C, 15)
     print(f"n=24576 fp64: {ms:.0f} ms, {64 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} TFLOP/s 64-equiv, "
-          f"{24 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} executed, sampled error {err:.3e}")
+          f"{24 * 2 * n**3 / (ms * 1e-3) / 1e12:.3f} executed, sampled error {err:.3e}, Freivalds {fv:.3e}")
     assert err <= 1e-14
+    assert fv <= 1e-14
 
 
 def test_streamed_n8192_from_host_equals_in_core(handle):
