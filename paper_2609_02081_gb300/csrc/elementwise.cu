@@ -291,6 +291,9 @@ __global__ void __launch_bounds__(TT * TY) hermiticity_kernel(HermParams p) {
   tri_index(blockIdx.x, &I, &J);
   const int64_t r0 = I * TT, q0 = J * TT;
   const uint32_t flags = p.x.flags & 0xFFu;
+  uint32_t negative = 0;         // op sign bits (a constant index keeps the parameter out of local memory)
+#pragma unroll
+  for (int c = 0; c < 8; ++c) negative |= (p.x.sign[c] < 0 ? 1u : 0u) << c;
   unsigned long long dev = 0;
   auto next_component = [&](int c) {
     while (c < 8 && !((flags >> c) & 1u)) ++c;
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(TT * TY) hermiticity_kernel(HermParams p) {
   if (c < 8) {
     const double* base = p.x.X + (int64_t)c * p.x.cs;
     fetch_tile(base, p.x.ld, true, false, false, r0, q0, p.n, p.n, t1);             // X[r0 + r][q0 + q]
-    fetch_tile(base, p.x.ld, true, true, p.x.sign[c] < 0, r0, q0, p.n, p.n, t2);    // s_c X[q0 + q][r0 + r]
+    fetch_tile(base, p.x.ld, true, true, (negative >> c) & 1u, r0, q0, p.n, p.n, t2);   // s_c X[q0 + q][r0 + r]
   }
   while (c < 8) {
     put_tile(t2, true, s2);
@@ -311,7 +314,7 @@ __global__ void __launch_bounds__(TT * TY) hermiticity_kernel(HermParams p) {
     if (cn < 8) {
       const double* base = p.x.X + (int64_t)cn * p.x.cs;
       fetch_tile(base, p.x.ld, true, false, false, r0, q0, p.n, p.n, t1n);
-      fetch_tile(base, p.x.ld, true, true, p.x.sign[cn] < 0, r0, q0, p.n, p.n, t2n);
+      fetch_tile(base, p.x.ld, true, true, (negative >> cn) & 1u, r0, q0, p.n, p.n, t2n);
     }
 #pragma unroll
     for (int k = 0; k < TT / TY; ++k) {

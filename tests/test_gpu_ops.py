@@ -157,6 +157,28 @@ def test_hermiticity(handle, n):
         assert np.isnan(hm.hmat_bq_hermiticity(handle, P).cpu().numpy()[0])
 
 
+@pytest.mark.parametrize("n", [33, 65, 130])
+def test_hermiticity_views_with_even_pitch(handle, n):
+    """n x n views of an (n + 1) or (n + 2) wide buffer (row pitch and
+    component stride larger than the view), ragged tiles, entries of the buffer
+    outside the view NaN (never read), subalgebra flags and a planted
+    deviation."""
+    pitch = n + 1 if n % 2 else n + 2
+    buf = torch.full((8, pitch, pitch), float("nan"), dtype=torch.float64)
+    X = bi.uniform(316 + n, n, n).numpy()
+    Hm = X + oracle.apply_op("H", X)
+    buf[:, :n, :n] = torch.from_numpy(Hm)
+    dbuf = buf.to(DEV)
+    view = dbuf[:, :n, :n]
+    assert view.stride(1) % 2 == 0 and view.stride(0) % 2 == 0
+    for flags in (bi.BQ, bi.TRS, 0x66):
+        assert hm.hmat_bq_hermiticity(handle, view, flags).cpu().numpy()[0] == 0.0
+    dbuf[5, n - 1, 3] += 0.25                 # X[n-1][3] - conj(X[3][n-1]) = 0.25 in component 6
+    got = hm.hmat_bq_hermiticity(handle, view).cpu().numpy()[0]
+    want = ops.hermiticity_deviation(dbuf[:, :n, :n].cpu().numpy())
+    assert got == want and abs(got - 0.25) < 1e-12
+
+
 def _hermitian(seed, n, flags):
     X = bi.uniform(seed, n, n, flags=flags).numpy()
     return bi.apply_flags(torch.from_numpy(X + oracle.apply_op("H", X)), flags)

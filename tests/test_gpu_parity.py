@@ -130,6 +130,25 @@ def test_beta_zero_ignores_nan_and_k_zero_scales(handle, mode):
     np.testing.assert_array_equal(got, want)
 
 
+@pytest.mark.parametrize("tol", [1e-3, 1e-6, 1e-9, 1e-13, 1e-14])
+@pytest.mark.parametrize("fa,fb", [(bi.BQ, bi.BQ), (bi.TRS, bi.TRA), (bi.COMPLEX, bi.BQ)])
+def test_split_tolerance_sweep(handle, tol, fa, fb):
+    """Split mode meets each requested tolerance (relative Frobenius error over
+    all eight components): 6 to 15 moduli, 2- and 3-limb encoding, 4- and
+    5-limb CRT sums, the structured and the generic recombination, ragged
+    shapes."""
+    m, n, k = 150, 70, 333
+    A = bi.uniform(70, m, k, flags=fa)
+    B = bi.uniform(71, k, n, flags=fb)
+    want = oracle.bq_gemm(A.numpy(), B.numpy(), alpha=0.5 + 2j)
+    dev = torch.device("cuda")
+    C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+    hm.hmat_bq_gemm(handle, A.to(dev), B.to(dev), C, "N", "N", fa, fb, 0.5 + 2j, 0.0, mode="split", tol=tol)
+    torch.cuda.synchronize()
+    err = rel(C.cpu().numpy(), want)
+    assert err <= tol, (err, hm.split_info(k, tol))
+
+
 def _product_tensor():
     """T[e, c, d]: output component e of the product of storage basis elements c and d (oracle)."""
     T = np.zeros((8, 8, 8))
