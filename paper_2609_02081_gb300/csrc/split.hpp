@@ -43,6 +43,11 @@ constexpr int kTileK = 64;         // BF16 elements per 128-byte swizzled row
 constexpr int kChunkK = 1024;      // inner steps per exact FP32 accumulation chunk
 constexpr int kTileBins = 16;      // tile-width table: bins of ceil(log2 m) x ceil(log2 n)
 constexpr int kCrtCols = 128;      // CRT output columns per block (two threads per element)
+// Largest sum_p |w4[e][p]| of a plan (the paper's full plan: 8 + 4 x 1 on the
+// three Gauss terms); with centred product residues |T| <= 127 every output
+// residue sum satisfies |4Q| <= 36 * 127 = 4572, which the CRT's integer
+// residue step relies on.  Plans above it are refused.
+constexpr int kMaxWeightSum = 36;
 
 struct SplitParams {
   int nmod = 0;

@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 
 #include "split.hpp"
@@ -149,6 +150,13 @@ static inline int64_t crt_blocks(int64_t m, int64_t n) { return m * ((n + kCrtCo
 // Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
 static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const int8_t* table, SplitJob* sj,
                               int64_t* offset) {
+  if (plan) {                      // the CRT's integer residue step needs |4Q| <= kMaxWeightSum * 127
+    for (int e = 0; e < 8; ++e) {
+      int wsum = 0;
+      for (int q = 0; q < plan->np; ++q) wsum += std::abs((int)plan->w4[e][q]);
+      if (wsum > kMaxWeightSum) return HMAT_STATUS_INTERNAL;
+    }
+  }
   SplitParams sp;
   hmat_status st = split_params(sh.k, tol, &sp);
   if (st != HMAT_STATUS_SUCCESS) return st;

@@ -429,10 +429,11 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
 // sum_p w4[e][p] T_p are formed (the paper's recombination for the bilinear
 // plan, __dp4a against the packed weights otherwise), times 4^-1 mod p gives
 // the residue of the output.  S_e = sum_l r_{l,e} c_l accumulates in 64-bit
-// limbs (c_l the CRT basis), is reduced mod P, centred, converted to FP64 with
-// one rounding and scaled by 2^-(s_i + t_j); then the complex alpha / beta
-// update (Sec. III scaling and addition), for which the two halves trade
-// their four components through shared memory.
+// limbs (c_l the CRT basis); S_e - q P with q the nearest integer to S_e / P is
+// the centred output, converted to FP64 with one rounding and scaled by
+// 2^-(s_i + t_j); then the complex alpha / beta update (Sec. III scaling and
+// addition), for which the two halves trade their four components through
+// shared memory.
 template <int L>
 __device__ __forceinline__ double limbs_to_double(const uint32_t* xin, int neg, int scale_exp) {
   // whole-limb shifts bring the top nonzero limb (index h) to position L - 1;
@@ -485,7 +486,8 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
-// Residue in [0, p) of 4Q times 4^-1 for |4Q| <= 4572: x = 4Q 4^-1 + K p lies
+// Residue in [0, p) of 4Q times 4^-1 for |4Q| <= kMaxWeightSum * 127 = 4572
+// (every plan; checked on the host): x = 4Q 4^-1 + K p lies
 // in [0, 2^23) (K p >= 2^21 > 4572 * 254), and with M = ceil(2^32 / p) the
 // quotient floor(x M / 2^32) is exact while x (M p - 2^32) < 2^32, i.e. for
 // x < 2^32 / p (Granlund and Montgomery, division by invariant integers).
@@ -624,14 +626,7 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel
           if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        // |o| <= sum_p |w4[e][p]| * 127 < 2^16 and 4^-1 < 2^8: o * 4^-1 is an exact
-        // float below 2^24 (int -> float through the 1.5 * 2^23 bias, |o| < 2^22)
-        const float of = __int_as_float(o[e] + 0x4B400000) - 12582912.0f;
-        float r = fmod_c(of * (float)mc.inv4, mc);
-        if (r < 0.f) r += mc.pf;
-        ru[e] = (uint32_t)(__float_as_int(r + 12582912.0f) - 0x4B400000);
-      }
+      for (int e = 0; e < 4; ++e) ru[e] = residue_q4(o[e], mc);   // |o| <= kMaxWeightSum * 127
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
