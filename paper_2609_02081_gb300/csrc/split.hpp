@@ -98,7 +98,8 @@ struct SplitSlot {
   SplitJob* h_jobs = nullptr;
   SplitJob* d_jobs = nullptr;
   size_t cap = 0;
-  cudaEvent_t done = nullptr;
+  cudaEvent_t done = nullptr;       // recorded on the call's stream after its last kernel
+  cudaEvent_t uploaded = nullptr;   // recorded on the upload stream after the table copy
   bool used = false;
 };
 constexpr int kSplitSlots = 2;
@@ -106,6 +107,7 @@ constexpr int kSplitSlots = 2;
 struct SplitState {
   SplitSlot slots[kSplitSlots];
   int next = 0;
+  cudaStream_t upload = nullptr;    // job-table copies, issued when the call is made
   bool has_table = false;
   int8_t tile_table[kTileBins * kTileBins] = {};   // tuned tile widths (0: default rule)
 };

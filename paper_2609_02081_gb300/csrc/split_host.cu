@@ -105,10 +105,13 @@ void split_release(SplitState& s) {
   for (SplitSlot& q : s.slots) {
     if (q.used && q.done) cudaEventSynchronize(q.done);
     if (q.done) cudaEventDestroy(q.done);
+    if (q.uploaded) cudaEventDestroy(q.uploaded);
     if (q.h_jobs) cudaFreeHost(q.h_jobs);
     if (q.d_jobs) cudaFree(q.d_jobs);
     q = SplitSlot();
   }
+  if (s.upload) cudaStreamDestroy(s.upload);
+  s.upload = nullptr;
 }
 
 // ----------------------------------------------------------------- layout
@@ -337,9 +340,28 @@ hmat_status run_split(hmat_context* h, const SplitPrep& sp, const KPlan* d_plans
     s.cap = cap;
   }
   std::memcpy(s.h_jobs, sp.jobs.data(), sp.jobs.size() * sizeof(SplitJob));
-  if (cudaMemcpyAsync(s.d_jobs, s.h_jobs, sp.jobs.size() * sizeof(SplitJob), cudaMemcpyHostToDevice, stream) !=
-      cudaSuccess)
+  // The table is copied on the handle's upload stream when the call is made
+  // (the slot's previous call has finished, synchronised above) and `stream`
+  // waits for it.  A copy in the order of `stream` would be issued only when
+  // the stream reaches it and could then wait behind bulk copies of other
+  // streams on the same copy engine (the operand blocks of a streamed
+  // product), holding up the kernels.  Under stream capture the copy stays
+  // on `stream`.
+  const size_t bytes = sp.jobs.size() * sizeof(SplitJob);
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &capture) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
+  if (capture == cudaStreamCaptureStatusNone) {
+    if (!st_all.upload && cudaStreamCreateWithFlags(&st_all.upload, cudaStreamNonBlocking) != cudaSuccess)
+      return HMAT_STATUS_CUDA_ERROR;
+    if (!s.uploaded && cudaEventCreateWithFlags(&s.uploaded, cudaEventDisableTiming) != cudaSuccess)
+      return HMAT_STATUS_CUDA_ERROR;
+    if (cudaMemcpyAsync(s.d_jobs, s.h_jobs, bytes, cudaMemcpyHostToDevice, st_all.upload) != cudaSuccess ||
+        cudaEventRecord(s.uploaded, st_all.upload) != cudaSuccess ||
+        cudaStreamWaitEvent(stream, s.uploaded, 0) != cudaSuccess)
+      return HMAT_STATUS_CUDA_ERROR;
+  } else if (cudaMemcpyAsync(s.d_jobs, s.h_jobs, bytes, cudaMemcpyHostToDevice, stream) != cudaSuccess) {
     return HMAT_STATUS_CUDA_ERROR;
+  }
   hmat_status st = split_launch(h, sp, s.d_jobs, d_plans, static_cast<unsigned char*>(workspace), stream);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (cudaEventRecord(s.done, stream) != cudaSuccess) return HMAT_STATUS_CUDA_ERROR;
