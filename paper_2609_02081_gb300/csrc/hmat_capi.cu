@@ -665,7 +665,8 @@ hmat_status hmat_create(hmat_handle* handle) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
   if (e == cudaSuccess) e = cudaMallocHost(&h->h_plans, kPlanSlots * sizeof(KPlan));
   if (e == cudaSuccess) e = cudaMalloc(&h->d_plans, kPlanSlots * sizeof(KPlan));
-  for (int i = 0; e == cudaSuccess && i < kStageSlots; ++i) e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
+  for (int i = 0; e == cudaSuccess && i < kStageSlots; ++i)
+    e = cudaEventCreateWithFlags(&h->slots[i].done, cudaEventDisableTiming);
   if (e == cudaSuccess) e = configure_device(h->device);
   if (e != cudaSuccess) {
     hmat_destroy(h);

@@ -497,9 +497,9 @@ __device__ __forceinline__ uint32_t residue_q4(int q4, const ModConst& mc) {
 }
 
 template <int L>
-__global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2) split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs,
-                                                                    const KPlan* __restrict__ plans,
-                                                                    unsigned char* __restrict__ ws) {
+__global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
+    split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs, const KPlan* __restrict__ plans,
+                     unsigned char* __restrict__ ws) {
   // four ring slots, prefetch distance two: the slot refilled at modulus l
   // was read at l - 2, which every thread has finished once it passes the
   // barrier of l - 1, so one barrier per modulus suffices
