@@ -101,13 +101,17 @@ __device__ __forceinline__ void scale_pair(int k, double ar, double ai, double x
   }
 }
 
-// a - b, correctly rounded, as a volatile instruction: it stays inside the
-// branch that guards it (the compiler may otherwise hoist a plain subtraction
-// above the branch and run it for every entry).
-__device__ __forceinline__ double dsub_in_place(double a, double b) {
-  double r;
-  asm volatile("sub.rn.f64 %0, %1, %2;" : "=d"(r) : "d"(a), "d"(b));
-  return r;
+// max |a_k - b_k| (as bit patterns) over the k whose bit is set in `mask`.
+// Not inlined: callers reach it through a warp-uniform branch, and a call
+// keeps its FP64 subtractions behind that branch.
+__device__ __noinline__ unsigned long long max_abs_diff4(double a0, double a1, double a2, double a3, double b0,
+                                                          double b1, double b2, double b3, unsigned mask) {
+  unsigned long long m = 0;
+  if (mask & 1u) m = umax(m, abs_bits(a0 - b0));
+  if (mask & 2u) m = umax(m, abs_bits(a1 - b1));
+  if (mask & 4u) m = umax(m, abs_bits(a2 - b2));
+  if (mask & 8u) m = umax(m, abs_bits(a3 - b3));
+  return m;
 }
 
 // Block max of bit patterns, then one atomicMax.  Every thread of the block
@@ -271,8 +275,11 @@ __global__ void __launch_bounds__(TT * TY) to_complex_tiles_kernel(ToComplexPara
 }
 
 __device__ __forceinline__ void tri_index(int64_t b, int64_t* I, int64_t* J) {
-  // row-major enumeration of the pairs I <= J: b = J (J + 1) / 2 + I
-  int64_t j = (int64_t)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+  // row-major enumeration of the pairs I <= J: b = J (J + 1) / 2 + I (b is a
+  // block index, below 2^32).  A single-precision estimate of J (within one of
+  // it) is corrected in integers: an FP64 square root in every thread kept the
+  // FP64 pipe 84 % busy and halved the kernel's DRAM rate.
+  int64_t j = (int64_t)((sqrtf(8.0f * (float)(uint32_t)b + 1.0f) - 1.0f) * 0.5f);
   while (j * (j + 1) / 2 > b) --j;
   while ((j + 1) * (j + 2) / 2 <= b) ++j;
   *J = j;
@@ -316,18 +323,22 @@ __global__ void __launch_bounds__(TT * TY) hermiticity_kernel(HermParams p) {
       fetch_tile(base, p.x.ld, true, false, false, r0, q0, p.n, p.n, t1n);
       fetch_tile(base, p.x.ld, true, true, (negative >> cn) & 1u, r0, q0, p.n, p.n, t2n);
     }
+    // equal bits of a finite value: deviation 0 without an FP64 instruction.
+    // The subtractions of entries that differ run in a call behind the
+    // warp-uniform test: written inline they were issued for every entry
+    // (predicated off), keeping the FP64 pipe 82 % busy on Hermitian input.
+    static_assert(TT / TY == 4, "max_abs_diff4 takes a thread's four entries");
+    double a[TT / TY], b[TT / TY];
+    unsigned differ = 0;
 #pragma unroll
     for (int k = 0; k < TT / TY; ++k) {
-      const double a = t1.v[k], b = s2[threadIdx.y + k * TY][threadIdx.x];
-      const long long ab = __double_as_longlong(a), bb = __double_as_longlong(b);
-      // equal bits of a finite value: deviation 0 without an FP64 instruction.
-      // The warp-uniform test keeps the subtraction behind a real branch (the
-      // compiler would otherwise evaluate it for every entry and select).
-      const bool differ = ab != bb || ((ab >> 52) & 0x7FF) == 0x7FF;
-      if (__any_sync(0xffffffffu, differ)) {
-        if (differ) dev = umax(dev, abs_bits(dsub_in_place(a, b)));
-      }
+      a[k] = t1.v[k];
+      b[k] = s2[threadIdx.y + k * TY][threadIdx.x];
+      const long long ab = __double_as_longlong(a[k]), bb = __double_as_longlong(b[k]);
+      differ |= (ab != bb || ((ab >> 52) & 0x7FF) == 0x7FF ? 1u : 0u) << k;
     }
+    if (__any_sync(0xffffffffu, differ != 0u)) dev = umax(dev, max_abs_diff4(a[0], a[1], a[2], a[3],
+                                                                            b[0], b[1], b[2], b[3], differ));
     __syncthreads();
     t1 = t1n;
     t2 = t2n;
