@@ -125,6 +125,39 @@ def test_split_parameters(k, tol):
     assert 1024 * 127 * 127 < 2 ** 24
 
 
+def test_split_crt_margin_every_k():
+    """The CRT takes its quotient as the nearest integer to a float estimate of
+    S / P, which needs the exact outputs |Q| <= 8 k 2^(2b) to stay below
+    P / 2^1.25 (|Q| < 0.42 P): every k the library accepts at tol 1e-12, and a
+    spread of k at other tolerances, leaves that margin.  Integer check:
+    (8 k 2^(2b))^4 * 2^5 < P^4."""
+    def margin_ok(k, tol):
+        try:
+            mods, bits = hm.split_info(k, tol)
+        except hm.HmatError:
+            return True
+        P = math.prod(mods)
+        return (8 * k * 4 ** bits) ** 4 * 32 < P ** 4
+    assert all(margin_ok(k, 1e-12) for k in range(1, 127 * 1024 + 1))
+    ks = sorted({1, 3, 100, 127 * 1024} | {2 ** e + d for e in range(2, 17) for d in (-1, 0, 1)})
+    for tol in (1e-3, 1e-6, 1e-9, 1e-13, 1e-14):
+        assert all(margin_ok(k, tol) for k in ks), tol
+
+
+def test_plan_weight_sums_within_the_crt_bound():
+    """Every plan's output weights satisfy sum_p |4 w| <= 36, the bound behind
+    the CRT's integer residue step (|4Q| <= 36 * 127 with centred residues)."""
+    flags = [bi.REAL, bi.COMPLEX, bi.TRS, bi.TRA, bi.BQ, 0x03, 0x55, 0x81]
+    worst = 0.0
+    for algo in ("bilinear", "standard"):
+        for fa, fb in itertools.product(flags, flags):
+            for opA, opB in (("N", "N"), ("H", "N"), ("N", "T"), ("C", "QC")):
+                P, U, V, W, _ = hm.plan_info(opA, opB, fa, fb, algo=algo)
+                if P:
+                    worst = max(worst, float(np.abs(4 * W).sum(axis=1).max()))
+    assert worst <= 36.0, worst
+
+
 def test_split_limits():
     with pytest.raises(hm.HmatError):
         hm.split_info(200000, 1e-12)           # beyond the int32 drained accumulators
