@@ -21,7 +21,8 @@ LIB = os.path.join(LIBDIR, "libhmat.so")
 UNITS = ["hmat_capi.cu", "capi_elementwise.cu", "capi_streamed.cu", "fp64_bilinear.cu", "split_host.cu",
          "split_kernels.cu", "split_gemm.cu", "isomorph.cu", "elementwise.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
+         "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]
 
 

@@ -9,9 +9,8 @@
 
 using namespace hmat;
 
-extern "C" {
-
 // ----------------------------------------------------------------- element-wise and mapping operations
+
 namespace {
 
 bool aligned(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
@@ -50,6 +49,8 @@ bool tiles_fit(int64_t m, int64_t n) {
 }
 
 }  // namespace
+
+extern "C" {
 
 hmat_status hmat_bq_add(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
                         int64_t n, double alpha_re, double alpha_im, const double* A, int64_t lda, int64_t strideA,

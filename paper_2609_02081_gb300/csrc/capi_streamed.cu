@@ -14,9 +14,8 @@
 
 using namespace hmat;
 
-extern "C" {
-
 // ----------------------------------------------------------------- streamed (out-of-core) products
+
 namespace {
 
 bool on_host(const void* p) {
@@ -145,10 +144,6 @@ hmat_status ensure_copy_streams(hmat_context* h) {
   return cuda_status(e);
 }
 
-}  // namespace
-
-namespace {
-
 // Which operands the streamed loop copies: A and B only when they are read
 // (k > 0, components present) and host-resident; C whenever host-resident.
 struct Residence {
@@ -175,6 +170,8 @@ int popcount8(uint32_t f) {
 }
 
 }  // namespace
+
+extern "C" {
 
 hmat_status hmat_streamed_plan(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
                                int64_t n, int64_t k, int32_t mode, double tol, size_t budget, int32_t a_on_host,
@@ -217,6 +214,8 @@ hmat_status hmat_streamed_traffic(hmat_handle h, int32_t opA, int32_t opB, uint3
   return HMAT_STATUS_SUCCESS;
 }
 
+}  // extern "C"
+
 namespace {
 hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
                           int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A, int64_t lda,
@@ -224,6 +223,8 @@ hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flag
                           double beta_im, double* C, int64_t ldc, int64_t strideC, int32_t mode, double tol,
                           void* workspace, size_t workspace_bytes, void* stream);
 }  // namespace
+
+extern "C" {
 
 hmat_status hmat_bq_gemm_streamed(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                                   int64_t m, int64_t n, int64_t k, double alpha_re, double alpha_im, const double* A,
@@ -249,6 +250,8 @@ hmat_status hmat_bq_gemm_streamed(hmat_handle h, int32_t opA, int32_t opB, uint3
   }
   return st;
 }
+
+}  // extern "C"
 
 namespace {
 hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
@@ -426,4 +429,3 @@ hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flag
 }
 }  // namespace
 
-}  // extern "C"
