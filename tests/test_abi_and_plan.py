@@ -36,6 +36,21 @@ def test_library_exports_every_declared_symbol():
     assert L.hmat_status_string(4) == b"workspace too small"
 
 
+def test_library_exports_only_the_c_abi():
+    """The shared library's exported functions are exactly the header's entry
+    points (internal symbols are hidden)."""
+    import shutil
+    import subprocess
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    hm.lib()
+    out = subprocess.run([nm, "-D", "--defined-only", hm.library_path()], capture_output=True, text=True,
+                         check=True).stdout
+    exported = sorted(line.split()[-1] for line in out.splitlines() if line.split()[1:2] == ["T"])
+    assert exported == declared_functions()
+
+
 def test_create_without_gpu_fails_cleanly():
     import torch
     if torch.cuda.is_available():
