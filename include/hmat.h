@@ -145,14 +145,17 @@ typedef struct {
  *                         file keeps the built-in rule and prints a warning. */
 
 /* Library version as major*10000 + minor*100 + patch. */
-HMAT_API int32_t hmat_version(void);
+HMAT_API
+int32_t hmat_version(void);
 
 /* Text for a status code (static storage, never NULL). */
-HMAT_API const char *hmat_status_string(hmat_status s);
+HMAT_API
+const char *hmat_status_string(hmat_status s);
 
 /* Name and text of the CUDA error behind the calling thread's last
  * HMAT_STATUS_CUDA_ERROR ("" if none yet); thread-local storage. */
-HMAT_API const char *hmat_last_cuda_error(void);
+HMAT_API
+const char *hmat_last_cuda_error(void);
 
 /* Create a handle bound to the current CUDA device.  Allocates host-side
  * state only (pinned staging for grouped descriptors).  The first handle on a
@@ -162,16 +165,19 @@ HMAT_API const char *hmat_last_cuda_error(void);
  * handle at a time).  A process that resets a device (cudaDeviceReset) must
  * not use the library on it afterwards.  Errors: INVALID_VALUE (NULL out
  * pointer), CUDA_ERROR. */
-HMAT_API hmat_status hmat_create(hmat_handle *handle);
+HMAT_API
+hmat_status hmat_create(hmat_handle *handle);
 
 /* Destroy a handle (NULL is accepted).  Synchronises nothing; the caller
  * must not destroy a handle whose work is still queued on a stream. */
-HMAT_API hmat_status hmat_destroy(hmat_handle handle);
+HMAT_API
+hmat_status hmat_destroy(hmat_handle handle);
 
 /* Workspace bytes that hmat_bq_gemm / hmat_bq_gemm_grouped need for these
  * problems in this mode (0 for FP64).  descs is a HOST array of `count`
  * descriptors (only op, flags, m, n, k are read).  tol: as for the call. */
-HMAT_API hmat_status hmat_workspace_size(hmat_handle handle, int32_t count,
+HMAT_API
+hmat_status hmat_workspace_size(hmat_handle handle, int32_t count,
                                 const hmat_gemm_desc *descs, int32_t mode,
                                 double tol, size_t *bytes);
 
@@ -185,7 +191,8 @@ HMAT_API hmat_status hmat_workspace_size(hmat_handle handle, int32_t count,
  * TOLERANCE_UNREACHABLE, UNSUPPORTED (any dimension above 2^30; in split
  * mode also m k or k n at or above 2^31, where one factor plane of the
  * encoded operand would exceed 4 GB: use hmat_bq_gemm_streamed), CUDA_ERROR. */
-HMAT_API hmat_status hmat_bq_gemm(hmat_handle handle, int32_t opA, int32_t opB,
+HMAT_API
+hmat_status hmat_bq_gemm(hmat_handle handle, int32_t opA, int32_t opB,
                          uint32_t flagsA, uint32_t flagsB,
                          int64_t m, int64_t n, int64_t k,
                          double alpha_re, double alpha_im,
@@ -204,7 +211,8 @@ HMAT_API hmat_status hmat_bq_gemm(hmat_handle handle, int32_t opA, int32_t opB,
  * on later calls with identical descriptors (the handle keeps the graph).
  * Errors as hmat_bq_gemm; the index of the first bad descriptor is reported
  * by hmat_last_bad_index(). */
-HMAT_API hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
+HMAT_API
+hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
                                  const hmat_gemm_desc *descs, int32_t mode,
                                  double tol, void *workspace,
                                  size_t workspace_bytes, void *stream,
@@ -233,7 +241,8 @@ HMAT_API hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
  *   - No cudaMalloc, cudaFree or other allocating routine is called; the
  *     handle's plan table (allocated by hmat_create) is reused.
  * Arguments, layout and the remaining errors as hmat_bq_gemm. */
-HMAT_API hmat_status hmat_bq_gemm_split_noalloc(hmat_handle handle, int32_t opA, int32_t opB,
+HMAT_API
+hmat_status hmat_bq_gemm_split_noalloc(hmat_handle handle, int32_t opA, int32_t opB,
                                        uint32_t flagsA, uint32_t flagsB,
                                        int64_t m, int64_t n, int64_t k,
                                        double alpha_re, double alpha_im,
@@ -244,16 +253,19 @@ HMAT_API hmat_status hmat_bq_gemm_split_noalloc(hmat_handle handle, int32_t opA,
                                        double tol, void *stream);
 
 /* Bytes of the fixed scratch array used by hmat_bq_gemm_split_noalloc. */
-HMAT_API size_t hmat_split_noalloc_capacity(void);
+HMAT_API
+size_t hmat_split_noalloc_capacity(void);
 
 /* Index of the descriptor that made the last grouped call fail, or -1. */
-HMAT_API int32_t hmat_last_bad_index(hmat_handle handle);
+HMAT_API
+int32_t hmat_last_bad_index(hmat_handle handle);
 
 /* Select the algorithm (hmat_algo) of later hmat_bq_gemm and
  * hmat_bq_gemm_grouped calls on this handle; hmat_workspace_size follows the
  * same setting.  hmat_bq_gemm_split_noalloc always uses BILINEAR.
  * Errors: NOT_INITIALIZED, INVALID_VALUE. */
-HMAT_API hmat_status hmat_set_algorithm(hmat_handle handle, int32_t algo);
+HMAT_API
+hmat_status hmat_set_algorithm(hmat_handle handle, int32_t algo);
 
 /* The product plan of algorithm algo (BILINEAR or STANDARD) for (opA, opB,
  * flagsA, flagsB) — host only, for tests and tools.  On return
@@ -268,14 +280,16 @@ HMAT_API hmat_status hmat_set_algorithm(hmat_handle handle, int32_t algo);
  * Gauss), 1 = component-wise terms with Gauss (chosen when fewer products),
  * 2 = the standard component-wise algorithm.
  * U, V, W may be NULL to query only the count. */
-HMAT_API hmat_status hmat_plan_info(int32_t algo, int32_t opA, int32_t opB, uint32_t flagsA,
+HMAT_API
+hmat_status hmat_plan_info(int32_t algo, int32_t opA, int32_t opB, uint32_t flagsA,
                            uint32_t flagsB, int32_t *n_products, int8_t *U,
                            int8_t *V, double *W, int32_t *strategy);
 
 /* Split-mode parameters for inner dimension k and target tol — host only.
  * On return *n_moduli = L, moduli[0..L-1] the moduli (caller array of >= 32),
  * *bits = the integer width b of the scaled operands (|X| <= 2^b). */
-HMAT_API hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
+HMAT_API
+hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
                             int32_t *moduli, int32_t *bits);
 
 /* Read and clear the device error word (0 = none; otherwise a bit mask:
@@ -285,7 +299,8 @@ HMAT_API hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
  * all handles on that device: a handle reads (and clears) bits that work of
  * any handle set.  Errors: NOT_INITIALIZED, INVALID_VALUE (NULL code, or
  * another device current), CUDA_ERROR. */
-HMAT_API hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
+HMAT_API
+hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
 
 /* Tile-width table for split mode (written by the autotuner,
  * paper_2609_02081_gb300/autotune.py).  table: 16 x 16 int8 codes indexed
@@ -293,7 +308,8 @@ HMAT_API hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
  * 1/2/3 = output tiles 128 x 64 / 128 x 128 / 128 x 256.  NULL restores the
  * built-in rule.  Affects later calls and hmat_workspace_size on this handle.
  * Errors: NOT_INITIALIZED, INVALID_VALUE (a code outside 0..3). */
-HMAT_API hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
+HMAT_API
+hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
 
 /* Failure-detection self-test: launch one thread that waits on a device
  * barrier nothing will ever complete, with the same bounded wait the kernels
@@ -302,7 +318,8 @@ HMAT_API hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table
  * the context stays usable.  hmat_get_device_error then reports 0x20.  Used by
  * the tests to show that a stuck wait ends with an error status, not a hang.
  * Errors: NOT_INITIALIZED, INVALID_VALUE, CUDA_ERROR. */
-HMAT_API hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, void *stream);
+HMAT_API
+hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_cycles, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Streamed products (out of core).  The paper's bilinear product moves its
@@ -336,7 +353,8 @@ HMAT_API hmat_status hmat_debug_wait_selftest(hmat_handle handle, int64_t limit_
  * handle may be NULL (then the default algorithm and tile rule).
  * Errors: INVALID_VALUE, WORKSPACE_TOO_SMALL (nothing fits),
  * TOLERANCE_UNREACHABLE / UNSUPPORTED as hmat_workspace_size. */
-HMAT_API hmat_status hmat_streamed_plan(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+HMAT_API
+hmat_status hmat_streamed_plan(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                                int64_t m, int64_t n, int64_t k, int32_t mode, double tol, size_t budget,
                                int32_t a_on_host, int32_t b_on_host, int32_t c_on_host,
                                int64_t *mb, int64_t *nb, int64_t *kb, size_t *bytes);
@@ -349,7 +367,8 @@ HMAT_API hmat_status hmat_streamed_plan(hmat_handle handle, int32_t opA, int32_t
  * else once per block row) and of C when beta_nonzero; *d2h_bytes counts C
  * (all eight components).  Host-only; handle may be NULL.
  * Errors: as hmat_streamed_plan. */
-HMAT_API hmat_status hmat_streamed_traffic(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+HMAT_API
+hmat_status hmat_streamed_traffic(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                                   int64_t m, int64_t n, int64_t k, int32_t mode, double tol, size_t budget,
                                   int32_t a_on_host, int32_t b_on_host, int32_t c_on_host, int32_t beta_nonzero,
                                   size_t *h2d_bytes, size_t *d2h_bytes);
@@ -365,7 +384,8 @@ HMAT_API hmat_status hmat_streamed_traffic(hmat_handle handle, int32_t opA, int3
  * run concurrently from several host threads.  When the call fails after
  * queueing copies, `stream` still completes only after them.
  * Errors: as hmat_bq_gemm; WORKSPACE_TOO_SMALL when no block plan fits. */
-HMAT_API hmat_status hmat_bq_gemm_streamed(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+HMAT_API
+hmat_status hmat_bq_gemm_streamed(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                                   int64_t m, int64_t n, int64_t k,
                                   double alpha_re, double alpha_im,
                                   const double *A, int64_t lda, int64_t strideA,
@@ -400,21 +420,24 @@ HMAT_API hmat_status hmat_bq_gemm_streamed(hmat_handle handle, int32_t opA, int3
  * of the formula's steps in order: (alpha_R a_e - alpha_I a_{e+4}) +
  * (beta_R b_e - beta_I b_{e+4}) for component e <= 4, and likewise for the
  * imaginary components. */
-HMAT_API hmat_status hmat_bq_add(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
+HMAT_API
+hmat_status hmat_bq_add(hmat_handle handle, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB,
                         int64_t m, int64_t n,
                         double alpha_re, double alpha_im, const double *A, int64_t lda, int64_t strideA,
                         double beta_re, double beta_im, const double *B, int64_t ldb, int64_t strideB,
                         double *C, int64_t ldc, int64_t strideC, void *stream);
 
 /* Y <- alpha op(X) (Sec. III, the alpha q formula); hmat_bq_add without B. */
-HMAT_API hmat_status hmat_bq_scale(hmat_handle handle, int32_t op, uint32_t flags, int64_t m, int64_t n,
+HMAT_API
+hmat_status hmat_bq_scale(hmat_handle handle, int32_t op, uint32_t flags, int64_t m, int64_t n,
                           double alpha_re, double alpha_im, const double *X, int64_t ldx, int64_t strideX,
                           double *Y, int64_t ldy, int64_t strideY, void *stream);
 
 /* result[0] + i result[1] <- Tr[op(X)] = 2 (Tr M1 + i Tr M5) for n x n X
  * (Sec. III trace formula).  One block sums the diagonal in a fixed order, so
  * repeated calls give identical bits. */
-HMAT_API hmat_status hmat_bq_trace(hmat_handle handle, int32_t op, uint32_t flags, int64_t n, const double *X,
+HMAT_API
+hmat_status hmat_bq_trace(hmat_handle handle, int32_t op, uint32_t flags, int64_t n, const double *X,
                           int64_t ldx, int64_t strideX, double *result, void *stream);
 
 /* Z <- the complex 2m x 2n image of op(X): [[E+G, F+H], [-F*+H*, E*-G*]]
@@ -422,7 +445,8 @@ HMAT_API hmat_status hmat_bq_trace(hmat_handle handle, int32_t op, uint32_t flag
  * M+ and M- blocks).  Z is interleaved complex (re, im) doubles, row-major,
  * ldz >= 2n complex elements per row, 16-byte aligned; the input of a
  * complex Hermitian eigensolver when X is Hermitian. */
-HMAT_API hmat_status hmat_bq_to_complex(hmat_handle handle, int32_t op, uint32_t flags, int64_t m, int64_t n,
+HMAT_API
+hmat_status hmat_bq_to_complex(hmat_handle handle, int32_t op, uint32_t flags, int64_t m, int64_t n,
                                const double *X, int64_t ldx, int64_t strideX, double *Z, int64_t ldz,
                                void *stream);
 
@@ -431,13 +455,15 @@ HMAT_API hmat_status hmat_bq_to_complex(hmat_handle handle, int32_t op, uint32_t
  * H = (B + C*)/2 (Eq. mapping-formulas), stored as [E_R, E_I, F_R, F_I, G_I,
  * -G_R, H_I, -H_R].  For a Z that is not an image, Y is the biquaternion whose
  * image is the nearest one (the M+ / M- parts of Z). */
-HMAT_API hmat_status hmat_complex_to_bq(hmat_handle handle, int64_t m, int64_t n, const double *Z, int64_t ldz,
+HMAT_API
+hmat_status hmat_complex_to_bq(hmat_handle handle, int64_t m, int64_t n, const double *Z, int64_t ldz,
                                double *Y, int64_t ldy, int64_t strideY, void *stream);
 
 /* *result <- max over components and entries of |X - X^dagger| (the
  * Hermitian-conjugation signs of Sec. III); 0 exactly when the complex image
  * is Hermitian, NaN if any compared entry is NaN.  n x n X. */
-HMAT_API hmat_status hmat_bq_hermiticity(hmat_handle handle, uint32_t flags, int64_t n, const double *X, int64_t ldx,
+HMAT_API
+hmat_status hmat_bq_hermiticity(hmat_handle handle, uint32_t flags, int64_t n, const double *X, int64_t ldx,
                                 int64_t strideX, double *result, void *stream);
 
 /* Hadamard block reduction (Sec. III C).  X (n x n) must have E and G absent
@@ -451,7 +477,8 @@ HMAT_API hmat_status hmat_bq_hermiticity(hmat_handle handle, uint32_t flags, int
  * offdiag = 0 means M is unitarily equivalent to diag(Z, -Z): pure j
  * (F_R + i H_I) with alpha = +-i, pure k (F_I - i H_R) with alpha = +-1
  * (Eq. reduced-hadamard-pure). */
-HMAT_API hmat_status hmat_bq_hadamard_block(hmat_handle handle, uint32_t flags, int64_t n, double alpha_re,
+HMAT_API
+hmat_status hmat_bq_hadamard_block(hmat_handle handle, uint32_t flags, int64_t n, double alpha_re,
                                    double alpha_im, const double *X, int64_t ldx, int64_t strideX, double *Z,
                                    int64_t ldz, double *offdiag, void *stream);
 
@@ -463,10 +490,13 @@ HMAT_API hmat_status hmat_bq_hadamard_block(hmat_handle handle, uint32_t flags, 
  * 4 split CRT/recombine, 5 beta-scale, 6 isomorph map-in, 7 isomorph
  * map-out, 8 add / scale, 9 to-complex, 10 from-complex, 11 trace,
  * 12 Hermiticity, 13 Hadamard block. */
-HMAT_API hmat_status hmat_set_profiling(hmat_handle handle, int32_t enable);
-HMAT_API hmat_status hmat_get_profile(hmat_handle handle, int32_t kernel_id,
+HMAT_API
+hmat_status hmat_set_profiling(hmat_handle handle, int32_t enable);
+HMAT_API
+hmat_status hmat_get_profile(hmat_handle handle, int32_t kernel_id,
                              int64_t *launches, double *total_ms);
-HMAT_API hmat_status hmat_reset_profile(hmat_handle handle);
+HMAT_API
+hmat_status hmat_reset_profile(hmat_handle handle);
 
 #ifdef __cplusplus
 }
