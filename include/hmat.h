@@ -219,16 +219,21 @@ hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
                                  int32_t use_graph);
 
 /* Split-mode product that allocates nothing: C <- alpha op(A) op(B) + beta C
- * exactly as hmat_bq_gemm with mode HMAT_MODE_SPLIT, but its workspace is a
- * fixed array compiled into this library instead of caller memory.  The paper
- * has no counterpart; it is for callers that cannot allocate device memory
- * (code running under a stream capture or a foreign memory manager, or an
- * embedding that owns every cudaMalloc) and whose products are small.
+ * exactly as hmat_bq_gemm with mode HMAT_MODE_SPLIT (the same kernels, the
+ * same result bits), but its workspace is a fixed array compiled into this
+ * library instead of caller memory.  The paper has no counterpart.  It serves
+ * callers that cannot allocate device memory and whose products are small:
+ * an application whose own memory manager owns every device allocation (a
+ * framework's caching allocator, a pool reserved once at start-up), or a
+ * plug-in whose host forbids cudaMalloc because it synchronises the device
+ * or may fail in the middle of a real-time loop.
  *   - Capacity: hmat_split_noalloc_capacity() bytes (48 MiB), held on every
- *     GPU that loads the library until the process exits.  A product whose
- *     split workspace (hmat_workspace_size) exceeds it is rejected with
- *     HMAT_STATUS_WORKSPACE_TOO_SMALL before anything is launched (full
- *     biquaternions fit up to about m = n = 128 with k <= 256).
+ *     GPU that loads the library until the process exits.  A product is
+ *     accepted when its split workspace, as hmat_workspace_size reports it
+ *     on the same handle, fits; otherwise it is rejected
+ *     with HMAT_STATUS_WORKSPACE_TOO_SMALL before anything is launched.  With
+ *     tol = 1e-12, full biquaternions with m = n = 96 and k = 256 fit, and
+ *     m = n = k = 1024 does not.
  *   - k == 0, or an operand without a present component, returns
  *     HMAT_STATUS_UNSUPPORTED (use hmat_bq_gemm).
  *   - The first call on a device looks up the array's device address

@@ -31,6 +31,10 @@ struct hmat_context {
   hmat::KPlan* h_plans = nullptr;
   hmat::KPlan* d_plans = nullptr;
   uint32_t plan_key[hmat::kPlanSlots];
+  // false while a slot's only upload so far was recorded into a stream
+  // capture: the copy has not run yet, so a later call uploads it again in its
+  // own stream order before using the slot
+  bool plan_resident[hmat::kPlanSlots] = {};
   int n_plans = 0;
   // job-descriptor staging ring
   struct Slot {

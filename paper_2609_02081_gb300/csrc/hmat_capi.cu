@@ -48,6 +48,12 @@ struct NoAllocAddrs {
 static NoAllocAddrs g_noalloc_addrs[kNoAllocMaxDevices];
 static std::mutex g_noalloc_mu;
 
+// Stores a job into the fixed job entry.  The job travels as a kernel
+// argument, which the runtime copies when the launch is made, so nothing on
+// the device ever reads the caller's host memory.
+static_assert(sizeof(SplitJob) <= 4096, "a job must fit the kernel argument space");
+__global__ void noalloc_store_job_kernel(SplitJob job) { g_noalloc_job = job; }
+
 static cudaError_t noalloc_setup(int device, NoAllocAddrs* out) {
   if (device < 0 || device >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
@@ -150,12 +156,35 @@ hmat_status validate(const hmat_gemm_desc& d, JobDesc* out) {
   return HMAT_STATUS_SUCCESS;
 }
 
-// Upload plan i (host copy already filled) on `stream`.
+// Upload plan i (host copy already filled, never rewritten) on `stream`.  A
+// copy recorded into a stream capture runs only when the graph is launched,
+// so the slot stays marked not resident until a call outside any capture has
+// uploaded it in its own stream order.
 hmat_status upload_plan(hmat_context* h, int i, uint32_t key, cudaStream_t stream) {
-  cudaError_t e = cudaMemcpyAsync(h->d_plans + i, h->h_plans + i, sizeof(KPlan), cudaMemcpyHostToDevice, stream);
+  cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+  cudaError_t e = cudaStreamIsCapturing(stream, &capture);
+  if (e != cudaSuccess) return cuda_status(e);
+  e = cudaMemcpyAsync(h->d_plans + i, h->h_plans + i, sizeof(KPlan), cudaMemcpyHostToDevice, stream);
   if (e != cudaSuccess) return cuda_status(e);
   h->plan_key[i] = key;
-  h->n_plans = i + 1;
+  h->plan_resident[i] = capture == cudaStreamCaptureStatusNone;
+  if (h->n_plans <= i) h->n_plans = i + 1;
+  return HMAT_STATUS_SUCCESS;
+}
+
+// Slot of an existing plan with this key (uploaded again if it is not yet
+// resident), or -1.
+hmat_status find_plan(hmat_context* h, uint32_t key, cudaStream_t stream, int* slot) {
+  *slot = -1;
+  for (int i = 0; i < h->n_plans; ++i) {
+    if (h->plan_key[i] != key) continue;
+    if (!h->plan_resident[i]) {
+      hmat_status st = upload_plan(h, i, key, stream);
+      if (st != HMAT_STATUS_SUCCESS) return st;
+    }
+    *slot = i;
+    return HMAT_STATUS_SUCCESS;
+  }
   return HMAT_STATUS_SUCCESS;
 }
 
@@ -167,14 +196,14 @@ uint32_t plan_key_of(int algo, int pass, uint32_t fa, uint32_t fb) {
 // Plan slot for (fa, fb) under algorithm algo; uploads a new plan on `stream` the first time.
 hmat_status plan_slot(hmat_context* h, uint32_t fa, uint32_t fb, int algo, cudaStream_t stream, int* slot) {
   const uint32_t key = plan_key_of(algo, 0, fa, fb);
-  for (int i = 0; i < h->n_plans; ++i)
-    if (h->plan_key[i] == key) { *slot = i; return HMAT_STATUS_SUCCESS; }
+  hmat_status st = find_plan(h, key, stream, slot);
+  if (st != HMAT_STATUS_SUCCESS || *slot >= 0) return st;
   if (h->n_plans >= kPlanSlots) return HMAT_STATUS_UNSUPPORTED;
   KPlan p;
   if (!build_plan(fa, fb, &p, algo)) return HMAT_STATUS_INTERNAL;
   const int i = h->n_plans;
   h->h_plans[i] = p;
-  hmat_status st = upload_plan(h, i, key, stream);
+  st = upload_plan(h, i, key, stream);
   if (st == HMAT_STATUS_SUCCESS) *slot = i;
   return st;
 }
@@ -184,8 +213,8 @@ hmat_status plan_slot(hmat_context* h, uint32_t fa, uint32_t fb, int algo, cudaS
 hmat_status pass_slot(hmat_context* h, int full, int pass, cudaStream_t stream, int* slot) {
   const uint32_t base = h->plan_key[full];
   const uint32_t key = (base & ~(0xFFu << 16)) | ((uint32_t)pass << 16);
-  for (int i = 0; i < h->n_plans; ++i)
-    if (h->plan_key[i] == key) { *slot = i; return HMAT_STATUS_SUCCESS; }
+  hmat_status st = find_plan(h, key, stream, slot);
+  if (st != HMAT_STATUS_SUCCESS || *slot >= 0) return st;
   if (h->n_plans >= kPlanSlots) return HMAT_STATUS_UNSUPPORTED;
   const KPlan& P = h->h_plans[full];
   const int per = fp64_max_products();
@@ -201,7 +230,7 @@ hmat_status pass_slot(hmat_context* h, int full, int pass, cudaStream_t stream, 
   s.bilinear_full = 0;
   const int i = h->n_plans;
   h->h_plans[i] = s;
-  hmat_status st = upload_plan(h, i, key, stream);
+  st = upload_plan(h, i, key, stream);
   if (st == HMAT_STATUS_SUCCESS) *slot = i;
   return st;
 }
@@ -817,8 +846,8 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   NoAllocAddrs a;
   cudaError_t e = noalloc_setup(h->device, &a);
   if (e != cudaSuccess) return cuda_status(e);
-  // the job table is copied from this stack frame (staged by the runtime before the call returns)
-  e = cudaMemcpyAsync(a.job, &sj, sizeof(SplitJob), cudaMemcpyHostToDevice, stream);
+  noalloc_store_job_kernel<<<1, 1, 0, stream>>>(sj);
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = launch_split_exponents(a.job, 1, u.exp, 0, stream, a.scratch);
   if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 0, u.encA, stream, a.scratch, u.max_bits);
   if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 1, u.encB, stream, a.scratch, u.max_bits);

@@ -1,19 +1,24 @@
 """The split-mode entry point that allocates nothing (hmat_bq_gemm_split_noalloc).
 
-Some callers cannot allocate device memory: code that runs while a stream is
-being captured, or an application whose memory manager owns every device
-allocation.  This entry point serves them by keeping the split-mode workspace
-in a fixed array inside the library.  The test calls it through the C ABI
-twice in a row and checks each result against the ordinary workspace-taking
-hmat_bq_gemm, within the tolerance the other parity tests use; it also checks
-that a product too large for the fixed array is refused.  This file sorts last
-so that a run stopping at its first failure has already run every other test.
+Some callers cannot allocate device memory: an application whose own memory
+manager owns every device allocation, or a plug-in whose host forbids
+cudaMalloc because it synchronises the device.  This entry point serves them
+by keeping the split-mode workspace in a fixed array inside the library.
+
+The tests call it through the C ABI, twice in a row with different operands,
+ops and scalars, and require the same bits as the ordinary workspace-taking
+hmat_bq_gemm (both run the same deterministic kernels); on small integers,
+where every step is exact, the result must also equal the CPU oracle.  They
+pin the size limit the header documents and check that a product too large
+for the fixed array is refused.  This file sorts last so that a run stopping
+at its first failure has already run every other test.
 """
 import numpy as np
 import pytest
 import torch
 
 import bq_inputs as bi
+import oracle
 import paper_2609_02081_gb300 as hm
 
 pytestmark = pytest.mark.gpu
@@ -26,39 +31,71 @@ def handle():
         pytest.skip("no GPU")
     with hm.Handle() as h:
         yield h
+        assert h.device_error() == 0
 
 
-def _rel(a, b):
-    return float(torch.linalg.norm(a - b) / torch.linalg.norm(b))
+def _noalloc(handle, A, B, C, opA, opB, fa, fb, alpha, beta):
+    """One call through the raw C ABI on the current stream; returns the status."""
+    L = hm.lib()
+    d = hm.make_desc(A, B, C, opA, opB, fa, fb, alpha, beta)
+    return L.hmat_bq_gemm_split_noalloc(handle.value, d.opA, d.opB, d.flagsA, d.flagsB, d.m, d.n, d.k,
+                                        d.alpha_re, d.alpha_im, d.A, d.lda, d.strideA, d.B, d.ldb, d.strideB,
+                                        d.beta_re, d.beta_im, d.C, d.ldc, d.strideC, TOL,
+                                        torch.cuda.current_stream().cuda_stream)
 
 
-def test_noalloc_matches_workspace_path_twice(handle):
+def test_noalloc_equals_workspace_path_bit_for_bit_twice(handle):
     dev = torch.device("cuda")
     m, n, k = 96, 112, 200
-    calls = [(bi.uniform(501, m, k), bi.uniform(502, k, n), "N", "N", 1.0, 0.0),
-             (bi.fock_like(503, k, m, row_scale=True), bi.uniform(504, n, k), "H", "T", 0.5 - 2j, 1.5 + 0.25j)]
-    C0 = bi.uniform(505, m, n).to(dev)
-    for A, B, opA, opB, alpha, beta in calls:
+    calls = [(bi.uniform(501, m, k), bi.uniform(502, k, n), "N", "N", bi.BQ, bi.BQ, 1.0, 0.0),
+             (bi.fock_like(503, k, m, row_scale=True), bi.uniform(504, n, k), "H", "T", bi.BQ, bi.BQ,
+              0.5 - 2j, 1.5 + 0.25j),
+             (bi.uniform(505, m, k, flags=bi.TRS), bi.uniform(506, k, n, flags=bi.TRA), "C", "QC", bi.TRS, bi.TRA,
+              -1.0 + 1j, 0.0)]
+    C0 = bi.uniform(507, m, n).to(dev)
+    for A, B, opA, opB, fa, fb, alpha, beta in calls:
         A, B = A.to(dev), B.to(dev)
         ref = C0.clone()
-        hm.hmat_bq_gemm(handle, A, B, ref, opA, opB, alpha=alpha, beta=beta, mode="split", tol=TOL)
+        hm.hmat_bq_gemm(handle, A, B, ref, opA, opB, fa, fb, alpha=alpha, beta=beta, mode="split", tol=TOL)
         got = C0.clone()
-        L = hm.lib()
-        d = hm.make_desc(A, B, got, opA, opB, hm.HMAT_BQ, hm.HMAT_BQ, alpha, beta)
-        st = L.hmat_bq_gemm_split_noalloc(handle.value, d.opA, d.opB, d.flagsA, d.flagsB, d.m, d.n, d.k,
-                                          d.alpha_re, d.alpha_im, d.A, d.lda, d.strideA, d.B, d.ldb, d.strideB,
-                                          d.beta_re, d.beta_im, d.C, d.ldc, d.strideC, TOL,
-                                          torch.cuda.current_stream().cuda_stream)
-        assert st == 0, st
+        assert _noalloc(handle, A, B, got, opA, opB, fa, fb, alpha, beta) == 0
         torch.cuda.synchronize()
-        assert torch.isfinite(got).all()
-        assert _rel(got, ref) <= TOL
+        assert torch.equal(got, ref)
+
+
+def test_noalloc_equals_the_oracle_on_small_integers(handle):
+    dev = torch.device("cuda")
+    m, n, k = 70, 90, 130
+    A = bi.small_int(511, k, m)
+    B = bi.small_int(512, k, n)
+    C0 = bi.small_int(513, m, n)
+    want = oracle.bq_gemm(A.numpy(), B.numpy(), "H", "N", alpha=2 - 3j, beta=-1 + 2j, C=C0.numpy())
+    for _ in range(2):
+        got = C0.to(dev)
+        assert _noalloc(handle, A.to(dev), B.to(dev), got, "H", "N", bi.BQ, bi.BQ, 2 - 3j, -1 + 2j) == 0
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(got.cpu().numpy(), want)
+
+
+def test_noalloc_size_limit_is_the_workspace_size(handle):
+    """The documented boundary: with tol 1e-12, m = n = 96, k = 256 full
+    biquaternions fit the fixed array and m = n = k = 1024 does not."""
+    cap = hm.lib().hmat_split_noalloc_capacity()
+    assert cap == 48 << 20
+
+    def need(m, n, k):
+        d = hm.hmat_gemm_desc()              # the size query reads only ops, flags and m, n, k
+        d.opA = d.opB = hm.HMAT_OP_N
+        d.flagsA = d.flagsB = hm.HMAT_BQ
+        d.m, d.n, d.k = m, n, k
+        return hm.hmat_workspace_size(handle, [d], "split", TOL)
+
+    assert need(96, 96, 256) <= cap
+    assert need(1024, 1024, 1024) > cap
 
 
 def test_noalloc_refuses_products_beyond_its_scratch(handle):
     dev = torch.device("cuda")
-    cap = hm.lib().hmat_split_noalloc_capacity()
-    assert cap == 48 << 20
     m = n = k = 1024
     A = torch.zeros((8, m, k), dtype=torch.float64, device=dev)
     B = torch.zeros((8, k, n), dtype=torch.float64, device=dev)
