@@ -316,6 +316,19 @@ hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
 HMAT_API
 hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
 
+/* FP64 throughput of the current device, measured: one launch of a probe
+ * kernel that fills every SM with independent FP64 operations for
+ * `iterations` loop trips, timed with CUDA events on the legacy default
+ * stream (synchronous).  kind 0: scalar DFMA (2 flops per FMA); 1: FP64
+ * tensor-core MMA mma.sync m8n8k4; 2: mma.sync m16n8k4.  On return *tflops =
+ * exact flop count / event time, and *ms (may be NULL) the time.  This is the
+ * denominator of the plain FP64 mode's roofline (the mode's kernel is
+ * DFMA-bound).  About 2^16 iterations give a launch of tens of ms.
+ * Errors: INVALID_VALUE (kind outside 0..2, iterations outside 1..2^30, NULL
+ * tflops), CUDA_ERROR. */
+HMAT_API
+hmat_status hmat_measure_fp64_peak(int32_t kind, int64_t iterations, double *tflops, double *ms);
+
 /* Failure-detection self-test: launch one thread that waits on a device
  * barrier nothing will ever complete, with the same bounded wait the kernels
  * use and a limit of limit_cycles clock cycles (1 .. 2^33).  The wait gives up,

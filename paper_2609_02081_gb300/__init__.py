@@ -90,6 +90,7 @@ SIGNATURES = {
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
     "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
     "hmat_debug_wait_selftest": (ctypes.c_int, [_ptr, _i64, _ptr]),
+    "hmat_measure_fp64_peak": (ctypes.c_int, [_i32, _i64, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
     "hmat_get_profile": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(_i64), ctypes.POINTER(_dbl)]),
     "hmat_reset_profile": (ctypes.c_int, [_ptr]),
@@ -170,6 +171,17 @@ def split_info(k: int, tol: float = 0.0):
     _check(L.hmat_split_info(int(k), float(tol), ctypes.byref(n), mods.ctypes.data, ctypes.byref(bits)),
            "hmat_split_info")
     return [int(x) for x in mods[:n.value]], bits.value
+
+
+FP64_PEAK_KINDS = {"dfma": 0, "dmma_m8n8k4": 1, "dmma_m16n8k4": 2}
+
+
+def measure_fp64_peak(kind="dfma", iterations: int = 1 << 16):
+    """(TFLOP/s, ms) of one FP64 probe launch on the current device (hmat_measure_fp64_peak)."""
+    tf, ms = _dbl(), _dbl()
+    _check(lib().hmat_measure_fp64_peak(FP64_PEAK_KINDS[kind], int(iterations), ctypes.byref(tf), ctypes.byref(ms)),
+           "hmat_measure_fp64_peak")
+    return tf.value, ms.value
 
 
 def _op(op) -> int:

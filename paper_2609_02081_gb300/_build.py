@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libhmat.so")
 UNITS = ["hmat_capi.cu", "capi_elementwise.cu", "capi_streamed.cu", "fp64_bilinear.cu", "split_host.cu",
-         "split_kernels.cu", "split_gemm.cu", "isomorph.cu", "elementwise.cu"]
+         "split_kernels.cu", "split_gemm.cu", "isomorph.cu", "elementwise.cu", "fp64_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr",
