@@ -96,6 +96,35 @@ def test_config_n4096_fock_like(handle, mode, name, fa, fb, opA, opB):
     assert fv <= (1e-14 if mode == "fp64" else TOL + 1e-14), fv
 
 
+# Mixed subalgebras at scale (the reduced plans of Sec. III B, last
+# paragraph: absent terms omitted) and a rectangular product.
+CASES_MIXED = [("R x BQ", bi.REAL, bi.BQ, 4096, 4096, 4096, "N", "N"),
+               ("C x BQ", bi.COMPLEX, bi.BQ, 4096, 4096, 4096, "N", "N"),
+               ("TRS x BQ", bi.TRS, bi.BQ, 4096, 4096, 4096, "N", "N"),
+               ("BQ x TRA, op(B) = H", bi.BQ, bi.TRA, 4096, 4096, 4096, "N", "H"),
+               ("C x C", bi.COMPLEX, bi.COMPLEX, 4096, 4096, 4096, "N", "N"),
+               ("BQ x BQ rectangular 8192 x 2048 x 16384", bi.BQ, bi.BQ, 8192, 2048, 16384, "N", "N")]
+
+
+@pytest.mark.parametrize("mode", ["split", "fp64"])
+@pytest.mark.parametrize("name,fa,fb,m,n,k,opA,opB", CASES_MIXED)
+def test_mixed_subalgebras_and_rectangular_at_scale(handle, mode, name, fa, fb, m, n, k, opA, opB):
+    dev = torch.device("cuda")
+    A = bi.fock_like(211, *((k, m) if opA in ("T", "H") else (m, k)), flags=fa, device=dev)
+    B = bi.fock_like(212, *((n, k) if opB in ("T", "H") else (k, n)), flags=fb, device=dev)
+    C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+    hm.hmat_bq_gemm(handle, A, B, C, opA, opB, fa, fb, mode=mode, tol=TOL)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(23)
+    rows = np.sort(rng.choice(m, 64, replace=False))
+    cols = np.sort(rng.choice(n, 64, replace=False))
+    err = sampled_check(A, B, C, opA, opB, rows, cols)
+    assert err <= (1e-14 if mode == "fp64" else TOL), err
+    assert torch.isfinite(C).all()
+    fv = freivalds(A, B, C, opA, opB, 29)
+    assert fv <= (1e-14 if mode == "fp64" else TOL + 1e-14), fv
+
+
 def test_config_n8192_split_whole_matrix(handle):
     """The n = 8192 precision workload (Fock-like, rows scaled over six
     decades) in split mode: every output element enters a Freivalds check
@@ -116,6 +145,53 @@ def test_config_n8192_split_whole_matrix(handle):
     assert fv <= TOL + 1e-14, fv
     fg = freivalds_gpu(handle, A, B, C, 13)       # the form the n = 24576 check uses
     assert abs(fg - fv) <= 1e-14, (fg, fv)
+
+
+# Component strides above 2^32 bytes (the n = 24576 configuration's 64-bit
+# offsets) in seconds: one operand at 24576 x 24576 (4.8 GB per component),
+# the others thin.  FP64 mode goes through hmat_bq_gemm; split mode's
+# workspace for such a product (hundreds of GB of encoded factors and
+# residues) exceeds HBM, so it runs through the streamed call with the
+# operands left in device memory, whose blocks index the same 24576-row
+# components with 64-bit offsets.
+BIG = 24576
+CASES_64BIT = [("C wide: m = n = 24576, k = 256", BIG, BIG, 256, "N"),
+               ("A large: m = k = 24576, n = 256", BIG, 256, BIG, "N"),
+               ("A large, op(A) = H: m = k = 24576, n = 256", BIG, 256, BIG, "H"),
+               ("B large: n = k = 24576, m = 256", 256, BIG, BIG, "N")]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "split"])
+@pytest.mark.parametrize("name,m,n,k,opA", CASES_64BIT)
+def test_component_strides_beyond_4gb(handle, mode, name, m, n, k, opA):
+    dev = torch.device("cuda")
+    if opA in ("T", "H"):
+        A = bi.fock_like(301, k, m, device=dev)
+    else:
+        A = bi.fock_like(301, m, k, device=dev)
+    B = bi.fock_like(302, k, n, device=dev)
+    C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+    assert max(A.stride(0), B.stride(0), C.stride(0)) * 8 > (1 << 32)
+    if mode == "fp64":
+        hm.hmat_bq_gemm(handle, A, B, C, opA, "N", mode="fp64")
+    else:
+        hm.hmat_bq_gemm_streamed(handle, A, B, C, opA, "N", mode="split", tol=TOL, budget=40 << 30)
+    torch.cuda.synchronize()
+    # The tolerance bounds the relative Frobenius error of the whole matrix, so
+    # the sample must hold entries of the band (|C| ~ 1 near the diagonal of
+    # these banded operands) as well as far ones (down to e^-60 of the band);
+    # the last row and column sit at the largest offsets and are always in.
+    rng = np.random.default_rng(17)
+    rows = np.unique(np.concatenate([rng.choice(min(m, 2048), 12, replace=False),
+                                     rng.choice(m, 12, replace=False), [m - 1]]))
+    cols = np.unique(np.concatenate([rng.choice(min(n, 2048), 12, replace=False),
+                                     rng.choice(n, 12, replace=False), [n - 1]]))
+    err = sampled_check(A, B, C, opA, "N", rows, cols)
+    assert err <= (1e-14 if mode == "fp64" else TOL), err
+    assert torch.isfinite(C).all()
+    if opA == "N":
+        fv = freivalds_gpu(handle, A, B, C, 19)
+        assert fv <= (1e-14 if mode == "fp64" else TOL + 1e-14), fv
 
 
 @pytest.mark.skipif(os.environ.get("HMAT_RUN_LARGE") != "1",
