@@ -7,20 +7,25 @@
 //
 // Exactness: every BF16 product is an integer of magnitude <= 2^14 and FP32
 // partial sums of at most 1024 of them stay <= 2^24, so the tensor-memory
-// accumulator is exact chunk by chunk; each 1024-deep chunk is drained into
-// int32 registers (exact), and the sum is reduced mod p at the end of the item.
+// accumulator is exact chunk by chunk; each 1024-deep chunk is drained, its
+// residue mod p added to a float running sum (exact), and the sum is reduced
+// mod p at the end of the item.
 //
 // Structure (one persistent CTA per SM, 320 threads):
 //   warp 0      producer: 1-D bulk copies (cp.async.bulk, TMA engine) of the
-//               pre-swizzled 16 KB A tile and bn x 128 B B tile per 64-deep
-//               k-block into a 4-stage shared-memory ring (mbarrier tx counts);
+//               pre-swizzled A tile (128 rows x 128 B) and B tile (bn rows x
+//               128 B) per 64-deep k-block into a 4-stage shared-memory ring
+//               (mbarrier tx counts); only the 8-row groups that hold rows of
+//               the product are copied (a 40-row tile moves 5 KB, not 16);
 //   warp 1      allocates 512 TMEM columns; one lane issues tcgen05.mma
 //               (kind::f16, BF16 in, FP32 accumulate, M=128, N=bn, K=16) into
 //               one of two accumulator buffers, commits stages and chunks;
 //   warps 2..9  epilogue: tcgen05.ld of finished chunks (each warp its 32-lane
-//               quadrant and half the columns), int32 accumulation, mod p,
-//               int8 stores.  Two accumulator buffers let chunk c+1 run on the
-//               tensor core while chunk c is drained.
+//               quadrant and half the columns), mod p, int8 stores of the rows
+//               and columns inside the product.  Two accumulator buffers let
+//               chunk c+1 run on the tensor core while chunk c is drained.
+// Each role walks its items in increasing order with a forward cursor over the
+// job table (no search per item).
 // Every mbarrier wait is bounded (~2 s); on timeout the CTA raises the device
 // error word, stops, waits (bounded) for its own copies and MMAs and frees TMEM.
 #include <cuda_runtime.h>
@@ -147,6 +152,8 @@ struct Item {
   int8_t* out;        // residue tile origin (row 0, column 0 of the tile)
   int64_t ncols;      // residue row pitch
   int nkb, bn, l;
+  int rows, cols;     // rows and columns of the tile inside the product (the rest is padding)
+  uint32_t a_bytes, b_bytes;   // bytes copied per k-block: the 8-row groups holding those rows / columns
 };
 
 __device__ __forceinline__ int find_item_job(const SplitJob* jobs, int njobs, int64_t u) {
@@ -159,8 +166,16 @@ __device__ __forceinline__ int find_item_job(const SplitJob* jobs, int njobs, in
   return lo;
 }
 
-__device__ __forceinline__ Item decode_item(const SplitJob* jobs, int njobs, int64_t item, uint8_t* ws) {
-  const SplitJob& sj = jobs[find_item_job(jobs, njobs, item)];
+// Job of `item` for a caller whose items only increase: moves the cursor
+// forward (one load per job boundary passed) instead of searching the whole
+// table for every item.
+__device__ __forceinline__ int advance_job(const SplitJob* jobs, int njobs, int64_t item, int cur) {
+  while (cur + 1 < njobs && __ldg(&jobs[cur + 1].item_begin) <= item) ++cur;
+  return cur;
+}
+
+__device__ __forceinline__ Item decode_item(const SplitJob* jobs, int job, int64_t item, uint8_t* ws) {
+  const SplitJob& sj = jobs[job];
   const int64_t local = item - sj.item_begin;
   const int64_t ntile = (int64_t)sj.tiles_m * sj.tiles_n;
   const int64_t tile = local % ntile;
@@ -178,6 +193,13 @@ __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int njobs, int
   it.nkb = sj.nkb;
   it.bn = sj.bn;
   it.l = l;
+  it.rows = min(kTileM, sj.d.m - tm * kTileM);
+  it.cols = min(sj.bn, sj.d.n - tn * sj.bn);
+  // padding rows hold whatever the workspace held: they meet only padding
+  // rows / columns of the product (D[i][j] sums A row i times B row j), which
+  // nothing stores or reads; the K padding inside a k-block is zero
+  it.a_bytes = (uint32_t)((it.rows + 7) >> 3) * 1024u;
+  it.b_bytes = (uint32_t)((it.cols + 7) >> 3) * 1024u;
   const int64_t a_tile = (int64_t)kATileBytes;
   const int64_t b_tile = (int64_t)sj.bn * kTileK * 2;
   it.a = ws + sj.off_encA + ((int64_t)l * sj.nlf + sj.pl[p]) * sj.encA_plane + ((int64_t)tm * sj.nkb) * a_tile;
@@ -249,15 +271,17 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      int job = find_item_job(jobs, njobs, blockIdx.x);
       for (int64_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
-        const Item it = decode_item(jobs, njobs, item, ws);
-        const uint32_t bbytes = (uint32_t)it.bn * kTileK * 2;
+        job = advance_job(jobs, njobs, item, job);
+        const Item it = decode_item(jobs, job, item, ws);
+        const uint32_t bstride = (uint32_t)it.bn * kTileK * 2;
         for (int kb = 0; kb < it.nkb; ++kb) {
           if (!mbar_wait(smem_u32(&s.empty[stage]), phase ^ 1u, abort_flag, err, kErrWaitProducer)) { ok = false; break; }
           const uint32_t fb = smem_u32(&s.full[stage]);
-          mbar_arrive_tx(fb, (uint32_t)kATileBytes + bbytes);
-          bulk_g2s(smem_u32(s.a[stage]), it.a + (int64_t)kb * kATileBytes, (uint32_t)kATileBytes, fb);
-          bulk_g2s(smem_u32(s.b[stage]), it.b + (int64_t)kb * bbytes, bbytes, fb);
+          mbar_arrive_tx(fb, it.a_bytes + it.b_bytes);
+          bulk_g2s(smem_u32(s.a[stage]), it.a + (int64_t)kb * kATileBytes, it.a_bytes, fb);
+          bulk_g2s(smem_u32(s.b[stage]), it.b + (int64_t)kb * bstride, it.b_bytes, fb);
           armed[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
@@ -280,8 +304,10 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
       uint32_t chunk_ctr = 0;
       bool ok = true;
       bool issued = false;
+      int job = find_item_job(jobs, njobs, blockIdx.x);
       for (int64_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
-        const Item it = decode_item(jobs, njobs, item, ws);
+        job = advance_job(jobs, njobs, item, job);
+        const Item it = decode_item(jobs, job, item, ws);
         const uint32_t idesc = instr_desc(it.bn);
         const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
         for (int c = 0; ok && c < nchunks; ++c) {
@@ -324,12 +350,14 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
     const int row = q * 32 + lane;
     uint32_t chunk_ctr = 0;
     bool ok = true;
+    int job = find_item_job(jobs, njobs, blockIdx.x);
     for (int64_t item = blockIdx.x; ok && item < total_items; item += gridDim.x) {
-      const Item it = decode_item(jobs, njobs, item, ws);
-      const int cols = it.bn >> 1;        // columns handled by this thread: 32, 64 or 128
+      job = advance_job(jobs, njobs, item, job);
+      const Item it = decode_item(jobs, job, item, ws);
+      const int cols = it.bn >> 1;        // columns handled by this thread: a multiple of 16 up to 128
       const int col0 = half * cols;
       const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
-      // running sum of chunk residues (each |r| <= (p+1)/2, at most 127 chunks:
+      // running sum of chunk residues (each |r| <= 129, at most 127 chunks:
       // exact in float)
       const float pf = c_gmod[it.l].pf, pinv = c_gmod[it.l].inv;
       float acc[kBnMax / 2];
@@ -361,27 +389,27 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         ++chunk_ctr;
       }
       if (!ok) break;
-      // reduce mod p to [-127, 127] and store this row's residues (16-byte stores)
-      int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
-      const float half = 0.5f * (pf - 1.f);
+      // reduce mod p to [-(p-1)/2, (p-1)/2] and store this row's residues
+      // (16-byte stores); rows and columns of padding are not stored.  |acc| <=
+      // 129 * 127 < 2^14, where acc * (1/p) is within 2^-9 of acc / p, which
+      // is at least 1/(2p) from a half-integer: the rounding is exact.
+      if (row < it.rows) {
+        int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
 #pragma unroll
-      for (int g = 0; g < kBnMax / 2 / 16; ++g) {
-        if (g * 16 < cols) {
-          uint32_t w[4];
+        for (int g = 0; g < kBnMax / 2 / 16; ++g) {
+          if (g * 16 < cols && col0 + g * 16 < it.cols) {
+            uint32_t w[4];
 #pragma unroll
-          for (int v = 0; v < 4; ++v) {
-            uint32_t packed = 0;
+            for (int v = 0; v < 4; ++v) {
+              // the low byte of (r + 1.5 * 2^23)'s bits is r mod 256 (two's complement)
+              uint32_t u[4];
 #pragma unroll
-            for (int bidx = 0; bidx < 4; ++bidx) {
-              float rr = fmod_centred(acc[g * 16 + v * 4 + bidx], pf, pinv);
-              rr = rr > half ? rr - pf : (rr < -half ? rr + pf : rr);
-              // float -> int through the 1.5 * 2^23 bias (exact for small integers)
-              const int ri = __float_as_int(rr + 12582912.0f) - 0x4B400000;
-              packed |= ((uint32_t)(ri & 0xFF)) << (8 * bidx);
+              for (int bidx = 0; bidx < 4; ++bidx)
+                u[bidx] = __float_as_uint(fmod_centred(acc[g * 16 + v * 4 + bidx], pf, pinv) + 12582912.0f);
+              w[v] = __byte_perm(__byte_perm(u[0], u[1], 0x0040), __byte_perm(u[2], u[3], 0x0040), 0x5410);
             }
-            w[v] = packed;
+            *reinterpret_cast<uint4*>(dst + g * 16) = make_uint4(w[0], w[1], w[2], w[3]);
           }
-          *reinterpret_cast<uint4*>(dst + g * 16) = make_uint4(w[0], w[1], w[2], w[3]);
         }
       }
     }

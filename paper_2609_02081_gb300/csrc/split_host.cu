@@ -115,10 +115,15 @@ void split_release(SplitState& s) {
 }
 
 // ----------------------------------------------------------------- layout
+// Built-in tile width: the fewest tiles of at most 256 columns, each as
+// narrow as a multiple of 32 allows (tcgen05 takes any N that is a multiple of
+// 16 with M = 128; the epilogue stores 16-column groups per half tile), so
+// that padding columns stay below 32 per tile (n = 96: one tile of 96; n = 300:
+// two of 160).
 static int pick_bn(int64_t n) {
-  if (n > 128) return 256;
-  if (n > 64) return 128;
-  return 64;
+  const int64_t tiles = (n + 255) / 256;
+  const int64_t per = (n + tiles - 1) / tiles;
+  return (int)std::min<int64_t>(256, std::max<int64_t>(32, (per + 31) / 32 * 32));
 }
 
 static int ceil_log2(int64_t x) {
@@ -145,8 +150,10 @@ static inline int64_t align256(int64_t x) { return (x + 255) & ~(int64_t)255; }
 static constexpr int64_t kPlaneSkewEnc = 3 * 256;
 static constexpr int64_t kPlaneSkewRes = 3 * 256;
 
-// encode blocks: tiles of 16 rows x 32 k over the padded operand
-static inline int64_t enc_blocks(int64_t rows_pad, int64_t nkb) { return (rows_pad / 16) * (nkb * kTileK / 32); }
+// encode blocks: tiles of 16 rows x 32 k over the operand's rows rounded up to
+// 16 (the residue GEMM copies whole 8-row groups of a tile and never reads the
+// rows beyond them) and the inner dimension padded to whole k-blocks (zeros)
+static inline int64_t enc_blocks(int64_t rows, int64_t nkb) { return ((rows + 15) / 16) * (nkb * kTileK / 32); }
 // CRT blocks: one per output row and kCrtCols consecutive columns
 static inline int64_t crt_blocks(int64_t m, int64_t n) { return m * ((n + kCrtCols - 1) / kCrtCols); }
 
@@ -244,9 +251,9 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     sj.exp_begin = sp.exp_units;
     sp.exp_units += (d.m + 31) / 32 + (d.n + 31) / 32;
     sj.encA_begin = sp.encA_units;
-    sp.encA_units += enc_blocks(sj.tiles_m * kTileM, sj.nkb);
+    sp.encA_units += enc_blocks(d.m, sj.nkb);
     sj.encB_begin = sp.encB_units;
-    sp.encB_units += enc_blocks(sj.tiles_n * sj.bn, sj.nkb);
+    sp.encB_units += enc_blocks(d.n, sj.nkb);
     sj.item_begin = sp.items;
     sp.items += (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
     sj.crt_begin = sp.crt_units;
@@ -271,8 +278,8 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
   if (st != HMAT_STATUS_SUCCESS) return st;
   units->exp = (d.m + 31) / 32 + (d.n + 31) / 32;
-  units->encA = enc_blocks(sj.tiles_m * kTileM, sj.nkb);
-  units->encB = enc_blocks(sj.tiles_n * sj.bn, sj.nkb);
+  units->encA = enc_blocks(d.m, sj.nkb);
+  units->encB = enc_blocks(d.n, sj.nkb);
   units->items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
   units->crt = crt_blocks(d.m, d.n);
   units->max_bits = sj.bits;
