@@ -44,10 +44,11 @@ def parse(argv=None):
     ap.add_argument("--e2e-budget-gb", type=float, default=100.0,
                     help="device budget of the end-to-end (host-resident operands) call")
     ap.add_argument("--seed", type=int, default=103)
-    ap.add_argument("--workload", choices=["single", "grouped", "ops", "streamed"], default="single",
+    ap.add_argument("--workload", choices=["single", "grouped", "ops", "streamed", "fp64-peak"], default="single",
                     help="single: the n-sized product; grouped: 512 products with m,n,k log-uniform in [32,1024]; "
                          "ops: the element-wise and mapping operations at n x n; streamed: the product with "
-                         "A, B, C in pinned host memory through a device budget (--budget-gb)")
+                         "A, B, C in pinned host memory through a device budget (--budget-gb); fp64-peak: the "
+                         "DFMA and DMMA probes that give the plain FP64 mode's roofline")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="streamed: device budget in GB")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--groups", type=int, default=512, help="grouped: the first G of the 512 problems")
@@ -225,6 +226,104 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
+def split_stage_work(hm, shapes, tol, opA="N", opB="N", fa=0xFF, fb=0xFF, algo="bilinear"):
+    """Algorithmic work of one split-mode step per stage, summed over (m, n, k) shapes:
+    bytes for the exponent, encode and CRT stages (what each stage must read and write:
+    the present FP64 components, the encoded factor tiles of the plan's nlf / nrf factors
+    per modulus, the int8 residue of every product and modulus, C) and BF16 flops for the
+    residue GEMM (moduli x products x 2 m n k)."""
+    P, U, V, _, _ = hm.plan_info(opA, opB, fa, fb, algo=algo)
+    nlf = len({tuple(r) for r in U.tolist()})
+    nrf = len({tuple(r) for r in V.tolist()})
+    ca, cb = bin(fa).count("1"), bin(fb).count("1")
+    w = {"split_exponents": 0.0, "split_encode": 0.0, "split_crt": 0.0, "split_residue_gemm": 0.0}
+    for m, n, k in shapes:
+        L = len(hm.split_info(k, tol)[0])
+        kp = -(-k // 64) * 64
+        raw = 8.0 * (ca * m * k + cb * k * n)
+        w["split_exponents"] += raw
+        w["split_encode"] += raw + 2.0 * L * (nlf * m + nrf * n) * kp
+        w["split_crt"] += L * P * m * n + 64.0 * m * n
+        w["split_residue_gemm"] += 2.0 * L * P * m * n * k
+    return w
+
+
+def stage_rates(stages, work, steps=1):
+    """GB/s (HBM stages) and TFLOP/s (residue GEMM) of each timed stage from its summed event time."""
+    for name, st in stages.items():
+        ms = st.get("ms_total", st.get("ms"))
+        if name not in work or not ms:
+            continue
+        if name == "split_residue_gemm":
+            st["TFLOP_per_s"] = work[name] * steps / (ms * 1e-3) / 1e12
+        else:
+            st["GB_per_s"] = work[name] * steps / (ms * 1e-3) / 1e9
+            st["algorithmic_bytes_per_step"] = work[name]
+    return stages
+
+
+def fp64_peaks(hm, iterations=1 << 16):
+    """Measured FP64 throughput of this GPU (best of 3 launches per probe), TFLOP/s:
+    {"dfma": ..., "dmma_m8n8k4": ..., "dmma_m16n8k4": ...}."""
+    out = {}
+    for kind in hm.FP64_PEAK_KINDS:
+        hm.measure_fp64_peak(kind, 1 << 10)                      # warm-up
+        out[kind] = max(hm.measure_fp64_peak(kind, iterations)[0] for _ in range(3))
+    return out
+
+
+def fp64_roofline(achieved, peaks, kernel="fp64_bilinear_kernel", **extra):
+    """Roofline of an FP64-mode launch against the measured DFMA peak (the kernel's pipe),
+    with its fraction of the best FP64 tensor-core (DMMA) probe beside it."""
+    dmma = max(peaks["dmma_m8n8k4"], peaks["dmma_m16n8k4"])
+    r = {"bound": "alu", "achieved": achieved, "peak": peaks["dfma"], "unit": "TFLOP/s",
+         "frac": achieved / peaks["dfma"], "traffic": None, "kernel": kernel,
+         "peak_source": "hmat_measure_fp64_peak DFMA probe, measured in this run (of measured)",
+         "frac_of_dmma": achieved / dmma, "peaks_measured": peaks}
+    r.update(extra)
+    return r
+
+
+def freivalds_host(A_cpu, B_cpu, C_cpu, opA, seed):
+    """Whole-matrix check of C = op(A) B: ||C x - op(A) (B x)|| / (||C||_F ||x||) for a
+    random biquaternion vector x, both sides by the CPU oracle (Freivalds 1977)."""
+    import numpy as np
+    import bq_inputs as bi
+    import oracle
+    x = bi.uniform(seed, C_cpu.shape[2], 1).numpy()
+    y1 = oracle.bq_gemm(C_cpu, x)
+    y2 = oracle.bq_gemm(A_cpu, oracle.bq_gemm(B_cpu, x), opA, "N")
+    return float(np.linalg.norm(y1 - y2) / (np.linalg.norm(C_cpu) * np.linalg.norm(x)))
+
+
+def fp64_peak_arm(args, rank, world, local):
+    """The FP64 probes alone: DFMA and the two DMMA shapes, each timed with CUDA events."""
+    import torch
+    import paper_2609_02081_gb300 as hm
+    dev = torch.device("cuda", local if torch.cuda.device_count() > local else 0)
+    torch.cuda.set_device(dev)
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    runs = {}
+    for kind in hm.FP64_PEAK_KINDS:
+        for _ in range(args.warmup):
+            hm.measure_fp64_peak(kind, 1 << 12)
+        vals = [hm.measure_fp64_peak(kind, 1 << 17) for _ in range(args.steps)]
+        runs[kind] = {"tflops_best": max(v[0] for v in vals), "tflops_median": statistics.median(v[0] for v in vals),
+                      "ms_median": statistics.median(v[1] for v in vals)}
+    clk = clocks.stop()
+    if rank == 0:
+        best = runs["dfma"]["tflops_best"]
+        line = {"metric": "FP64 throughput TFLOP/s (DFMA probe; DMMA probes beside it)", "value": best,
+                "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": runs["dfma"]["ms_median"], "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "FP64 probe kernels: 8 blocks per SM, 8 independent chains per thread "
+                                       "(DFMA) or per warp (mma.sync m8n8k4 / m16n8k4), 2^17 loop trips"},
+                "probes": runs, "clocks": clk, "gpu_launches": args.steps * len(runs)}
+        emit(args, line)
+
+
 # ----------------------------------------------------------------------------- oracle sample
 def oracle_rows(A_cpu, B_cpu, rows, opA="N"):
     """Selected output rows of op(A) B from the CPU oracle; returns (rows x, seconds, threads)."""
@@ -358,10 +457,18 @@ def ours(args, rank, world, local):
             torch.cuda.synchronize()
             fms = e0.elapsed_time(e1)
             got64 = C[:, torch.as_tensor(rows, device=dev), :].cpu().numpy()
+            ex64 = P * size * 2.0 * n ** 3 / (fms * 1e-3) / 1e12
             info["fp64_plain"] = {"ms": fms, "tflops_64equiv": flops64 / (fms * 1e-3) / 1e12,
-                                  "tflops_executed": P * size * 2.0 * n ** 3 / (fms * 1e-3) / 1e12,
+                                  "tflops_executed": ex64,
                                   "rel_fro_err_sampled": float(np.linalg.norm(got64 - want) / np.linalg.norm(want)),
-                                  "speedup_split_vs_fp64": fms / ms}
+                                  "speedup_split_vs_fp64": fms / ms,
+                                  "roofline": fp64_roofline(ex64, fp64_peaks(hm))}
+            step()                          # C back to the timed mode's result for the checks below
+            torch.cuda.synchronize()
+        # whole-matrix accuracy of the timed mode's C (Freivalds, oracle matrix-vector products)
+        t0 = time.perf_counter()
+        info["freivalds_ratio"] = freivalds_host(A_cpu, B_cpu, C.cpu().numpy(), args.opA, args.seed + 11)
+        info["freivalds_s"] = time.perf_counter() - t0
 
         # end to end with the operands in pinned host memory.  Serial form: copy A, B in, the product,
         # copy C out, one after another on the stream (bq_gemm_host).
@@ -431,11 +538,11 @@ def ours(args, rank, world, local):
             alg = P * size * 2.0 * n * n * n * args.steps / max(gl, 1)   # a plan over 24 products takes passes
             avg = gms / max(gl, 1)
             ach = alg / (avg * 1e-3) / 1e12
-            peak = 1.204   # measured DFMA throughput (152 SMs x 2 FP64 FMA/clk)
-            roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                    "traffic": None, "kernel": "fp64_bilinear_kernel", "peak_source": "measured DFMA probe",
-                    "algorithmic_flops_per_launch": alg, "avg_launch_ms": avg}
+            roof = fp64_roofline(ach, fp64_peaks(hm), algorithmic_flops_per_launch=alg, avg_launch_ms=avg)
         stages = {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items() if v[0] > 0}
+        if args.mode == "split" and args.algo == "bilinear":
+            stages = stage_rates(stages, split_stage_work(hm, [(n, n, n)], args.tol, args.opA, "N", fa, fb),
+                                 args.steps)
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16" if args.mode == "split" else "f64", "data": "synthetic",
@@ -444,7 +551,12 @@ def ours(args, rank, world, local):
                 "roofline": roof, "cpu_baseline": info.get("cpu_baseline"), "e2e": info.get("e2e"),
                 "gpu_launches": launches, "clocks": clk,
                 "rel_fro_err_sampled": info.get("rel_fro_err_sampled"),
-                "err_ok": (info.get("rel_fro_err_sampled") is not None and info["rel_fro_err_sampled"] <= 1e-12),
+                "freivalds_ratio": info.get("freivalds_ratio"),
+                "freivalds_note": "||C x - op(A)(B x)|| / (||C||_F ||x||) over the whole output, random "
+                                  "biquaternion x, both sides in the CPU oracle; bound tol + 1e-14",
+                "err_ok": (info.get("rel_fro_err_sampled") is not None and info["rel_fro_err_sampled"] <= 1e-12
+                           and info.get("freivalds_ratio") is not None
+                           and info["freivalds_ratio"] <= args.tol + 1e-14),
                 "fp64_plain": info.get("fp64_plain"), "stages": stages,
                 "executed_tflops": value * size * (len(mods) * P if args.mode == "split" else P) / 64.0,
                 "naive_equiv_tflops": value * naive / 64.0,
@@ -521,17 +633,26 @@ def grouped(args, rank, world, local):
         P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ)[0]
         fst = stages.get("fp64_bilinear", {"launches": 1, "ms": float("nan")})
         ach = sum(P * 2.0 * m * n * k for m, n, k in shapes) / (fst["ms"] / fst["launches"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": ach, "peak": 1.204, "unit": "TFLOP/s", "frac": ach / 1.204,
-                "traffic": None, "kernel": "fp64_bilinear_kernel", "peak_source": "measured DFMA probe"}
+        roof = fp64_roofline(ach, fp64_peaks(hm))
     if rank == 0:
         # accuracy: 16 sampled problems against the oracle
         rng = np.random.default_rng(5)
         errs = []
         small = [i for i, (m, n, k) in enumerate(shapes) if m * n * k <= (1 << 25)]
+        t_or, f_or = 0.0, 0.0
         for i in rng.choice(small, size=min(16, len(small)), replace=False):
             A, B, C = mats[i]
-            want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy())
+            An, Bn = A.cpu().numpy(), B.cpu().numpy()
+            t0 = time.perf_counter()
+            want = oracle.bq_gemm(An, Bn)
+            t_or += time.perf_counter() - t0
+            m, n, k = shapes[i]
+            f_or += 64 * 2.0 * m * n * k
             errs.append(float(np.linalg.norm(C.cpu().numpy() - want) / np.linalg.norm(want)))
+        cpu_base = {"value": f_or / t_or / 1e12, "unit": "TFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
+                    "sample": f"the 16 sampled problems of the batch (m n k <= 2^25), {t_or:.1f} s"}
+        if args.mode == "split":
+            stages = stage_rates(stages, split_stage_work(hm, shapes, args.tol))
         line = {"metric": "grouped biquaternion GEMM TFLOP/s (64-GEMM-equiv.)", "value": value, "unit": "TFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -541,7 +662,7 @@ def grouped(args, rank, world, local):
                            "tol": args.tol, "total_flops_64equiv": flops64,
                            "tile_table": args.tile_table, "workspace_bytes": ws_bytes},
                 "max_rel_fro_err_16_sampled": max(errs), "clocks": clk, "stages_one_step": stages,
-                "roofline": roof, "gpu_launches": launches_per_step * args.steps}
+                "roofline": roof, "cpu_baseline": cpu_base, "gpu_launches": launches_per_step * args.steps}
         emit(args, line)
     barrier(world)
     h.close()
@@ -725,6 +846,8 @@ def main():
             streamed_arm(args, rank, world, local)
         elif args.workload == "grouped" and args.impl == "ours":
             grouped(args, rank, world, local)
+        elif args.workload == "fp64-peak" and args.impl == "ours":
+            fp64_peak_arm(args, rank, world, local)
         elif args.impl == "reference":
             reference_arm(args, rank, world)
         else:
