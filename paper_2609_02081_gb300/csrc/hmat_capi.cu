@@ -759,7 +759,7 @@ hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const 
     if (!build_plan(fa, fb, &p, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
       return HMAT_STATUS_INTERNAL;
     if (p.np == 0) continue;
-    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf});
+    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf, p.bilinear_full});
   }
   size_t split = 0;
   if (!shapes.empty()) {
@@ -853,7 +853,7 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 1, u.encB, stream, a.scratch, u.max_bits);
   if (e == cudaSuccess)
     e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch);
-  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod);
+  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod, u.all_full);
   return cuda_status(e);
 }
 

@@ -62,6 +62,7 @@ hmat_status split_params(int64_t k, double tol, SplitParams* out);
 struct SplitShape {
   int64_t m, n, k;
   int np, nlf, nrf;
+  int full = 0;                     // the plan is the paper's full 24-product plan (KPlan::bilinear_full)
 };
 
 // Per-problem layout inside the caller's workspace.
@@ -70,6 +71,7 @@ struct SplitJob {
   int32_t nmod, bits, bn;           // moduli, integer width, tile N
   int32_t tiles_m, tiles_n, nkb;    // 128-row tiles, bn-column tiles, 64-wide k blocks
   int32_t np, nlf, nrf;
+  int32_t full;                     // the plan is the paper's full 24-product plan (KPlan::bilinear_full)
   int8_t pl[kMaxProducts], pr[kMaxProducts];
   int64_t off_sexp, off_texp;       // int32 exponents (bytes into workspace)
   int64_t off_encA, off_encB;       // BF16 factor tiles
@@ -121,6 +123,7 @@ struct SplitPrep {
   int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
   int64_t ws_needed = 0;
   int max_bits = 0, max_nmod = 0;
+  bool all_full = true;             // every job uses the paper's full plan
   // one job whose A-side exponents and encoded factor tiles are already in the
   // workspace from the previous call with the same A block and the same shape
   bool reuse_a = false;
@@ -145,6 +148,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
 struct SplitUnits {
   int64_t exp = 0, encA = 0, encB = 0, items = 0, crt = 0, ws_bytes = 0;
   int max_bits = 0, max_nmod = 0;
+  bool all_full = false;
 };
 hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
                                 SplitUnits* units);
@@ -183,8 +187,9 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
                                 cudaStream_t s, unsigned char* ws, int max_bits);
 cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
                               unsigned char* ws);
+// all_full: every job uses the paper's full plan, served by the unrolled kernel
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod);
+                             cudaStream_t s, unsigned char* ws, int max_nmod, bool all_full);
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint32_t* crt_c, const uint32_t* crt_P);
 
 }  // namespace hmat

@@ -179,6 +179,7 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
   sj->np = sh.np;
   sj->nlf = sh.nlf;
   sj->nrf = sh.nrf;
+  sj->full = (plan ? plan->bilinear_full != 0 : sh.full != 0) ? 1 : 0;
   if (plan) {
     for (int p = 0; p < kMaxProducts; ++p) {
       sj->pl[p] = plan->pl[p];
@@ -245,7 +246,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     SplitJob sj;
     std::memset(&sj, 0, sizeof(sj));
     sj.d = d;
-    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf};
+    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full};
     hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
     if (st != HMAT_STATUS_SUCCESS) return st;
     sj.exp_begin = sp.exp_units;
@@ -260,6 +261,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     sp.crt_units += crt_blocks(d.m, d.n);
     sp.max_bits = std::max(sp.max_bits, sj.bits);
     sp.max_nmod = std::max(sp.max_nmod, sj.nmod);
+    sp.all_full = sp.all_full && sj.full;
     sp.jobs.push_back(sj);
   }
   if ((size_t)off > ws_bytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
@@ -273,7 +275,7 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   SplitJob sj;
   std::memset(&sj, 0, sizeof(sj));
   sj.d = d;
-  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf};
+  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full};
   int64_t off = 0;
   hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
   if (st != HMAT_STATUS_SUCCESS) return st;
@@ -284,6 +286,7 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   units->crt = crt_blocks(d.m, d.n);
   units->max_bits = sj.bits;
   units->max_nmod = sj.nmod;
+  units->all_full = sj.full != 0;
   units->ws_bytes = off;
   *out = sj;
   return HMAT_STATUS_SUCCESS;
@@ -319,7 +322,7 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
   if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 4, stream);
-    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod);
+    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod, sp.all_full);
   }
   return e == cudaSuccess ? HMAT_STATUS_SUCCESS : split_cuda_error(e);
 }

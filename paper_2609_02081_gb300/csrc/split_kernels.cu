@@ -498,146 +498,15 @@ __device__ __forceinline__ uint32_t residue_q4(int q4, const ModConst& mc) {
   return x - __umulhi(x, mc.magic) * (uint32_t)mc.p;
 }
 
+// The output stage shared by the CRT kernels: S_e = sum_l r_{l,e} c_l in the
+// 64-bit limb accumulators acc[e] becomes the centred integer X_e = S_e - q P,
+// then the double X_e 2^-(s_i + t_j), then C (plain store, or the complex
+// alpha / beta update for which the two halves trade their four components
+// through xch).  Every thread of the block calls it (it may synchronise).
 template <int L>
-__global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
-    split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs, const KPlan* __restrict__ plans,
-                     unsigned char* __restrict__ ws) {
-  // four ring slots, prefetch distance two: the slot refilled at modulus l
-  // was read at l - 2, which every thread has finished once it passes the
-  // barrier of l - 1, so one barrier per modulus suffices
-  constexpr int kStages = 4;
-  constexpr int kChunksPerRow = kCrtCols / 16;    // 16-byte cp.async chunks per residue row
-  __shared__ uint32_t wpk[8][kMaxProducts / 4];
-  __shared__ __align__(16) uint8_t ring[kStages][kMaxProducts][kCrtCols];
-  __shared__ double xch[8][kCrtCols];            // the four components of each half, for alpha / beta
-  const int64_t blk = blockIdx.x;
-  const int g = find_split_job(jobs, njobs, blk, 4);
-  const SplitJob& sj = jobs[g];
-  const JobDesc& d = sj.d;
-  const KPlan& P = plans[d.plan];
-  const int np = sj.np, nw = (np + 3) / 4, nm = sj.nmod;
-  const int tid = threadIdx.x;
-  const int col = tid % kCrtCols, half = tid / kCrtCols;   // half 0: M1..M4, half 1: M5..M8
-  if (tid < 8 * (kMaxProducts / 4)) {
-    const int e = tid / (kMaxProducts / 4), w = tid % (kMaxProducts / 4);
-    uint32_t word = 0;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int p = 4 * w + b;
-      const int v = p < np ? (int)P.w4[e][p] : 0;
-      word |= ((uint32_t)(v & 0xFF)) << (8 * b);
-    }
-    wpk[e][w] = word;
-  }
-  // this block: row i, columns jb*kCrtCols .. jb*kCrtCols + kCrtCols - 1 of the output
-  const int64_t local = blk - sj.crt_begin;
-  const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
-  const int i = (int)(local / colblocks);
-  const int jb = (int)(local % colblocks);
-  const int j = jb * kCrtCols + col;
-  const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
-  const int64_t plane = sj.res_plane;
-  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
-  const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
-  const int cmax = cavail < kChunksPerRow ? (int)cavail : kChunksPerRow;
-
-  // prefetch modulus l's np residue rows (kCrtCols bytes each) into ring slot
-  // l % 4: thread tid copies chunk tid (all of them for np <= 32), further
-  // chunks (larger plans) are computed per modulus
-  const int p0 = tid / kChunksPerRow, c0 = tid % kChunksPerRow;
-  const bool has0 = tid < np * kChunksPerRow && c0 < cmax;
-  const int64_t src0 = (int64_t)p0 * plane + c0 * 16;
-  const int dst0 = p0 * kCrtCols + c0 * 16;
-  auto issue = [&](int l) {
-    if (l < nm) {
-      uint8_t* slot = &ring[l % kStages][0][0];
-      const unsigned char* src = rowbase + (int64_t)l * np * plane;
-      if (has0) cp_async16(slot + dst0, src + src0);
-      for (int idx = tid + 2 * kCrtCols; idx < np * kChunksPerRow; idx += 2 * kCrtCols) {
-        const int p = idx / kChunksPerRow, c = idx % kChunksPerRow;
-        if (c < cmax) cp_async16(slot + p * kCrtCols + c * 16, src + (int64_t)p * plane + c * 16);
-      }
-    }
-    cp_async_commit();
-  };
-  issue(0);
-  issue(1);
-
-  unsigned long long acc[4][L];
-#pragma unroll
-  for (int e = 0; e < 4; ++e)
-#pragma unroll
-    for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
-
-  const bool structured = P.bilinear_full != 0;
-  // outputs of this half with a nonzero weight (a subalgebra plan leaves some
-  // components identically zero: they skip the sums and convert to +0)
-  uint32_t emask = 0xFu;          // the full plan weights every output
-  if (!structured) {
-    __syncthreads();               // wpk filled
-    emask = 0;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      uint32_t any = 0;
-      for (int w = 0; w < nw; ++w) any |= wpk[4 * half + e][w];
-      emask |= (any != 0u ? 1u : 0u) << e;
-    }
-  }
-  for (int l = 0; l < nm; ++l) {
-    issue(l + 2);
-    cp_async_wait2();            // modulus l has landed
-    __syncthreads();
-    const ModConst& mc = c_mod[l];
-    uint32_t cl[L];
-#pragma unroll
-    for (int q = 0; q < L; ++q) cl[q] = c_crt[nm][l][q];
-    const uint8_t(*slot)[kCrtCols] = ring[l % kStages];
-    uint32_t ru[4];
-    if (structured) {
-      // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
-      // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
-      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); real parts
-      // in half 0, imaginary parts in half 1, in 32-bit integers
-      // (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
-      int v[8];
-      if (half == 0) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
-      } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
-      }
-      const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
-      ru[0] = residue_q4(8 * v[0] - (a + c), mc);
-      ru[1] = residue_q4(-8 * v[1] + (a - c), mc);
-      ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
-      ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
-    } else {
-      // np residues packed four to a word, dotted with the packed weights of
-      // this half's outputs; only the plan's words, only outputs with weights
-      int o[4] = {0, 0, 0, 0};
-#pragma unroll 2
-      for (int w = 0; emask != 0u && w < nw; ++w) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (4 * w + b < np) word |= (uint32_t)slot[4 * w + b][col] << (8 * b);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) ru[e] = residue_q4(o[e], mc);   // |o| <= kMaxWeightSum * 127
-    }
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      if ((emask >> e) & 1u) {
-#pragma unroll
-        for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
-      }
-  }
-
+__device__ __forceinline__ void crt_output(const unsigned long long (&acc)[4][L], uint32_t emask, const SplitJob& sj,
+                                           const JobDesc& d, const unsigned char* ws, int nm, int i, int j, int half,
+                                           int col, double (*xch)[kCrtCols]) {
   const bool valid = j < d.n;
   double q4v[4] = {0.0, 0.0, 0.0, 0.0};
   if (valid) {
@@ -725,6 +594,240 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
   }
 }
 
+template <int L>
+__global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
+    split_crt_kernel(const SplitJob* __restrict__ jobs, int njobs, const KPlan* __restrict__ plans,
+                     unsigned char* __restrict__ ws) {
+  // four ring slots, prefetch distance two: the slot refilled at modulus l
+  // was read at l - 2, which every thread has finished once it passes the
+  // barrier of l - 1, so one barrier per modulus suffices
+  constexpr int kStages = 4;
+  constexpr int kChunksPerRow = kCrtCols / 16;    // 16-byte cp.async chunks per residue row
+  __shared__ uint32_t wpk[8][kMaxProducts / 4];
+  __shared__ __align__(16) uint8_t ring[kStages][kMaxProducts][kCrtCols];
+  __shared__ double xch[8][kCrtCols];            // the four components of each half, for alpha / beta
+  const int64_t blk = blockIdx.x;
+  const int g = find_split_job(jobs, njobs, blk, 4);
+  const SplitJob& sj = jobs[g];
+  const JobDesc& d = sj.d;
+  const KPlan& P = plans[d.plan];
+  const int np = sj.np, nw = (np + 3) / 4, nm = sj.nmod;
+  const int tid = threadIdx.x;
+  const int col = tid % kCrtCols, half = tid / kCrtCols;   // half 0: M1..M4, half 1: M5..M8
+  if (tid < 8 * (kMaxProducts / 4)) {
+    const int e = tid / (kMaxProducts / 4), w = tid % (kMaxProducts / 4);
+    uint32_t word = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int p = 4 * w + b;
+      const int v = p < np ? (int)P.w4[e][p] : 0;
+      word |= ((uint32_t)(v & 0xFF)) << (8 * b);
+    }
+    wpk[e][w] = word;
+  }
+  // this block: row i, columns jb*kCrtCols .. jb*kCrtCols + kCrtCols - 1 of the output
+  const int64_t local = blk - sj.crt_begin;
+  const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
+  const int i = (int)(local / colblocks);
+  const int jb = (int)(local % colblocks);
+  const int j = jb * kCrtCols + col;
+  const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
+  const int64_t plane = sj.res_plane;
+  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
+  const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
+  const int cmax = cavail < kChunksPerRow ? (int)cavail : kChunksPerRow;
+
+  // prefetch modulus l's np residue rows (kCrtCols bytes each) into ring
+  // slot l % 4: thread tid copies chunk tid (all of them for np <= 32),
+  // further chunks (larger plans) are computed per modulus
+  const int p0 = tid / kChunksPerRow, c0 = tid % kChunksPerRow;
+  const bool has0 = tid < np * kChunksPerRow && c0 < cmax;
+  const int64_t src0 = (int64_t)p0 * plane + c0 * 16;
+  const int dst0 = p0 * kCrtCols + c0 * 16;
+  auto issue = [&](int l) {
+    if (l < nm) {
+      uint8_t* slot = &ring[l % kStages][0][0];
+      const unsigned char* src = rowbase + (int64_t)l * np * plane;
+      if (has0) cp_async16(slot + dst0, src + src0);
+      for (int idx = tid + 2 * kCrtCols; idx < np * kChunksPerRow; idx += 2 * kCrtCols) {
+        const int p = idx / kChunksPerRow, c = idx % kChunksPerRow;
+        if (c < cmax) cp_async16(slot + p * kCrtCols + c * 16, src + (int64_t)p * plane + c * 16);
+      }
+    }
+    cp_async_commit();
+  };
+  issue(0);
+  issue(1);
+
+  unsigned long long acc[4][L];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
+
+  const bool structured = sj.full != 0;     // the paper's full plan
+  // outputs of this half with a nonzero weight (a subalgebra plan leaves some
+  // components identically zero: they skip the sums and convert to +0)
+  uint32_t emask = 0xFu;          // the full plan weights every output
+  if (!structured) {
+    __syncthreads();               // wpk filled
+    emask = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      uint32_t any = 0;
+      for (int w = 0; w < nw; ++w) any |= wpk[4 * half + e][w];
+      emask |= (any != 0u ? 1u : 0u) << e;
+    }
+  }
+  for (int l = 0; l < nm; ++l) {
+    issue(l + 2);
+    cp_async_wait2();            // modulus l has landed
+    __syncthreads();
+    const ModConst& mc = c_mod[l];
+    uint32_t cl[L];
+#pragma unroll
+    for (int q = 0; q < L; ++q) cl[q] = c_crt[nm][l][q];
+    const uint8_t(*slot)[kCrtCols] = ring[l % kStages];
+    uint32_t ru[4];
+    if (structured) {
+      // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
+      // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
+      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); real parts
+      // in half 0, imaginary parts in half 1, in 32-bit integers
+      // (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
+      int v[8];
+      if (half == 0) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+      } else {
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+      }
+      const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
+      ru[0] = residue_q4(8 * v[0] - (a + c), mc);
+      ru[1] = residue_q4(-8 * v[1] + (a - c), mc);
+      ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
+      ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
+    } else {
+      // np residues packed four to a word, dotted with the packed weights of
+      // this half's outputs; only the plan's words, only outputs with weights
+      int o[4] = {0, 0, 0, 0};
+#pragma unroll 2
+      for (int w = 0; emask != 0u && w < nw; ++w) {
+        uint32_t word = 0;
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+          if (4 * w + b < np) word |= (uint32_t)slot[4 * w + b][col] << (8 * b);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) ru[e] = residue_q4(o[e], mc);   // |o| <= kMaxWeightSum * 127
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((emask >> e) & 1u) {
+#pragma unroll
+        for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
+      }
+  }
+
+  crt_output<L>(acc, emask, sj, d, ws, nm, i, j, half, col, xch);
+}
+
+// CRT of the paper's full plan, for launches whose jobs all use it: the 24
+// product planes per modulus in a 12 KB ring, the modulus loop unrolled for
+// the usual modulus counts (13 and 14: k up to 8192 at tol 1e-12) so that the
+// CRT basis words and the modulus constants are compile-time addresses, and
+// 64 registers a thread for four resident blocks per SM.
+constexpr int kFullPlanes = 24;
+
+template <int L, int NM>
+__device__ __forceinline__ void crt_full_accumulate(unsigned long long (&acc)[4][L], const unsigned char* rowbase,
+                                                    int64_t plane, int cmax, int nm_dyn, int tid, int col, int half,
+                                                    uint8_t (*ring)[kFullPlanes][kCrtCols]) {
+  const int nm = NM > 0 ? NM : nm_dyn;
+  // thread tid < 192 prefetches 16-byte chunk tid % 8 of plane tid / 8
+  const int pc = tid >> 3, cc = tid & 7;
+  const bool has = tid < kFullPlanes * (kCrtCols / 16) && cc < cmax;
+  const int64_t src0 = (int64_t)pc * plane + cc * 16;
+  const int dst0 = pc * kCrtCols + cc * 16;
+  auto issue = [&](int l) {
+    if (l < nm && has) cp_async16(&ring[l & 3][0][0] + dst0, rowbase + (int64_t)l * kFullPlanes * plane + src0);
+    cp_async_commit();
+  };
+  auto step = [&](int l) {
+    issue(l + 2);
+    cp_async_wait2();            // modulus l has landed
+    __syncthreads();
+    const ModConst& mc = c_mod[l];
+    const uint8_t(*slot)[kCrtCols] = ring[l & 3];
+    // P_r = (T1 - T2) + i (T3 - T1 - T2); 4 Q_e = +-8 P_e +- P5 +- P6 +- P7 +- P8
+    int v[8];
+    if (half == 0) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+    } else {
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+    }
+    const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
+    uint32_t ru[4];
+    ru[0] = residue_q4(8 * v[0] - (a + c), mc);
+    ru[1] = residue_q4(-8 * v[1] + (a - c), mc);
+    ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
+    ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * c_crt[nm][l][q];
+  };
+  issue(0);
+  issue(1);
+  if constexpr (NM > 0) {
+#pragma unroll
+    for (int l = 0; l < NM; ++l) step(l);
+  } else {
+#pragma unroll 1
+    for (int l = 0; l < nm; ++l) step(l);
+  }
+}
+
+template <int L>
+__global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                                         unsigned char* __restrict__ ws) {
+  __shared__ __align__(16) uint8_t ring[4][kFullPlanes][kCrtCols];
+  __shared__ double xch[8][kCrtCols];
+  const int64_t blk = blockIdx.x;
+  const SplitJob& sj = jobs[find_split_job(jobs, njobs, blk, 4)];
+  const JobDesc& d = sj.d;
+  const int nm = sj.nmod;
+  const int tid = threadIdx.x;
+  const int col = tid % kCrtCols, half = tid / kCrtCols;
+  const int64_t local = blk - sj.crt_begin;
+  const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
+  const int i = (int)(local / colblocks);
+  const int jb = (int)(local % colblocks);
+  const int j = jb * kCrtCols + col;
+  const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
+  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
+  const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
+  const int cmax = cavail < kCrtCols / 16 ? (int)cavail : kCrtCols / 16;
+  unsigned long long acc[4][L];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
+  const int64_t pl = sj.res_plane;
+  if (L == 4 && nm == 13) crt_full_accumulate<L, 13>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
+  else if (L == 4 && nm == 14) crt_full_accumulate<L, 14>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
+  else crt_full_accumulate<L, 0>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
+  crt_output<L>(acc, 0xFu, sj, d, ws, nm, i, j, half, col, xch);
+}
+
 // ------------------------------------------------------------------ launchers
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint32_t* crt_c, const uint32_t* crt_P) {
   ModConst mc[kModTable];
@@ -790,11 +893,17 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
 }
 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod) {
+                             cudaStream_t s, unsigned char* ws, int max_nmod, bool all_full) {
   if (units <= 0) return cudaSuccess;
   // 4 limbs hold sum_l r_l c_l < nmod * 255 * P below 2^128 (nmod <= 14)
-  if (max_nmod <= 14) split_crt_kernel<4><<<(unsigned)units, 2 * kCrtCols, 0, s>>>(d_jobs, njobs, d_plans, ws);
-  else split_crt_kernel<kLimbs><<<(unsigned)units, 2 * kCrtCols, 0, s>>>(d_jobs, njobs, d_plans, ws);
+  const unsigned grid = (unsigned)units, block = 2 * kCrtCols;
+  if (all_full) {
+    if (max_nmod <= 14) split_crt_full_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    else split_crt_full_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+  } else {
+    if (max_nmod <= 14) split_crt_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
+    else split_crt_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
+  }
   return cudaGetLastError();
 }
 
