@@ -245,6 +245,33 @@ def test_grouped_mixed_shapes(handle, mode, use_graph):
             np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy(), oa, ob))
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_grouped_full_plans_of_different_widths(handle, use_graph):
+    """Several full-biquaternion products of different output widths (tile
+    widths 32 to 256) in one grouped split-mode call: the residue GEMM's work
+    items of different products interleave on every SM, so per-item state must
+    not depend on a neighbouring item's shape.  Bit-exact on small integers."""
+    dev = torch.device("cuda")
+    shapes = [(100, 20, 90), (30, 250, 200), (200, 70, 64), (64, 160, 300), (140, 33, 17), (90, 300, 130),
+              (257, 224, 40), (12, 96, 1000)]
+    probs, descs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A = bi.small_int(140 + i, m, k)
+        B = bi.small_int(150 + i, k, n)
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        dA, dB = A.to(dev), B.to(dev)          # kept alive: the descriptors hold their addresses
+        probs.append((A, B, C, dA, dB))
+        descs.append(hm.make_desc(dA, dB, C))
+    for _ in range(2):
+        for p in probs:
+            p[2].fill_(float("nan"))
+        hm.hmat_bq_gemm_grouped(handle, descs, mode="split", tol=TOL, use_graph=use_graph,
+                                stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for A, B, C, _, _ in probs:
+            np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+
+
 def test_argument_errors(handle):
     dev = torch.device("cuda")
     A = torch.zeros((8, 4, 4), dtype=torch.float64, device=dev)
