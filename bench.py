@@ -29,13 +29,24 @@ sys.path.insert(0, ROOT)
 METRIC = "biquaternion GEMM TFLOP/s (64-GEMM-equiv.) vs plain FP64 at n=8192, err≤1e-12"
 
 
+FLAG_PAIRS = {"BQxBQ": (0xFF, 0xFF), "TRSxTRA": (0x0F, 0xF0), "TRSxTRS": (0x0F, 0x0F), "CxBQ": (0x11, 0xFF),
+              "RxBQ": (0x01, 0xFF), "TRSxBQ": (0x0F, 0xFF), "BQxTRA": (0xFF, 0xF0), "CxC": (0x11, 0x11)}
+FLAG_WORDS = {"BQxBQ": "full biquaternions x full biquaternions",
+              "TRSxTRA": "real quaternions (TRS) x i*real quaternions (TRA)",
+              "TRSxTRS": "real quaternions x real quaternions", "CxBQ": "complex x full biquaternions",
+              "RxBQ": "real x full biquaternions", "TRSxBQ": "real quaternions x full biquaternions",
+              "BQxTRA": "full biquaternions x i*real quaternions", "CxC": "complex x complex"}
+
+
 def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=8192)
+    ap.add_argument("--n", type=int, default=8192, help="output columns (and m, k unless given)")
+    ap.add_argument("--m", type=int, default=None, help="output rows (default: n)")
+    ap.add_argument("--k", type=int, default=None, help="inner dimension (default: n)")
     ap.add_argument("--mode", choices=["split", "fp64"], default="split")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--sample-rows", type=int, default=8)
@@ -56,7 +67,7 @@ def parse(argv=None):
     ap.add_argument("--results", default=None,
                     help="JSON-lines file: append each result with its configuration key; a configuration already "
                          "in the file is not run again (its stored line is printed)")
-    ap.add_argument("--flags", choices=["BQxBQ", "TRSxTRA", "TRSxTRS", "CxBQ"], default="BQxBQ",
+    ap.add_argument("--flags", choices=sorted(FLAG_PAIRS), default="BQxBQ",
                     help="subalgebra flags of A x B (single workload)")
     ap.add_argument("--opA", choices=["N", "T", "C", "H", "QC"], default="N", help="op(A) (single workload)")
     ap.add_argument("--no-row-scale", action="store_true",
@@ -67,10 +78,15 @@ def parse(argv=None):
     return ap.parse_args(argv)
 
 
-FLAG_PAIRS = {"BQxBQ": (0xFF, 0xFF), "TRSxTRA": (0x0F, 0xF0), "TRSxTRS": (0x0F, 0x0F), "CxBQ": (0x11, 0xFF)}
-FLAG_WORDS = {"BQxBQ": "full biquaternions x full biquaternions",
-              "TRSxTRA": "real quaternions (TRS) x i*real quaternions (TRA)",
-              "TRSxTRS": "real quaternions x real quaternions", "CxBQ": "complex x full biquaternions"}
+def dims(args):
+    """(m, n, k) of the single workload."""
+    n = args.n
+    return (getattr(args, "m", None) or n), n, (getattr(args, "k", None) or n)
+
+
+def stored_shape(op, rows, cols):
+    """Stored (rows, cols) of an operand whose op(X) is rows x cols."""
+    return (cols, rows) if op in ("T", "H") else (rows, cols)
 
 
 def workload_config(args):
@@ -78,9 +94,11 @@ def workload_config(args):
     opA = getattr(args, "opA", "N")
     scaled = not getattr(args, "no_row_scale", False)
     scale_txt = " with per-row scales 10^U(-6,0)" if scaled else ""
-    return {"workload": f"bq_gemm m=n=k={args.n} Fock-like N(0,1)*exp(-|i-j|/200){scale_txt}, "
+    m, n, k = dims(args)
+    size = f"m=n=k={n}" if m == n == k else f"m={m} n={n} k={k}"
+    return {"workload": f"bq_gemm {size} Fock-like N(0,1)*exp(-|i-j|/200){scale_txt}, "
                         f"{FLAG_WORDS[flags]}, op {opA},N, C=op(A)B",
-            "m": args.n, "n": args.n, "k": args.n, "mode": args.mode, "tol": args.tol,
+            "m": m, "n": n, "k": k, "mode": args.mode, "tol": args.tol,
             "flags": flags, "opA": opA, "row_scale": scaled, "seed": args.seed,
             "algo": getattr(args, "algo", "bilinear"),
             "l2": "inputs larger than L2 (8 x n^2 x 8 B per operand), no flush"}
@@ -346,24 +364,24 @@ def reference_arm(args, rank, world):
     import torch
     import bq_inputs as bi
     import oracle
-    n = args.n
+    m, n, k = dims(args)
     fa, fb = FLAG_PAIRS[args.flags]
     scaled = not args.no_row_scale
-    A = bi.fock_like(args.seed, n, n, flags=fa, row_scale=scaled).numpy()
-    B = bi.fock_like(args.seed + 1, n, n, flags=fb, row_scale=scaled).numpy()
+    A = bi.fock_like(args.seed, *stored_shape(args.opA, m, k), flags=fa, row_scale=scaled).numpy()
+    B = bi.fock_like(args.seed + 1, k, n, flags=fb, row_scale=scaled).numpy()
     threads = oracle.max_threads()
     rows_per_step = max(1, min(threads, 16))
     times = []
     rng = np.random.default_rng(args.seed)
     for step in range(args.warmup + args.steps):
-        rows = np.sort(rng.choice(n, size=rows_per_step, replace=False))
+        rows = np.sort(rng.choice(m, size=rows_per_step, replace=False))
         _, dt, _ = oracle_rows(A, B, rows, args.opA)
         if step >= args.warmup:
             times.append(dt)
     t = statistics.mean(times)
-    flops64 = 64 * 2.0 * rows_per_step * n * n
+    flops64 = 64 * 2.0 * rows_per_step * n * k
     value = flops64 / t / 1e12
-    sample = f"{rows_per_step} of {n} output rows per step (all 8 components), oracle on {threads} threads"
+    sample = f"{rows_per_step} of {m} output rows per step (all 8 components), oracle on {threads} threads"
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "impl": "reference", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -383,12 +401,12 @@ def ours(args, rank, world, local):
 
     dev = torch.device("cuda", local if torch.cuda.device_count() > local else 0)
     torch.cuda.set_device(dev)
-    n = args.n
+    m, n, k = dims(args)
     fa, fb = FLAG_PAIRS[args.flags]
     scaled = not args.no_row_scale
-    A = bi.fock_like(args.seed, n, n, flags=fa, row_scale=scaled, device=dev)
-    B = bi.fock_like(args.seed + 1, n, n, flags=fb, row_scale=scaled, device=dev)
-    C = torch.empty((8, n, n), dtype=torch.float64, device=dev)
+    A = bi.fock_like(args.seed, *stored_shape(args.opA, m, k), flags=fa, row_scale=scaled, device=dev)
+    B = bi.fock_like(args.seed + 1, k, n, flags=fb, row_scale=scaled, device=dev)
+    C = torch.empty((8, m, n), dtype=torch.float64, device=dev)
     h = hm.Handle()
     h.set_algorithm(args.algo)
     d = hm.make_desc(A, B, C, args.opA, "N", fa, fb)
@@ -421,7 +439,7 @@ def ours(args, rank, world, local):
     kernels = {k: h.profile(k) for k in hm.KERNEL_IDS}
     h.set_profiling(False)
     launches = sum(v[0] for v in kernels.values())
-    flops64 = 64 * 2.0 * n * n * n
+    flops64 = 64 * 2.0 * m * n * k
     value = world * flops64 / (ms * 1e-3) / 1e12
 
     # accuracy on sampled rows (rank 0)
@@ -430,23 +448,23 @@ def ours(args, rank, world, local):
     # the real products one step executes: plan products x their size relative to n^3
     if args.algo == "isomorph":
         P = hm.plan_info("N", "N", hm.HMAT_COMPLEX, hm.HMAT_COMPLEX)[0]
-        size, kin = 8, 2 * n          # one complex product of 2n x 2n x 2n
+        size, kin = 8, 2 * k          # one complex product of 2m x 2n x 2k
     else:
         P = hm.plan_info(args.opA, "N", fa, fb, algo=args.algo)[0]
-        size, kin = 1, n
+        size, kin = 1, k
     mods, bits = hm.split_info(kin, args.tol)
     if rank == 0:
         rng = np.random.default_rng(args.seed + 7)
-        rows = np.sort(rng.choice(n, size=args.sample_rows, replace=False))
+        rows = np.sort(rng.choice(m, size=args.sample_rows, replace=False))
         A_cpu = A.cpu().numpy()
         B_cpu = B.cpu().numpy()
         want, t_or, threads = oracle_rows(A_cpu, B_cpu, rows, args.opA)
         got = C[:, torch.as_tensor(rows, device=dev), :].cpu().numpy()
         err = float(np.linalg.norm(got - want) / np.linalg.norm(want))
         info["rel_fro_err_sampled"] = err
-        cpu_value = 64 * 2.0 * len(rows) * n * n / t_or / 1e12
+        cpu_value = 64 * 2.0 * len(rows) * n * k / t_or / 1e12
         info["cpu_baseline"] = {"value": cpu_value, "unit": "TFLOP/s", "cores": threads, "kind": "oracle",
-                                "sample": f"{len(rows)} of {n} output rows (all 8 components) of the same "
+                                "sample": f"{len(rows)} of {m} output rows (all 8 components) of the same "
                                           f"product, C oracle on {threads} OpenMP threads, {t_or:.1f} s"}
         # plain FP64 mode on the same inputs (1 timed call)
         if not args.no_fp64_compare and args.mode == "split":
@@ -457,7 +475,7 @@ def ours(args, rank, world, local):
             torch.cuda.synchronize()
             fms = e0.elapsed_time(e1)
             got64 = C[:, torch.as_tensor(rows, device=dev), :].cpu().numpy()
-            ex64 = P * size * 2.0 * n ** 3 / (fms * 1e-3) / 1e12
+            ex64 = P * size * 2.0 * m * n * k / (fms * 1e-3) / 1e12
             info["fp64_plain"] = {"ms": fms, "tflops_64equiv": flops64 / (fms * 1e-3) / 1e12,
                                   "tflops_executed": ex64,
                                   "rel_fro_err_sampled": float(np.linalg.norm(got64 - want) / np.linalg.norm(want)),
@@ -474,7 +492,7 @@ def ours(args, rank, world, local):
         # copy C out, one after another on the stream (bq_gemm_host).
         Ah = A.cpu().pin_memory()
         Bh = B.cpu().pin_memory()
-        Ch = torch.empty((8, n, n), dtype=torch.float64).pin_memory()
+        Ch = torch.empty((8, m, n), dtype=torch.float64).pin_memory()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
         A.copy_(Ah, non_blocking=True)
@@ -494,7 +512,7 @@ def ours(args, rank, world, local):
         del ws
         torch.cuda.empty_cache()
         budget = int(args.e2e_budget_gb * (1 << 30))
-        mb, nb, kb, _ = hm.streamed_plan(n, n, n, args.opA, "N", fa, fb, args.mode, args.tol, budget, handle=h)
+        mb, nb, kb, _ = hm.streamed_plan(m, n, k, args.opA, "N", fa, fb, args.mode, args.tol, budget, handle=h)
         ws_e2e = torch.empty(budget, dtype=torch.uint8, device=dev)
 
         def e2e_step():
@@ -511,7 +529,7 @@ def ours(args, rank, world, local):
         torch.cuda.synchronize()
         ems = e0.elapsed_time(e1) / args.e2e_steps
         got_e2e = Ch.numpy()[:, rows, :]
-        h2d, d2h = hm.streamed_traffic(n, n, n, args.opA, "N", fa, fb, args.mode, args.tol, budget, handle=h)
+        h2d, d2h = hm.streamed_traffic(m, n, k, args.opA, "N", fa, fb, args.mode, args.tol, budget, handle=h)
         info["e2e"] = {"value": flops64 / (ems * 1e-3) / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "ms_per_step": ems,
                        "api": "hmat_bq_gemm_streamed (pinned host A, B, C)", "blocks": [mb, nb, kb],
@@ -523,10 +541,11 @@ def ours(args, rank, world, local):
     if rank == 0:
         peaks, src = measured_peaks()
         gl, gms = kernels["split_residue_gemm"] if args.mode == "split" else kernels["fp64_bilinear"]
-        wl_key = f"n={n} split tol={args.tol}" + ("" if args.algo == "bilinear" else f" algo={args.algo}")
+        wl_key = ((f"n={n}" if m == n == k else f"m={m} n={n} k={k}") + f" split tol={args.tol}" +
+                  ("" if args.algo == "bilinear" else f" algo={args.algo}"))
         if args.mode == "split":
             # BF16 tensor flops of the GEMM launches of one step, per launch
-            alg = len(mods) * P * size * 2.0 * n * n * n * args.steps / max(gl, 1)
+            alg = len(mods) * P * size * 2.0 * m * n * k * args.steps / max(gl, 1)
             avg = gms / max(gl, 1)
             ach = alg / (avg * 1e-3) / 1e12
             peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
@@ -535,13 +554,13 @@ def ours(args, rank, world, local):
                     "kernel": "split_residue_gemm_kernel", "peak_source": f"bf16 sustained ({src})",
                     "algorithmic_flops_per_launch": alg, "avg_launch_ms": avg}
         else:
-            alg = P * size * 2.0 * n * n * n * args.steps / max(gl, 1)   # a plan over 24 products takes passes
+            alg = P * size * 2.0 * m * n * k * args.steps / max(gl, 1)   # a plan over 24 products takes passes
             avg = gms / max(gl, 1)
             ach = alg / (avg * 1e-3) / 1e12
             roof = fp64_roofline(ach, fp64_peaks(hm), algorithmic_flops_per_launch=alg, avg_launch_ms=avg)
         stages = {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items() if v[0] > 0}
         if args.mode == "split" and args.algo == "bilinear":
-            stages = stage_rates(stages, split_stage_work(hm, [(n, n, n)], args.tol, args.opA, "N", fa, fb),
+            stages = stage_rates(stages, split_stage_work(hm, [(m, n, k)], args.tol, args.opA, "N", fa, fb),
                                  args.steps)
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
