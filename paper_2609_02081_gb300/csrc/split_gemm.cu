@@ -176,19 +176,23 @@ __device__ __forceinline__ int advance_job(const SplitJob* jobs, int njobs, int6
 
 __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int job, int64_t item, uint8_t* ws) {
   const SplitJob& sj = jobs[job];
-  const int64_t local = item - sj.item_begin;
-  const int64_t ntile = (int64_t)sj.tiles_m * sj.tiles_n;
-  const int64_t tile = local % ntile;
-  const int64_t rest = local / ntile;
-  const int p = (int)(rest % sj.np);
-  const int l = (int)(rest / sj.np);
+  // 32-bit arithmetic: a job has fewer than 2^31 items (checked on the host);
+  // every role decodes every item, so the divisions are a per-item cost
+  const uint32_t local = (uint32_t)(item - sj.item_begin);
+  const uint32_t ntile = (uint32_t)sj.tiles_m * (uint32_t)sj.tiles_n;
+  const uint32_t rest = local / ntile;
+  const uint32_t tile = local - rest * ntile;
+  const uint32_t l32 = rest / (uint32_t)sj.np;
+  const int p = (int)(rest - l32 * (uint32_t)sj.np);
+  const int l = (int)l32;
   // grouped raster: kRasterGroup tile rows, column-major inside the group
-  const int64_t per_group = (int64_t)kRasterGroup * sj.tiles_n;
-  const int grp = (int)(tile / per_group);
-  const int64_t within = tile % per_group;
-  const int rows_here = min(kRasterGroup, sj.tiles_m - grp * kRasterGroup);
-  const int tm = grp * kRasterGroup + (int)(within % rows_here);
-  const int tn = (int)(within / rows_here);
+  const uint32_t per_group = (uint32_t)kRasterGroup * (uint32_t)sj.tiles_n;
+  const uint32_t grp = tile / per_group;
+  const uint32_t within = tile - grp * per_group;
+  const uint32_t rows_here = (uint32_t)min(kRasterGroup, sj.tiles_m - (int)grp * kRasterGroup);
+  const uint32_t tn32 = within / rows_here;
+  const int tm = (int)(grp * kRasterGroup + (within - tn32 * rows_here));
+  const int tn = (int)tn32;
   Item it;
   it.nkb = sj.nkb;
   it.bn = sj.bn;
@@ -357,9 +361,60 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
       const int cols = it.bn >> 1;        // columns handled by this thread: a multiple of 16 up to 128
       const int col0 = half * cols;
       const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
+      const float pf = c_gmod[it.l].pf, pinv = c_gmod[it.l].inv;
+      if (nchunks == 1) {
+        // One chunk: each 32-column load is reduced and stored at once.
+        // fmod_centred rounds the exact product v * fl(1/p), which is within
+        // |v| 2^-24 / p of v / p, while v / p is at least 1/(2p) from a
+        // half-integer: for |v| < 2^23 (K <= 512: 127^2 K) one reduction
+        // gives the centred residue; longer products take a second one.
+        const uint32_t buf = chunk_ctr & 1u, aph = (chunk_ctr >> 1) & 1u;
+        int got = 0;
+        if (lane == 0) got = mbar_wait(smem_u32(&s.tfull[buf]), aph, abort_flag, err, kErrWaitEpilogue) ? 1 : 0;
+        got = __shfl_sync(0xffffffffu, got, 0);
+        __syncwarp();
+        if (!got) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * kBnMax + (uint32_t)col0;
+        const bool twice = it.nkb > 8;
+        int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
+#pragma unroll
+        for (int g = 0; g < kBnMax / 2 / 32; ++g) {
+          if (g * 32 < cols) {
+            uint32_t r[32];
+            TMEM_LD32(taddr + (uint32_t)(g * 32), r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < it.rows) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                const int c16 = g * 32 + h * 16;
+                if (c16 < cols && col0 + c16 < it.cols) {
+                  uint32_t w[4];
+#pragma unroll
+                  for (int v = 0; v < 4; ++v) {
+                    uint32_t u[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                      float t = fmod_centred(__uint_as_float(r[h * 16 + v * 4 + b]), pf, pinv);
+                      if (twice) t = fmod_centred(t, pf, pinv);
+                      u[b] = __float_as_uint(t + 12582912.0f);
+                    }
+                    w[v] = __byte_perm(__byte_perm(u[0], u[1], 0x0040), __byte_perm(u[2], u[3], 0x0040), 0x5410);
+                  }
+                  *reinterpret_cast<uint4*>(dst + c16) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+              }
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s.tempty[buf]));
+        ++chunk_ctr;
+        continue;
+      }
       // running sum of chunk residues (each |r| <= 129, at most 127 chunks:
       // exact in float)
-      const float pf = c_gmod[it.l].pf, pinv = c_gmod[it.l].inv;
       float acc[kBnMax / 2];
 #pragma unroll
       for (int i = 0; i < kBnMax / 2; ++i) acc[i] = 0.f;

@@ -256,7 +256,10 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     sj.encB_begin = sp.encB_units;
     sp.encB_units += enc_blocks(d.n, sj.nkb);
     sj.item_begin = sp.items;
-    sp.items += (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
+    // the residue GEMM decodes a job's items with 32-bit arithmetic
+    const int64_t job_items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
+    if (job_items >= ((int64_t)1 << 31)) return HMAT_STATUS_UNSUPPORTED;
+    sp.items += job_items;
     sj.crt_begin = sp.crt_units;
     sp.crt_units += crt_blocks(d.m, d.n);
     sp.max_bits = std::max(sp.max_bits, sj.bits);
@@ -283,6 +286,7 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   units->encA = enc_blocks(d.m, sj.nkb);
   units->encB = enc_blocks(d.n, sj.nkb);
   units->items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
+  if (units->items >= ((int64_t)1 << 31)) return HMAT_STATUS_UNSUPPORTED;
   units->crt = crt_blocks(d.m, d.n);
   units->max_bits = sj.bits;
   units->max_nmod = sj.nmod;
