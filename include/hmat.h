@@ -90,8 +90,12 @@ enum {
 
 typedef enum {
     /* Plain FP64: the bilinear products in FP64 arithmetic, pre-additions in
-     * the GEMM prologue and the recombination in its epilogue. Needs no
-     * workspace. */
+     * the GEMM prologue and the recombination in its epilogue.  Runs without
+     * workspace.  Given the workspace hmat_workspace_size reports, a call
+     * whose output tiles leave SMs idle splits the inner dimension of its
+     * products into slices (split-k, hmat_set_fp64_splitk_table) and adds the
+     * slices' partial outputs in slice order before alpha / beta: the result
+     * is deterministic but its rounding differs from the unsplit one. */
     HMAT_MODE_FP64 = 0,
     /* Split precision (Ozaki-type, integer modular): op(A), op(B) scaled by
      * per-row / per-column powers of two and rounded to integers; the
@@ -141,8 +145,10 @@ typedef struct {
  *                         mode, algorithm and the returned status.
  *   HMAT_TUNE_TABLE=file  install a tile-width table (the autotuner's JSON:
  *                         256 codes 0..3 after a "table" key) on the new
- *                         handle, as hmat_set_tile_table would; an unreadable
- *                         file keeps the built-in rule and prints a warning. */
+ *                         handle, as hmat_set_tile_table would, and, when the
+ *                         file has an "fp64_splitk" key, its 256 codes 0..4
+ *                         as hmat_set_fp64_splitk_table would; an unreadable
+ *                         file keeps the built-in rules and prints a warning. */
 
 /* Library version as major*10000 + minor*100 + patch. */
 HMAT_API
@@ -329,6 +335,18 @@ hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
 HMAT_API
 hmat_status hmat_measure_fp64_peak(int32_t kind, int64_t iterations, double *tflops, double *ms);
 
+/* FP64 split-k table: 16 x 16 int8 codes indexed [min(15, ceil(log2 T))]
+ * [min(15, ceil(log2 k))], T = output tiles (32 x 32) of the call, k = the
+ * product's inner dimension: 0 = built-in rule (double the slices, up to 8,
+ * while twice the tile-slices fit the SMs once and each slice keeps at least
+ * 64 of k), 1/2/3/4 = 1/2/4/8 slices.  Written by the autotuner
+ * (paper_2609_02081_gb300/autotune.py --fp64); NULL restores the rule.
+ * Applies to single-pass FP64 calls (every BILINEAR plan) made with
+ * workspace; hmat_workspace_size accounts for it.  Streamed products never
+ * split k.  Errors: NOT_INITIALIZED, INVALID_VALUE (a code outside 0..4). */
+HMAT_API
+hmat_status hmat_set_fp64_splitk_table(hmat_handle handle, const int8_t *table);
+
 /* Failure-detection self-test: launch one thread that waits on a device
  * barrier nothing will ever complete, with the same bounded wait the kernels
  * use and a limit of limit_cycles clock cycles (1 .. 2^33).  The wait gives up,
@@ -507,7 +525,7 @@ hmat_status hmat_bq_hadamard_block(hmat_handle handle, uint32_t flags, int64_t n
  * 0 fp64 bilinear, 1 split exponents, 2 split encode, 3 split residue GEMM,
  * 4 split CRT/recombine, 5 beta-scale, 6 isomorph map-in, 7 isomorph
  * map-out, 8 add / scale, 9 to-complex, 10 from-complex, 11 trace,
- * 12 Hermiticity, 13 Hadamard block. */
+ * 12 Hermiticity, 13 Hadamard block, 14 FP64 split-k reduction. */
 HMAT_API
 hmat_status hmat_set_profiling(hmat_handle handle, int32_t enable);
 HMAT_API

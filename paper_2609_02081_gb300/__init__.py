@@ -40,7 +40,7 @@ ALGOS = {"bilinear": HMAT_ALGO_BILINEAR, "standard": HMAT_ALGO_STANDARD, "isomor
 MODES = {"fp64": HMAT_MODE_FP64, "split": HMAT_MODE_SPLIT}
 KERNEL_IDS = {"fp64_bilinear": 0, "split_exponents": 1, "split_encode": 2, "split_residue_gemm": 3,
               "split_crt": 4, "beta_scale": 5, "iso_map_in": 6, "iso_map_out": 7, "add": 8, "to_complex": 9,
-              "from_complex": 10, "trace": 11, "hermiticity": 12, "hadamard": 13}
+              "from_complex": 10, "trace": 11, "hermiticity": 12, "hadamard": 13, "fp64_splitk_reduce": 14}
 STATUS = {0: "SUCCESS", 1: "INVALID_VALUE", 2: "UNSUPPORTED", 3: "MISALIGNED", 4: "WORKSPACE_TOO_SMALL",
           5: "CUDA_ERROR", 6: "DEVICE_TIMEOUT", 7: "NOT_INITIALIZED", 8: "TOLERANCE_UNREACHABLE", 9: "INTERNAL"}
 
@@ -89,6 +89,7 @@ SIGNATURES = {
     "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
     "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
+    "hmat_set_fp64_splitk_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
     "hmat_debug_wait_selftest": (ctypes.c_int, [_ptr, _i64, _ptr]),
     "hmat_measure_fp64_peak": (ctypes.c_int, [_i32, _i64, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
     "hmat_set_profiling": (ctypes.c_int, [_ptr, _i32]),
@@ -247,6 +248,14 @@ class Handle:
             return
         t = np.ascontiguousarray(table, dtype=np.int8).reshape(16, 16)
         _check(lib().hmat_set_tile_table(self._h, t.ctypes.data), "hmat_set_tile_table")
+
+    def set_fp64_splitk_table(self, table):
+        """Install a 16 x 16 FP64 split-k code table (None: built-in rule); see autotune.py."""
+        if table is None:
+            _check(lib().hmat_set_fp64_splitk_table(self._h, None), "hmat_set_fp64_splitk_table")
+            return
+        t = np.ascontiguousarray(table, dtype=np.int8).reshape(16, 16)
+        _check(lib().hmat_set_fp64_splitk_table(self._h, t.ctypes.data), "hmat_set_fp64_splitk_table")
 
     def device_error(self) -> int:
         code = _u32()

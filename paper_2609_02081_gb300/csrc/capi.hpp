@@ -18,7 +18,7 @@ namespace hmat {
 
 constexpr int kPlanSlots = 256;
 constexpr int kStageSlots = 8;
-constexpr int kKernelIds = 14;
+constexpr int kKernelIds = 15;
 constexpr size_t kGraphCache = 8;
 
 }  // namespace hmat
@@ -75,6 +75,10 @@ struct hmat_context {
   static constexpr int kStreamEvents = 16;
   cudaEvent_t sev[kStreamEvents] = {};
   bool log = false;                    // HMAT_LOG: one stderr line per product call
+  // FP64 split-k table (hmat_set_fp64_splitk_table): codes 0 (built-in rule),
+  // 1..4 (2^(code-1) slices) by [ceil(log2 tiles of the call)][ceil(log2 k)]
+  bool has_fp64_splitk = false;
+  int8_t fp64_splitk[hmat::kTileBins * hmat::kTileBins] = {};
 };
 
 namespace hmat {
@@ -101,6 +105,9 @@ struct SplitReuse {
   bool a = false;
   int64_t b_offset = -1;
   bool b_cached = false;
+  // FP64 mode: never split the inner dimension (the streamed blocks, so that
+  // they compute exactly what the in-core product computes)
+  bool fp64_whole_k = false;
 };
 
 // Validate, plan and launch `count` products on `stream_ptr` (hmat_bq_gemm and
@@ -108,9 +115,10 @@ struct SplitReuse {
 hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
                 void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse = SplitReuse{});
 
-// Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule).
+// Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule);
+// with a handle, FP64 mode includes the split-k partials the handle would use.
 hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
-                            double tol, size_t* bytes);
+                            double tol, size_t* bytes, const hmat_context* h = nullptr);
 
 // One stderr line per product call when HMAT_LOG is set.
 void log_call(const hmat_context* h, const char* fn, const hmat_gemm_desc& d, int32_t mode, hmat_status st);

@@ -35,6 +35,12 @@ struct JobDesc {
   double alpha_re, alpha_im, beta_re, beta_im;
   int32_t tiles_m, tiles_n;
   int64_t tile_begin;    // first global tile of this job (FP64 kernel)
+  // FP64 split-k: the inner dimension in kslices slices of kchunk (a multiple
+  // of the k-block); with kslices > 1 each (slice, tile) writes its eight
+  // recombined components to part[slice][tile][component][32 x 32] and a
+  // reduction adds the slices in order, then applies alpha / beta
+  int32_t kslices, kchunk;
+  double* part;
 };
 
 // Complex-isomorph route (isomorph.cu): image of op(X) as two planes (real,

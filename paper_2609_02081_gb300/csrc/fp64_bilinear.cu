@@ -50,8 +50,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
-// Stage k-block kb of the present components of op(A) (BM x BK) and op(B) (BK x BN).
-__device__ __forceinline__ void stage_raw(Fp64Smem& s, int buf, const JobDesc& jb, int i0, int j0, int k0) {
+// Stage k-block kb of the present components of op(A) (BM x BK) and op(B) (BK x BN);
+// inner indices at or beyond kend read as zero.
+__device__ __forceinline__ void stage_raw(Fp64Smem& s, int buf, const JobDesc& jb, int i0, int j0, int k0, int kend) {
   const int t = threadIdx.x;
   // op(A)[i, kk]: non-transposed reads run along k, transposed along i
   int r, kk;
@@ -59,7 +60,7 @@ __device__ __forceinline__ void stage_raw(Fp64Smem& s, int buf, const JobDesc& j
   else { r = t / F_BK; kk = t % F_BK; }
   {
     const int i = i0 + r, kg = k0 + kk;
-    const bool valid = (i < jb.m) && (kg < jb.k);
+    const bool valid = (i < jb.m) && (kg < kend);
     const int64_t off = jb.transA ? (int64_t)kg * jb.lda + i : (int64_t)i * jb.lda + kg;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -74,7 +75,7 @@ __device__ __forceinline__ void stage_raw(Fp64Smem& s, int buf, const JobDesc& j
   else { cj = t % F_BN; kk = t / F_BN; }
   {
     const int j = j0 + cj, kg = k0 + kk;
-    const bool valid = (j < jb.n) && (kg < jb.k);
+    const bool valid = (j < jb.n) && (kg < kend);
     const int64_t off = jb.transB ? (int64_t)j * jb.ldb + kg : (int64_t)kg * jb.ldb + j;
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -152,9 +153,13 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
   for (int64_t tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
     const int j = find_job(jobs, njobs, tile);
     const JobDesc& jb = jobs[j];
-    const int64_t local = tile - jb.tile_begin;
+    const int64_t ntile = (int64_t)jb.tiles_m * jb.tiles_n;
+    const int64_t local = (tile - jb.tile_begin) % ntile;
+    const int slice = (int)((tile - jb.tile_begin) / ntile);   // 0 unless the inner dimension is split
     const int i0 = (int)(local / jb.tiles_n) * F_BM;
     const int j0 = (int)(local % jb.tiles_n) * F_BN;
+    const int kbeg = slice * jb.kchunk;
+    const int kend = min(jb.k, kbeg + jb.kchunk);
     if (s.plan_id != jb.plan) {
       __syncthreads();
       if (t == 0) { s.plan = plans[jb.plan]; s.plan_id = jb.plan; }
@@ -169,11 +174,11 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
 #pragma unroll
     for (int q = 0; q < F_MAXP; ++q) acc[q][0] = acc[q][1] = acc[q][2] = acc[q][3] = 0.0;
 
-    const int nkb = (jb.k + F_BK - 1) / F_BK;
-    if (nkb > 0) stage_raw(s, 0, jb, i0, j0, 0);
+    const int nkb = (kend - kbeg + F_BK - 1) / F_BK;
+    if (nkb > 0) stage_raw(s, 0, jb, i0, j0, kbeg, kend);
     cp_async_commit();
     for (int kb = 0; kb < nkb; ++kb) {
-      if (kb + 1 < nkb) stage_raw(s, (kb + 1) & 1, jb, i0, j0, (kb + 1) * F_BK);
+      if (kb + 1 < nkb) stage_raw(s, (kb + 1) & 1, jb, i0, j0, kbeg + (kb + 1) * F_BK, kend);
       cp_async_commit();
       cp_async_wait<1>();
       __syncthreads();                // staged block kb visible; previous compute finished
@@ -215,6 +220,13 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
         }
         q[e] = o;
       }
+      if (jb.kslices > 1) {            // partial result of this slice, reduced later
+        double* dst = jb.part + ((int64_t)slice * ntile + local) * 8 * (F_BM * F_BN) +
+                      (2 * ty + (pt >> 1)) * F_BN + 2 * tx + (pt & 1);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[(int64_t)e * (F_BM * F_BN)] = q[e];
+        continue;
+      }
       if (i < jb.m && jj < jb.n) {
         double* cbase = jb.C + (int64_t)i * jb.ldc + jj;
         if (plain) {
@@ -240,6 +252,59 @@ fp64_bilinear_kernel(const JobDesc* __restrict__ jobs, int njobs, const KPlan* _
   }
 }
 
+// Split-k reduction of one job: C <- alpha (sum over the slices, in slice
+// order) + beta C, one thread per output element.
+__global__ void __launch_bounds__(256) fp64_splitk_reduce_kernel(JobDesc jb) {
+  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)jb.m * jb.n) return;
+  const int i = (int)(idx / jb.n), jj = (int)(idx % jb.n);
+  const int64_t ntile = (int64_t)jb.tiles_m * jb.tiles_n;
+  const int64_t tile = (int64_t)(i / F_BM) * jb.tiles_n + jj / F_BN;
+  const int within = (i % F_BM) * F_BN + jj % F_BN;
+  double q[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) q[e] = 0.0;
+  for (int sl = 0; sl < jb.kslices; ++sl) {
+    const double* src = jb.part + ((int64_t)sl * ntile + tile) * 8 * (F_BM * F_BN) + within;
+#pragma unroll
+    for (int e = 0; e < 8; ++e) q[e] += src[(int64_t)e * (F_BM * F_BN)];
+  }
+  double* cbase = jb.C + (int64_t)i * jb.ldc + jj;
+  const bool plain = (jb.alpha_re == 1.0 && jb.alpha_im == 0.0 && jb.beta_re == 0.0 && jb.beta_im == 0.0);
+  if (plain) {
+#pragma unroll
+    for (int e = 0; e < 8; ++e) cbase[(int64_t)e * jb.sC] = q[e];
+    return;
+  }
+  const bool use_beta = (jb.beta_re != 0.0 || jb.beta_im != 0.0);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    double re = jb.alpha_re * q[e] - jb.alpha_im * q[e + 4];
+    double im = jb.alpha_re * q[e + 4] + jb.alpha_im * q[e];
+    if (use_beta) {
+      const double cre = cbase[(int64_t)e * jb.sC];
+      const double cim = cbase[(int64_t)(e + 4) * jb.sC];
+      re += jb.beta_re * cre - jb.beta_im * cim;
+      im += jb.beta_re * cim + jb.beta_im * cre;
+    }
+    cbase[(int64_t)e * jb.sC] = re;
+    cbase[(int64_t)(e + 4) * jb.sC] = im;
+  }
+}
+
+cudaError_t launch_fp64_splitk_reduce(const JobDesc& jb, cudaStream_t stream) {
+  const int64_t elems = (int64_t)jb.m * jb.n;
+  if (elems <= 0) return cudaSuccess;
+  fp64_splitk_reduce_kernel<<<(unsigned)((elems + 255) / 256), 256, 0, stream>>>(jb);
+  return cudaGetLastError();
+}
+
+// Bytes of the split-k partial outputs of one product with kslices slices.
+int64_t fp64_splitk_bytes(int64_t m, int64_t n, int kslices) {
+  const int64_t tiles = ((m + F_BM - 1) / F_BM) * ((n + F_BN - 1) / F_BN);
+  return kslices > 1 ? (int64_t)kslices * tiles * 8 * F_BM * F_BN * (int64_t)sizeof(double) : 0;
+}
+
 size_t fp64_smem_bytes() { return sizeof(Fp64Smem); }
 
 cudaError_t fp64_configure() {
@@ -256,5 +321,6 @@ cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* 
 int fp64_tile_m() { return F_BM; }
 int fp64_max_products() { return F_MAXP; }
 int fp64_tile_n() { return F_BN; }
+int fp64_tile_k() { return F_BK; }
 
 }  // namespace hmat

@@ -80,7 +80,10 @@ cudaError_t launch_fp64_bilinear(const JobDesc* d_jobs, int njobs, const KPlan* 
                                  int grid, cudaStream_t stream);
 int fp64_tile_m();
 int fp64_tile_n();
+int fp64_tile_k();
 int fp64_max_products();
+int64_t fp64_splitk_bytes(int64_t m, int64_t n, int kslices);
+cudaError_t launch_fp64_splitk_reduce(const JobDesc& jb, cudaStream_t stream);
 cudaError_t launch_iso_map_in(const IsoMapIn& p, cudaStream_t s);
 cudaError_t launch_iso_map_out(const IsoMapOut& p, cudaStream_t s);
 
@@ -337,8 +340,78 @@ void add_fp64_job(Prepared* out, const JobDesc& j, int group) {
   out->f[group].push_back(j);
 }
 
+static int ceil_log2_bin(int64_t x) {
+  int b = 0;
+  while (b < kTileBins - 1 && ((int64_t)1 << b) < x) ++b;
+  return b;
+}
+
+// Slices of the inner dimension for an FP64 product of inner dimension k in a
+// call of `tiles` output tiles: the tuned table's entry when one is set, else
+// the built-in rule (double the slices while twice the tile-slices still fit
+// the SMs once and every slice keeps at least 64 of k; at most 8).
+int fp64_kslices(const hmat_context* h, int64_t tiles, int64_t k) {
+  int s = 1;
+  const int code = h->has_fp64_splitk ? h->fp64_splitk[ceil_log2_bin(tiles) * kTileBins + ceil_log2_bin(k)] : 0;
+  if (code >= 1 && code <= 4) {
+    s = 1 << (code - 1);
+  } else {
+    while (s < 8 && tiles * 2 * s <= h->sm_count && k >= 2 * s * 64) s *= 2;
+  }
+  while (s > 1 && k < s * fp64_tile_k()) s >>= 1;
+  return s;
+}
+
+// FP64 tile counts of the prepared launch groups; with `allow_splitk`, a
+// single-pass call whose tiles leave SMs idle splits the inner dimension of
+// its products (fp64_kslices) when the workspace holds the partial outputs
+// behind everything else (otherwise k is not split).
+void fp64_layout(hmat_context* h, Prepared* out, unsigned char* ws, size_t ws_bytes, bool allow_splitk) {
+  const int tm = fp64_tile_m(), tn = fp64_tile_n(), tk = fp64_tile_k();
+  int64_t call_tiles = 0;
+  for (auto& group : out->f)
+    for (auto& j : group) {
+      j.tiles_m = (j.m + tm - 1) / tm;
+      j.tiles_n = (j.n + tn - 1) / tn;
+      j.kslices = 1;
+      j.kchunk = j.k;
+      j.part = nullptr;
+      if (&group == &out->f[0]) call_tiles += (int64_t)j.tiles_m * j.tiles_n;
+    }
+  if (allow_splitk && out->f.size() == 1 && ws) {
+    int64_t off = align_up256(out->ws_needed);
+    bool fits = true;
+    for (auto& j : out->f[0]) {
+      const int s = fp64_kslices(h, call_tiles, j.k);
+      if (s <= 1) continue;
+      const int chunk = (int)((((int64_t)j.k + s - 1) / s + tk - 1) / tk * tk);
+      const int slices = (j.k + chunk - 1) / chunk;
+      if (slices <= 1) continue;
+      const int64_t bytes = fp64_splitk_bytes(j.m, j.n, slices);
+      if ((size_t)(off + bytes) > ws_bytes) { fits = false; break; }
+      j.kslices = slices;
+      j.kchunk = chunk;
+      j.part = reinterpret_cast<double*>(ws + off);
+      off = align_up256(off + bytes);
+    }
+    if (fits) {
+      out->ws_needed = std::max(out->ws_needed, off);
+    } else {
+      for (auto& j : out->f[0]) { j.kslices = 1; j.kchunk = j.k; j.part = nullptr; }
+    }
+  }
+  for (auto& group : out->f) {
+    int64_t tiles = 0;
+    for (auto& j : group) {
+      j.tile_begin = tiles;
+      tiles += (int64_t)j.tiles_m * j.tiles_n * j.kslices;
+    }
+    out->f_tiles.push_back(tiles);
+  }
+}
+
 hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                    void* workspace, size_t ws_bytes, cudaStream_t stream, Prepared* out) {
+                    void* workspace, size_t ws_bytes, cudaStream_t stream, Prepared* out, bool allow_splitk = true) {
   if (count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
   if (tol < 0 || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
@@ -404,17 +477,6 @@ hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs,
       }
     }
   }
-  const int tm = fp64_tile_m(), tn = fp64_tile_n();
-  for (auto& group : out->f) {
-    int64_t tiles = 0;
-    for (auto& j : group) {
-      j.tiles_m = (j.m + tm - 1) / tm;
-      j.tiles_n = (j.n + tn - 1) / tn;
-      j.tile_begin = tiles;
-      tiles += (int64_t)j.tiles_m * j.tiles_n;
-    }
-    out->f_tiles.push_back(tiles);
-  }
   out->split_offset = align_up256(iso_off);
   out->ws_needed = out->split_offset;
   if (!split_jobs.empty()) {
@@ -424,14 +486,26 @@ hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs,
     out->has_split = true;
     out->ws_needed += out->sp.ws_needed;
   }
+  fp64_layout(h, out, ws, ws_bytes, allow_splitk);
   return HMAT_STATUS_SUCCESS;
 }
 
 hmat_status launch_fp64_group(hmat_context* h, const Prepared& pr, int g, const JobDesc* d_jobs,
                               cudaStream_t stream) {
   const int grid = (int)std::min<int64_t>(pr.f_tiles[g], h->sm_count);
-  ProfScope ps(h, 0, stream);
-  return cuda_status(launch_fp64_bilinear(d_jobs, (int)pr.f[g].size(), h->d_plans, pr.f_tiles[g], grid, stream));
+  {
+    ProfScope ps(h, 0, stream);
+    cudaError_t e = launch_fp64_bilinear(d_jobs, (int)pr.f[g].size(), h->d_plans, pr.f_tiles[g], grid, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  // split-k: the slices of each split product added in order, then alpha / beta
+  for (const JobDesc& j : pr.f[g]) {
+    if (j.kslices <= 1) continue;
+    ProfScope ps(h, 14, stream);
+    cudaError_t e = launch_fp64_splitk_reduce(j, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return HMAT_STATUS_SUCCESS;
 }
 
 hmat_status launch_iso_in(hmat_context* h, const Prepared& pr, cudaStream_t stream) {
@@ -462,7 +536,7 @@ hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int
   h->last_bad = -1;
   if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
   Prepared pr;
-  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr);
+  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr, !reuse.fp64_whole_k);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (pr.has_split && pr.sp.jobs.size() == 1 && h->algo != HMAT_ALGO_ISOMORPH) {
     pr.sp.reuse_a = reuse.a;
@@ -631,6 +705,26 @@ cudaError_t configure_device(int device) {
 // key followed by 16 x 16 integer codes 0..3) installed on every new handle.
 // A file that cannot be read or parsed leaves the built-in rule and prints one
 // warning line.
+// 16 x 16 integer codes 0..max_code following `key` in text; false if absent or malformed.
+static bool read_codes(const std::string& text, const char* key, int max_code, int8_t* table) {
+  const size_t at = text.find(key);
+  if (at == std::string::npos) return false;
+  int count = 0;
+  for (size_t i = at + std::strlen(key); i < text.size() && count < kTileBins * kTileBins; ++i) {
+    const char c = text[i];
+    if (c >= '0' && c <= '9') {
+      int v = 0;
+      while (i < text.size() && text[i] >= '0' && text[i] <= '9') v = 10 * v + (text[i++] - '0');
+      if (v > max_code) return false;
+      table[count++] = (int8_t)v;
+      --i;
+    } else if (c == '-' || c == '}') {
+      return false;
+    }
+  }
+  return count == kTileBins * kTileBins;
+}
+
 void load_env_tile_table(hmat_context* h) {
   const char* path = std::getenv("HMAT_TUNE_TABLE");
   if (!path || !*path) return;
@@ -644,30 +738,24 @@ void load_env_tile_table(hmat_context* h) {
   size_t got;
   while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
   std::fclose(f);
-  const size_t key = text.find("\"table\"");
   int8_t table[kTileBins * kTileBins];
-  int count = 0;
-  bool ok = key != std::string::npos;
-  for (size_t i = ok ? key + 7 : text.size(); i < text.size() && count < kTileBins * kTileBins; ++i) {
-    const char c = text[i];
-    if (c >= '0' && c <= '9') {
-      int v = 0;
-      while (i < text.size() && text[i] >= '0' && text[i] <= '9') v = 10 * v + (text[i++] - '0');
-      if (v > 3) { ok = false; break; }
-      table[count++] = (int8_t)v;
-      --i;
-    } else if (c == '-' || c == '}') {
-      ok = false;
-      break;
-    }
-  }
-  if (!ok || count != kTileBins * kTileBins) {
+  if (!read_codes(text, "\"table\"", 3, table)) {
     std::fprintf(stderr, "hmat: HMAT_TUNE_TABLE %s: expected %d codes 0..3 after \"table\"; using the built-in "
                  "tile rule\n", path, kTileBins * kTileBins);
     return;
   }
   std::memcpy(h->split.tile_table, table, sizeof(table));
   h->split.has_table = true;
+  // optional: the FP64 split-k table
+  if (text.find("\"fp64_splitk\"") != std::string::npos) {
+    if (read_codes(text, "\"fp64_splitk\"", 4, table)) {
+      std::memcpy(h->fp64_splitk, table, sizeof(table));
+      h->has_fp64_splitk = true;
+    } else {
+      std::fprintf(stderr, "hmat: HMAT_TUNE_TABLE %s: expected %d codes 0..4 after \"fp64_splitk\"; using the "
+                   "built-in split-k rule\n", path, kTileBins * kTileBins);
+    }
+  }
 }
 
 const char* kModeNames[] = {"fp64", "split"};
@@ -737,7 +825,7 @@ namespace hmat {
 
 // Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule).
 hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
-                            double tol, size_t* bytes) {
+                            double tol, size_t* bytes, const hmat_context* h) {
   if (!bytes || count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
   if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
   *bytes = 0;
@@ -767,6 +855,30 @@ hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const 
     if (st != HMAT_STATUS_SUCCESS) return st;
   }
   *bytes = (size_t)align_up256(iso) + split;
+  if (h && mode == HMAT_MODE_FP64 && algo != HMAT_ALGO_STANDARD) {
+    // the split-k partials of a call whose products all run in one FP64 pass
+    // (every bilinear plan has at most 24 products), as fp64_layout places them
+    const int tm = fp64_tile_m(), tn = fp64_tile_n(), tk = fp64_tile_k();
+    int64_t tiles = 0;
+    for (int32_t i = 0; i < count; ++i) {
+      const int64_t m = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].m : descs[i].m;
+      const int64_t n = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].n : descs[i].n;
+      if (m > 0 && n > 0) tiles += ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
+    }
+    int64_t off = (int64_t)align_up256((int64_t)*bytes);
+    for (int32_t i = 0; i < count; ++i) {
+      const int64_t m = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].m : descs[i].m;
+      const int64_t n = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].n : descs[i].n;
+      const int64_t k = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].k : descs[i].k;
+      if (m <= 0 || n <= 0 || k <= 0) continue;
+      const int s = fp64_kslices(h, tiles, k);
+      if (s <= 1) continue;
+      const int64_t chunk = ((k + s - 1) / s + tk - 1) / tk * tk;
+      const int slices = (int)((k + chunk - 1) / chunk);
+      if (slices > 1) off = align_up256(off + fp64_splitk_bytes(m, n, slices));
+    }
+    if (off > (int64_t)align_up256((int64_t)*bytes)) *bytes = (size_t)off;
+  }
   return HMAT_STATUS_SUCCESS;
 }
 
@@ -777,7 +889,7 @@ extern "C" {
 hmat_status hmat_workspace_size(hmat_handle h, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
                                 double tol, size_t* bytes) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
-  return workspace_bytes(h->algo, split_table(h), count, descs, mode, tol, bytes);
+  return workspace_bytes(h->algo, split_table(h), count, descs, mode, tol, bytes, h);
 }
 
 hmat_status hmat_bq_gemm(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, uint32_t flagsB, int64_t m,
@@ -934,6 +1046,21 @@ hmat_status hmat_set_tile_table(hmat_handle h, const int8_t* table) {
     if (table[i] < 0 || table[i] > 3) return HMAT_STATUS_INVALID_VALUE;
   std::memcpy(h->split.tile_table, table, sizeof(h->split.tile_table));
   h->split.has_table = true;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_set_fp64_splitk_table(hmat_handle h, const int8_t* table) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  std::lock_guard<std::mutex> lock(h->mu);
+  if (!table) {
+    h->has_fp64_splitk = false;
+    std::memset(h->fp64_splitk, 0, sizeof(h->fp64_splitk));
+    return HMAT_STATUS_SUCCESS;
+  }
+  for (int i = 0; i < kTileBins * kTileBins; ++i)
+    if (table[i] < 0 || table[i] > 4) return HMAT_STATUS_INVALID_VALUE;
+  std::memcpy(h->fp64_splitk, table, sizeof(h->fp64_splitk));
+  h->has_fp64_splitk = true;
   return HMAT_STATUS_SUCCESS;
 }
 

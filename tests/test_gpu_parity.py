@@ -272,6 +272,78 @@ def test_grouped_full_plans_of_different_widths(handle, use_graph):
             np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
 
 
+def _splitk_table(code):
+    t = np.zeros((16, 16), dtype=np.int8)
+    t[:, :] = code
+    return t
+
+
+@pytest.mark.parametrize("code", [1, 2, 3, 4])
+@pytest.mark.parametrize("opA,opB,fa,fb", [("N", "N", bi.BQ, bi.BQ), ("H", "T", bi.TRS, bi.TRA),
+                                           ("C", "QC", bi.COMPLEX, bi.BQ)])
+def test_fp64_split_k(handle, code, opA, opB, fa, fb):
+    """FP64 mode with the inner dimension in 1, 2, 4 or 8 slices (forced by the
+    split-k table): within FP64 rounding of the oracle on random data with
+    complex alpha, beta, and bit-exact on small integers; one slice is the
+    unsplit computation bit for bit."""
+    dev = torch.device("cuda")
+    m, n, k = 96, 80, 700
+    A = bi.uniform(160, *stored(opA, m, k), flags=fa)
+    B = bi.uniform(161, *stored(opB, k, n), flags=fb)
+    C0 = bi.uniform(162, m, n)
+    want = oracle.bq_gemm(A.numpy(), B.numpy(), opA, opB, alpha=0.5 + 1.5j, beta=-1 + 0.5j, C=C0.numpy())
+    handle.set_fp64_splitk_table(_splitk_table(code))
+    try:
+        got = run(handle, A, B, opA, opB, fa, fb, alpha=0.5 + 1.5j, beta=-1 + 0.5j, C0=C0, mode="fp64")
+        assert rel(got, want) <= 1e-14
+        Ai = bi.small_int(163, *stored(opA, m, k), flags=fa)
+        Bi = bi.small_int(164, *stored(opB, k, n), flags=fb)
+        wi = oracle.bq_gemm(Ai.numpy(), Bi.numpy(), opA, opB)
+        np.testing.assert_array_equal(run(handle, Ai, Bi, opA, opB, fa, fb, mode="fp64"), wi)
+        if code == 1:                          # one slice: no workspace needed, same bits
+            Cn = C0.clone().to(dev)
+            hm.hmat_bq_gemm(handle, A.to(dev), B.to(dev), Cn, opA, opB, fa, fb, 0.5 + 1.5j, -1 + 0.5j,
+                            mode="fp64", workspace=None)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(Cn.cpu().numpy(), got)
+    finally:
+        handle.set_fp64_splitk_table(None)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_fp64_split_k_builtin_rule_grouped(handle, use_graph):
+    """Few-tile FP64 products in one grouped call take the built-in split-k
+    rule (the workspace size query accounts for it); bit-exact on small
+    integers, eager and replayed from a graph."""
+    dev = torch.device("cuda")
+    shapes = [(64, 64, 1024), (40, 100, 333), (128, 32, 65)]
+    probs, descs = [], []
+    for i, (m, n, k) in enumerate(shapes):
+        A = bi.small_int(170 + i, m, k)
+        B = bi.small_int(180 + i, k, n)
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        dA, dB = A.to(dev), B.to(dev)
+        probs.append((A, B, C, dA, dB))
+        descs.append(hm.make_desc(dA, dB, C))
+    assert hm.hmat_workspace_size(handle, descs, "fp64") > 0      # the partial outputs of the slices
+    for _ in range(2):
+        for p in probs:
+            p[2].fill_(float("nan"))
+        hm.hmat_bq_gemm_grouped(handle, descs, mode="fp64", use_graph=use_graph, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for A, B, C, _, _ in probs:
+            np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+    h2 = hm.Handle()
+    try:
+        h2.set_profiling(True)
+        probs[0][2].fill_(float("nan"))
+        hm.hmat_bq_gemm(h2, probs[0][3], probs[0][4], probs[0][2], mode="fp64")
+        torch.cuda.synchronize()
+        assert h2.profile("fp64_splitk_reduce")[0] == 1               # n = 64: 4 tiles, k split
+    finally:
+        h2.close()
+
+
 def test_argument_errors(handle):
     dev = torch.device("cuda")
     A = torch.zeros((8, 4, 4), dtype=torch.float64, device=dev)
