@@ -63,7 +63,8 @@ def parse(argv=None):
     ap.add_argument("--budget-gb", type=float, default=64.0, help="streamed: device budget in GB")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--groups", type=int, default=512, help="grouped: the first G of the 512 problems")
-    ap.add_argument("--tile-table", default=None, help="tile-width table JSON written by the autotuner")
+    ap.add_argument("--tile-table", default=None,
+                    help="tuned tables (tile width, FP64 split-k) JSON written by the autotuner")
     ap.add_argument("--results", default=None,
                     help="JSON-lines file: append each result with its configuration key; a configuration already "
                          "in the file is not run again (its stored line is printed)")
@@ -409,6 +410,12 @@ def ours(args, rank, world, local):
     C = torch.empty((8, m, n), dtype=torch.float64, device=dev)
     h = hm.Handle()
     h.set_algorithm(args.algo)
+    if args.tile_table:
+        from paper_2609_02081_gb300 import autotune
+        h.set_tile_table(autotune.load(args.tile_table))
+        fp = autotune.load_fp64(args.tile_table)
+        if fp is not None:
+            h.set_fp64_splitk_table(fp)
     d = hm.make_desc(A, B, C, args.opA, "N", fa, fb)
     ws_bytes = hm.hmat_workspace_size(h, [d], args.mode, args.tol)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
@@ -607,6 +614,9 @@ def grouped(args, rank, world, local):
     if args.tile_table:
         from paper_2609_02081_gb300 import autotune
         h.set_tile_table(autotune.load(args.tile_table))
+        fp = autotune.load_fp64(args.tile_table)
+        if fp is not None:
+            h.set_fp64_splitk_table(fp)
     ws_bytes = hm.hmat_workspace_size(h, descs, args.mode, args.tol)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)

@@ -1,13 +1,22 @@
-"""Autotuner for the split-mode output tile width (hmat_set_tile_table).
+"""Autotuner for the split-mode output tile width (hmat_set_tile_table) and
+the FP64 split-k slice count (hmat_set_fp64_splitk_table).
 
-For every (ceil(log2 m), ceil(log2 n)) bin that a set of problem shapes
-touches, the tuner times one representative product of that bin on the GPU
-with each tile width (128 x 64, 128 x 128, 128 x 256) and keeps the fastest.
-The result is a 16 x 16 table of codes (0 = built-in rule, 1/2/3 = 64/128/256
-columns) that :meth:`Handle.set_tile_table` installs; it is saved as JSON.
+Tile width: for every (ceil(log2 m), ceil(log2 n)) bin that a set of problem
+shapes touches, the tuner times one representative product of that bin on the
+GPU with each tile width (128 x 64, 128 x 128, 128 x 256) and keeps the
+fastest.  The result is a 16 x 16 table of codes (0 = built-in rule, 1/2/3 =
+64/128/256 columns) that :meth:`Handle.set_tile_table` installs.
+
+Split-k (--fp64): for every (ceil(log2 tiles), ceil(log2 k)) bin of the FP64
+shapes, one representative product is timed in FP64 mode with its inner
+dimension in 1, 2, 4 and 8 slices; the fastest code (1..4) goes into a second
+16 x 16 table that :meth:`Handle.set_fp64_splitk_table` installs.  Both are
+saved in one JSON file ("table", "fp64_splitk"), the format HMAT_TUNE_TABLE
+reads.
 
     python -m paper_2609_02081_gb300.autotune --out tile_table.json          # the 512-shape batch
     python -m paper_2609_02081_gb300.autotune --shapes 256x256x256,1024x64x512
+    python -m paper_2609_02081_gb300.autotune --fp64 256x256x256,128x128x2048 --out tuned.json
 """
 from __future__ import annotations
 
@@ -74,14 +83,71 @@ def tune(shapes, tol: float = 1e-12, reps: int = 5, seed: int = 0):
     return table, report
 
 
-def save(table, report, path):
+def _time_fp64(h, A, B, C, reps):
+    import torch
+    stream = torch.cuda.current_stream()
+    nbytes = hmat_workspace_size(h, [make_desc(A, B, C)], "fp64")
+    ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=A.device)
+    hmat_bq_gemm(h, A, B, C, mode="fp64", workspace=ws, stream=stream)   # warm
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        hmat_bq_gemm(h, A, B, C, mode="fp64", workspace=ws, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_fp64(shapes, reps: int = 5, seed: int = 0):
+    """Return (split-k table, report) for FP64 products of the given (m, n, k) shapes."""
+    import torch
+    dev = torch.device("cuda")
+    groups = {}
+    for m, n, k in shapes:
+        tiles = math.ceil(m / 32) * math.ceil(n / 32)
+        groups.setdefault((_bin(tiles), _bin(k)), []).append((m, n, k))
+    table = np.zeros((BINS, BINS), dtype=np.int8)
+    report = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(seed)
+    with Handle() as h:
+        for (bt, bk), members in sorted(groups.items()):
+            members.sort(key=lambda s: s[0] * s[1] * s[2])
+            m, n, k = members[len(members) // 2]
+            A = torch.rand((8, m, k), generator=g, device=dev, dtype=torch.float64) * 2 - 1
+            B = torch.rand((8, k, n), generator=g, device=dev, dtype=torch.float64) * 2 - 1
+            C = torch.empty((8, m, n), dtype=torch.float64, device=dev)
+            times = {}
+            for code in (1, 2, 3, 4):
+                t = np.zeros((BINS, BINS), dtype=np.int8)
+                t[bt, bk] = code
+                h.set_fp64_splitk_table(t)
+                times[1 << (code - 1)] = _time_fp64(h, A, B, C, reps)
+            best = min(times, key=times.get)
+            table[bt, bk] = int(math.log2(best)) + 1
+            report[f"{bt},{bk}"] = {"shape": [m, n, k], "ms": times, "best_slices": best, "members": len(members)}
+    return table, report
+
+
+def save(table, report, path, fp64_table=None, fp64_report=None):
+    out = {"table": np.asarray(table).astype(int).tolist(), "report": report}
+    if fp64_table is not None:
+        out["fp64_splitk"] = np.asarray(fp64_table).astype(int).tolist()
+        out["fp64_report"] = fp64_report
     with open(path, "w") as f:
-        json.dump({"table": np.asarray(table).astype(int).tolist(), "report": report}, f, indent=1)
+        json.dump(out, f, indent=1)
 
 
 def load(path):
     with open(path) as f:
         return np.asarray(json.load(f)["table"], dtype=np.int8)
+
+
+def load_fp64(path):
+    """The FP64 split-k table of a tuned JSON file, or None."""
+    with open(path) as f:
+        t = json.load(f).get("fp64_splitk")
+    return None if t is None else np.asarray(t, dtype=np.int8)
 
 
 def main():
@@ -90,6 +156,7 @@ def main():
                     help="'batch512' (512 log-uniform shapes in [32,1024], seed 104) or 'MxNxK,MxNxK,...'")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--fp64", default=None, help="'MxNxK,...': also tune the FP64 split-k table on these shapes")
     ap.add_argument("--out", default="tile_table.json")
     args = ap.parse_args()
     if args.shapes == "batch512":
@@ -100,8 +167,12 @@ def main():
     else:
         shapes = [tuple(int(x) for x in s.split("x")) for s in args.shapes.split(",")]
     table, report = tune(shapes, args.tol, args.reps)
-    save(table, report, args.out)
-    print(json.dumps({"bins": len(report), "out": args.out}))
+    ftable = freport = None
+    if args.fp64:
+        fshapes = [tuple(int(x) for x in s.split("x")) for s in args.fp64.split(",")]
+        ftable, freport = tune_fp64(fshapes, args.reps)
+    save(table, report, args.out, ftable, freport)
+    print(json.dumps({"bins": len(report), "fp64_bins": len(freport or {}), "out": args.out}))
 
 
 if __name__ == "__main__":
