@@ -378,38 +378,41 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * kBnMax + (uint32_t)col0;
         const bool twice = it.nkb > 8;
         int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
+        // 32 columns at a time; the buffer goes back to the MMA issuer right
+        // after the last load, before that group's arithmetic and stores
 #pragma unroll
         for (int g = 0; g < kBnMax / 2 / 32; ++g) {
-          if (g * 32 < cols) {
-            uint32_t r[32];
-            TMEM_LD32(taddr + (uint32_t)(g * 32), r);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-            if (row < it.rows) {
+          if (g * 32 >= cols) break;
+          uint32_t r[32];
+          TMEM_LD32(taddr + (uint32_t)(g * 32), r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if ((g + 1) * 32 >= cols) {                // last load: release the buffer
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&s.tempty[buf]));
+          }
+          if (row < it.rows) {
 #pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                const int c16 = g * 32 + h * 16;
-                if (c16 < cols && col0 + c16 < it.cols) {
-                  uint32_t w[4];
+            for (int h = 0; h < 2; ++h) {
+              const int c16 = g * 32 + h * 16;
+              if (c16 < cols && col0 + c16 < it.cols) {
+                uint32_t w[4];
 #pragma unroll
-                  for (int v = 0; v < 4; ++v) {
-                    uint32_t u[4];
+                for (int v = 0; v < 4; ++v) {
+                  uint32_t u[4];
 #pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                      float t = fmod_centred(__uint_as_float(r[h * 16 + v * 4 + b]), pf, pinv);
-                      if (twice) t = fmod_centred(t, pf, pinv);
-                      u[b] = __float_as_uint(t + 12582912.0f);
-                    }
-                    w[v] = __byte_perm(__byte_perm(u[0], u[1], 0x0040), __byte_perm(u[2], u[3], 0x0040), 0x5410);
+                  for (int b = 0; b < 4; ++b) {
+                    float t = fmod_centred(__uint_as_float(r[h * 16 + v * 4 + b]), pf, pinv);
+                    if (twice) t = fmod_centred(t, pf, pinv);
+                    u[b] = __float_as_uint(t + 12582912.0f);
                   }
-                  *reinterpret_cast<uint4*>(dst + c16) = make_uint4(w[0], w[1], w[2], w[3]);
+                  w[v] = __byte_perm(__byte_perm(u[0], u[1], 0x0040), __byte_perm(u[2], u[3], 0x0040), 0x5410);
                 }
+                *reinterpret_cast<uint4*>(dst + c16) = make_uint4(w[0], w[1], w[2], w[3]);
               }
             }
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&s.tempty[buf]));
         ++chunk_ctr;
         continue;
       }
