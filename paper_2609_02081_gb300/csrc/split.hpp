@@ -190,6 +190,7 @@ cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, 
 // all_full: every job uses the paper's full plan, served by the unrolled kernel
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
                              cudaStream_t s, unsigned char* ws, int max_nmod, bool all_full);
-cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint32_t* crt_c, const uint32_t* crt_P);
+cudaError_t split_upload_constants(const int* moduli, int nmod_table, const int32_t* crt_d, const uint32_t* crt_P,
+                                   const uint32_t* crt_off);
 
 }  // namespace hmat

@@ -218,9 +218,22 @@ __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int job, int64
 // v - p * round(v / p) for an integer-valued float |v| <= 2^24 (exact; the
 // rounding uses the 1.5 * 2^23 shift, valid while |v / p| < 2^22).
 // The result lies in [-(p+1)/2, (p+1)/2].
-__device__ __forceinline__ float fmod_centred(float v, float pf, float inv) {
-  const float q = fmaf(v, inv, 12582912.0f) - 12582912.0f;
-  return fmaf(-q, pf, v);
+// Two lanes at once with paired FP32 instructions (npf = -p, inv = fl(1/p)
+// in both lanes); each lane rounds as fmaf(v, inv, 1.5 * 2^23) - 1.5 * 2^23
+// and fmaf(-q, p, v) would.
+__device__ __forceinline__ float2 fmod_centred2(float2 v, float2 npf, float2 inv) {
+  const float2 q = __fadd2_rn(__ffma2_rn(v, inv, make_float2(12582912.0f, 12582912.0f)),
+                              make_float2(-12582912.0f, -12582912.0f));
+  return __ffma2_rn(q, npf, v);
+}
+
+// the int8 residues of four centred values (|t| <= 128) in one word: the low
+// byte of the bits of t + 1.5 * 2^23 is t mod 256 (two's complement)
+__device__ __forceinline__ uint32_t pack4_residues(float2 t01, float2 t23) {
+  const float2 m = make_float2(12582912.0f, 12582912.0f);
+  const float2 u01 = __fadd2_rn(t01, m), u23 = __fadd2_rn(t23, m);
+  return __byte_perm(__byte_perm(__float_as_uint(u01.x), __float_as_uint(u01.y), 0x0040),
+                     __byte_perm(__float_as_uint(u23.x), __float_as_uint(u23.y), 0x0040), 0x5410);
 }
 
 }  // namespace
@@ -362,9 +375,10 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
       const int col0 = half * cols;
       const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
       const float pf = c_gmod[it.l].pf, pinv = c_gmod[it.l].inv;
+      const float2 npf2 = make_float2(-pf, -pf), inv2 = make_float2(pinv, pinv);
       if (nchunks == 1) {
         // One chunk: each 32-column load is reduced and stored at once.
-        // fmod_centred rounds the exact product v * fl(1/p), which is within
+        // fmod_centred2 rounds the exact product v * fl(1/p), which is within
         // |v| 2^-24 / p of v / p, while v / p is at least 1/(2p) from a
         // half-integer: for |v| < 2^23 (K <= 512: 127^2 K) one reduction
         // gives the centred residue; longer products take a second one.
@@ -399,14 +413,15 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
                 uint32_t w[4];
 #pragma unroll
                 for (int v = 0; v < 4; ++v) {
-                  uint32_t u[4];
-#pragma unroll
-                  for (int b = 0; b < 4; ++b) {
-                    float t = fmod_centred(__uint_as_float(r[h * 16 + v * 4 + b]), pf, pinv);
-                    if (twice) t = fmod_centred(t, pf, pinv);
-                    u[b] = __float_as_uint(t + 12582912.0f);
+                  const int b = h * 16 + v * 4;
+                  float2 t01 = fmod_centred2(make_float2(__uint_as_float(r[b]), __uint_as_float(r[b + 1])), npf2, inv2);
+                  float2 t23 =
+                      fmod_centred2(make_float2(__uint_as_float(r[b + 2]), __uint_as_float(r[b + 3])), npf2, inv2);
+                  if (twice) {
+                    t01 = fmod_centred2(t01, npf2, inv2);
+                    t23 = fmod_centred2(t23, npf2, inv2);
                   }
-                  w[v] = __byte_perm(__byte_perm(u[0], u[1], 0x0040), __byte_perm(u[2], u[3], 0x0040), 0x5410);
+                  w[v] = pack4_residues(t01, t23);
                 }
                 *reinterpret_cast<uint4*>(dst + c16) = make_uint4(w[0], w[1], w[2], w[3]);
               }
@@ -438,7 +453,12 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
             TMEM_LD32(taddr + (uint32_t)(g * 32), r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 32; ++i) acc[g * 32 + i] += fmod_centred(__uint_as_float(r[i]), pf, pinv);
+            for (int i = 0; i < 32; i += 2) {
+              const float2 t = fmod_centred2(make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), npf2, inv2);
+              const float2 a = __fadd2_rn(make_float2(acc[g * 32 + i], acc[g * 32 + i + 1]), t);
+              acc[g * 32 + i] = a.x;
+              acc[g * 32 + i + 1] = a.y;
+            }
           }
         }
         tc_fence_before();
@@ -459,12 +479,9 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
             uint32_t w[4];
 #pragma unroll
             for (int v = 0; v < 4; ++v) {
-              // the low byte of (r + 1.5 * 2^23)'s bits is r mod 256 (two's complement)
-              uint32_t u[4];
-#pragma unroll
-              for (int bidx = 0; bidx < 4; ++bidx)
-                u[bidx] = __float_as_uint(fmod_centred(acc[g * 16 + v * 4 + bidx], pf, pinv) + 12582912.0f);
-              w[v] = __byte_perm(__byte_perm(u[0], u[1], 0x0040), __byte_perm(u[2], u[3], 0x0040), 0x5410);
+              const int b = g * 16 + v * 4;
+              w[v] = pack4_residues(fmod_centred2(make_float2(acc[b], acc[b + 1]), npf2, inv2),
+                                    fmod_centred2(make_float2(acc[b + 2], acc[b + 3]), npf2, inv2));
             }
             *reinterpret_cast<uint4*>(dst + g * 16) = make_uint4(w[0], w[1], w[2], w[3]);
           }

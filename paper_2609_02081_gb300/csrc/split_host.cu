@@ -79,24 +79,43 @@ uint32_t inv_mod(uint32_t a, uint32_t m) {
 }  // namespace
 
 cudaError_t split_configure() {
-  uint32_t crt[kMaxModuli + 1][kMaxModuli][kLimbs];
+  int32_t crt[kMaxModuli + 1][kMaxModuli][kLimbs];
   uint32_t P[kMaxModuli + 1][kLimbs];
+  uint32_t off[kMaxModuli + 1][kLimbs];
   std::memset(crt, 0, sizeof(crt));
   std::memset(P, 0, sizeof(P));
+  std::memset(off, 0, sizeof(off));
   for (int n = 1; n <= kMaxModuli; ++n) {
     P[n][0] = 1;
     for (int l = 0; l < n; ++l) big_mul_small(P[n], (uint32_t)kModuli[l]);
+    // offset N P with N = n * kMaxWeightSum * 127 (the CRT sums stay positive)
+    std::memcpy(off[n], P[n], sizeof(off[n]));
+    big_mul_small(off[n], (uint32_t)(n * kMaxWeightSum * 127));
     for (int l = 0; l < n; ++l) {
-      // c_l = (P / p_l) * ((P / p_l)^-1 mod p_l)
+      // d_l = (P / p_l) * ((P / p_l)^-1 4^-1 mod p_l): congruent to 4^-1 modulo
+      // p_l and to 0 modulo the other moduli, below P
+      const uint32_t p = (uint32_t)kModuli[l];
       uint32_t Ml[kLimbs] = {1, 0, 0, 0, 0};
       for (int j = 0; j < n; ++j)
         if (j != l) big_mul_small(Ml, (uint32_t)kModuli[j]);
-      const uint32_t inv = inv_mod(big_mod_small(Ml, (uint32_t)kModuli[l]), (uint32_t)kModuli[l]);
-      big_mul_small(Ml, inv);
-      std::memcpy(crt[n][l], Ml, sizeof(Ml));
+      const uint32_t inv = inv_mod(big_mod_small(Ml, p), p);
+      const uint32_t inv4 = inv_mod(4u, p);
+      big_mul_small(Ml, (uint32_t)((unsigned long long)inv * inv4 % p));
+      // signed 32-bit digits: each word above 2^31 - 1 borrows from the next
+      long long carry = 0;
+      for (int q = 0; q < kLimbs; ++q) {
+        long long w = (long long)Ml[q] + carry;
+        carry = 0;
+        if (w >= (1ll << 31)) {
+          w -= 1ll << 32;
+          carry = 1;
+        }
+        crt[n][l][q] = (int32_t)w;
+      }
+      if (carry != 0) return cudaErrorInvalidValue;   // d_l < P < 2^(32 kLimbs - 1)
     }
   }
-  cudaError_t e = split_upload_constants(kModuli, kModTable, &crt[0][0][0], &P[0][0]);
+  cudaError_t e = split_upload_constants(kModuli, kModTable, &crt[0][0][0], &P[0][0], &off[0][0]);
   if (e != cudaSuccess) return e;
   return split_gemm_configure(kModuli, kModTable);
 }

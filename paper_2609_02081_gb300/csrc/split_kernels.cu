@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include "split.hpp"
 
 namespace hmat {
@@ -21,15 +23,15 @@ struct ModConst {
   float c18;    // 2^18 mod p, centred
   float c36;    // 2^36 mod p, centred
   float c23;    // 2^23 mod p, in [0, p)
-  int inv4;     // 4^-1 mod p
-  int kp;       // p ceil(2^21 / p): makes 4Q 4^-1 non-negative
-  uint32_t magic;  // ceil(2^32 / p)
   unsigned long long fm;  // floor(2^64 / p) + 1 (fast exact 32-bit mod)
 };
 
 __constant__ ModConst c_mod[kModTable];
-__constant__ uint32_t c_crt[kMaxModuli + 1][kMaxModuli][kLimbs];  // [nmod][l] CRT basis (P/p_l)*inv_l
+// [nmod][l]: d_l = (P/p_l) ((P/p_l)^-1 4^-1 mod p_l) in signed 32-bit digits
+// (digit q weighs 2^(32 q), each in [-2^31, 2^31))
+__constant__ int32_t c_crt[kMaxModuli + 1][kMaxModuli][kLimbs];
 __constant__ uint32_t c_P[kMaxModuli + 1][kLimbs];                // product of the first nmod moduli
+__constant__ uint32_t c_off[kMaxModuli + 1][kLimbs];              // N P with N = nmod * kMaxWeightSum * 127
 __constant__ float c_Pinv[kMaxModuli + 1];                        // 2^(32 Pbase) / P as float
 __constant__ int c_Pbase[kMaxModuli + 1];                         // limb index one below P's top limb
 
@@ -428,11 +430,13 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
 // imaginary-part ones (M5..M8); the split is warp-uniform.  The np residue
 // rows of each modulus are prefetched into a four-slot shared-memory ring
 // with cp.async two moduli ahead.  Per modulus the output residues
-// sum_p w4[e][p] T_p are formed (the paper's recombination for the bilinear
-// plan, __dp4a against the packed weights otherwise), times 4^-1 mod p gives
-// the residue of the output.  S_e = sum_l r_{l,e} c_l accumulates in 64-bit
-// limbs (c_l the CRT basis); S_e - q P with q the nearest integer to S_e / P is
-// the centred output, converted to FP64 with one rounding and scaled by
+// sum_p w4[e][p] T_p = x_{l,e} are formed (the paper's recombination for the
+// bilinear plan, __dp4a against the packed weights otherwise): x_{l,e} 4^-1 is
+// congruent to the output modulo p_l.  S_e = N P + sum_l x_{l,e} d_l, with d_l
+// the CRT basis element that also carries 4^-1 mod p_l, accumulates in signed
+// 64-bit limb sums without any per-modulus reduction; S_e - q P with q the
+// nearest integer to S_e / P is the centred output, converted to FP64 with one
+// rounding and scaled by
 // 2^-(s_i + t_j); then the complex alpha / beta update (Sec. III scaling and
 // addition), for which the two halves trade their four components through
 // shared memory.
@@ -488,23 +492,47 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 
-// Residue in [0, p) of 4Q times 4^-1 for |4Q| <= kMaxWeightSum * 127 = 4572
-// (every plan; checked on the host): x = 4Q 4^-1 + K p lies
-// in [0, 2^23) (K p >= 2^21 > 4572 * 254), and with M = ceil(2^32 / p) the
-// quotient floor(x M / 2^32) is exact while x (M p - 2^32) < 2^32, i.e. for
-// x < 2^32 / p (Granlund and Montgomery, division by invariant integers).
-__device__ __forceinline__ uint32_t residue_q4(int q4, const ModConst& mc) {
-  const uint32_t x = (uint32_t)(q4 * mc.inv4 + mc.kp);
-  return x - __umulhi(x, mc.magic) * (uint32_t)mc.p;
+// |X| = [x3 x2 x1 x0] (below 2^127) times 2^scale_exp as a double, rounded
+// to nearest even: the top 64 significant bits from the two 64-bit halves and
+// one leading-zero count, the bits below as a sticky bit.
+__device__ __forceinline__ double limbs4_to_double(const uint32_t* x, int neg, int scale_exp) {
+  unsigned long long hi = ((unsigned long long)x[3] << 32) | x[2];
+  unsigned long long lo = ((unsigned long long)x[1] << 32) | x[0];
+  const bool hz = hi == 0ull;
+  int e0 = hz ? scale_exp : 64 + scale_exp;       // weight 2^e0 of hi's bit 0
+  hi = hz ? lo : hi;
+  lo = hz ? 0ull : lo;
+  if (hi == 0ull) return neg ? -0.0 : 0.0;
+  const int lz = __clzll((long long)hi);
+  unsigned long long top = (hi << lz) | ((lo >> 1) >> (63 - lz));   // bit 63 set
+  if ((lo << lz) != 0ull) top |= 1ull;            // sticky bit: one correct rounding below
+  const int E = e0 - lz;                          // value = top 2^E
+  const int bexp = E + 1086;                      // IEEE biased exponent of top 2^E
+  if (bexp >= 1 && bexp <= 2046) {
+    const unsigned long long mant = top >> 11;
+    const uint32_t rem = (uint32_t)top & 0x7FFu;
+    const unsigned long long up = (rem > 0x400u || (rem == 0x400u && (mant & 1ull))) ? 1ull : 0ull;
+    const unsigned long long bits = ((unsigned long long)(bexp - 1) << 52) + mant + up;
+    return __longlong_as_double((long long)(bits | ((unsigned long long)neg << 63)));
+  }
+  const double v = __ull2double_rn(top);          // subnormal or overflowing result
+  const double r = scalbn(v, E);
+  return neg ? -r : r;
 }
 
-// The output stage shared by the CRT kernels: S_e = sum_l r_{l,e} c_l in the
-// 64-bit limb accumulators acc[e] becomes the centred integer X_e = S_e - q P,
-// then the double X_e 2^-(s_i + t_j), then C (plain store, or the complex
-// alpha / beta update for which the two halves trade their four components
-// through xch).  Every thread of the block calls it (it may synchronise).
+// The output stage shared by the CRT kernels.  acc[e] holds S_e in L signed
+// 64-bit limb sums (limb q weighs 2^(32 q)): S_e = N P + sum_l x_{l,e} d_l with
+// |x| <= kMaxWeightSum * 127 and 0 <= d_l < P, so 0 < S_e < 2 N P.  S_e is
+// congruent to the output X_e modulo P, and the modulus count leaves
+// |X| < 2^-1.25 P: S_e / P lies within 0.42 of the integer q = (S_e - X_e) / P.
+// The float estimate of S_e / P from the leading limbs (six roundings,
+// relative error below 2^-21.4; S_e / P < 2 N <= 2^17.4, so the absolute error
+// stays below 0.06) rounds to q, and S_e - q P is X_e itself.  X_e becomes the
+// double X_e 2^-(s_i + t_j), then C (plain store, or the complex alpha / beta
+// update for which the two halves trade their four components through xch).
+// Every thread of the block calls it (it may synchronise).
 template <int L>
-__device__ __forceinline__ void crt_output(const unsigned long long (&acc)[4][L], uint32_t emask, const SplitJob& sj,
+__device__ __forceinline__ void crt_output(const long long (&acc)[4][L], uint32_t emask, const SplitJob& sj,
                                            const JobDesc& d, const unsigned char* ws, int nm, int i, int j, int half,
                                            int col, double (*xch)[kCrtCols]) {
   const bool valid = j < d.n;
@@ -512,28 +540,24 @@ __device__ __forceinline__ void crt_output(const unsigned long long (&acc)[4][L]
   if (valid) {
     const int s_i = reinterpret_cast<const int32_t*>(ws + sj.off_sexp)[i];
     const int t_j = reinterpret_cast<const int32_t*>(ws + sj.off_texp)[j];
+    const int pb = c_Pbase[nm];
+    const float pinv = c_Pinv[nm];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       if (!((emask >> e) & 1u)) continue;      // identically zero: +0
       uint32_t x[L];
-      unsigned long long carry = 0;
+      long long t = acc[e][0];
+      x[0] = (uint32_t)t;
 #pragma unroll
-      for (int q = 0; q < L; ++q) {
-        const unsigned long long tq = acc[e][q] + carry;
-        x[q] = (uint32_t)tq;
-        carry = tq >> 32;
+      for (int q = 1; q < L; ++q) {            // signed carries; t ends as S >> 32 (L - 1), below 2^35
+        t = acc[e][q] + (t >> 32);
+        x[q] = (uint32_t)t;
       }
-      // S = sum_l r_l c_l is congruent to the output X mod P, and the modulus
-      // count leaves |X| < 2^-1.25 P, so S / P lies within 0.42 of the integer
-      // q = (S - X) / P.  The float estimate of S / P from the leading limbs
-      // (S < nmod * 255 * P: relative error ~2^-22, absolute below 10^-3)
-      // rounds to q, and S - q P is X itself, no correction step.
-      const int pb = c_Pbase[nm];
-      float sf = 0.f;
+      float sf = fmaf((float)(int)(t >> 32), 4294967296.f, (float)x[L - 1]);
 #pragma unroll
-      for (int q = L - 1; q >= 0; --q)
-        if (q >= pb) sf = sf * 4294967296.f + (float)x[q];
-      const uint32_t qq = (uint32_t)__float2int_rn(sf * c_Pinv[nm]);
+      for (int q = L - 2; q >= 0; --q)
+        if (q >= pb) sf = fmaf(sf, 4294967296.f, (float)x[q]);
+      const uint32_t qq = __float2uint_rn(sf * pinv);
       long long borrow = 0;
       unsigned long long mulc = 0;
 #pragma unroll
@@ -544,20 +568,19 @@ __device__ __forceinline__ void crt_output(const unsigned long long (&acc)[4][L]
         x[q] = (uint32_t)diff;
         borrow = diff >> 32;
       }
-      const int neg = (int)(x[L - 1] >> 31);
-      if (neg) {                               // |X| = ~x + 1
-        unsigned long long c = 1;
+      const uint32_t neg = x[L - 1] >> 31;     // |X| = (x ^ -neg) + neg, without a branch
+      const uint32_t flip = 0u - neg;
+      unsigned long long c = neg;
 #pragma unroll
-        for (int q = 0; q < L; ++q) {
-          const unsigned long long tq = (unsigned long long)(~x[q]) + c;
-          x[q] = (uint32_t)tq;
-          c = tq >> 32;
-        }
+      for (int q = 0; q < L; ++q) {
+        const unsigned long long tq = (unsigned long long)(x[q] ^ flip) + c;
+        x[q] = (uint32_t)tq;
+        c = tq >> 32;
       }
-      q4v[e] = limbs_to_double<L>(x, neg, -(s_i + t_j));
+      if constexpr (L == 4) q4v[e] = limbs4_to_double(x, (int)neg, -(s_i + t_j));
+      else q4v[e] = limbs_to_double<L>(x, (int)neg, -(s_i + t_j));
     }
   }
-
   double* cbase = d.C + (int64_t)i * d.ldc + j;
   const bool plain = (d.alpha_re == 1.0 && d.alpha_im == 0.0 && d.beta_re == 0.0 && d.beta_im == 0.0);
   if (plain) {                                 // block-uniform
@@ -659,11 +682,11 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
   issue(0);
   issue(1);
 
-  unsigned long long acc[4][L];
+  long long acc[4][L];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
-    for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
+    for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
 
   const bool structured = sj.full != 0;     // the paper's full plan
   // outputs of this half with a nonzero weight (a subalgebra plan leaves some
@@ -683,12 +706,11 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
     issue(l + 2);
     cp_async_wait2();            // modulus l has landed
     __syncthreads();
-    const ModConst& mc = c_mod[l];
-    uint32_t cl[L];
+    int32_t cl[L];
 #pragma unroll
     for (int q = 0; q < L; ++q) cl[q] = c_crt[nm][l][q];
     const uint8_t(*slot)[kCrtCols] = ring[l % kStages];
-    uint32_t ru[4];
+    int x4[4];
     if (structured) {
       // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
       // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
@@ -705,10 +727,10 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
           v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
       }
       const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
-      ru[0] = residue_q4(8 * v[0] - (a + c), mc);
-      ru[1] = residue_q4(-8 * v[1] + (a - c), mc);
-      ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
-      ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
+      x4[0] = 8 * v[0] - (a + c);
+      x4[1] = -8 * v[1] + (a - c);
+      x4[2] = -8 * v[2] + (b + dd);
+      x4[3] = -8 * v[3] + (b - dd);
     } else {
       // np residues packed four to a word, dotted with the packed weights of
       // this half's outputs; only the plan's words, only outputs with weights
@@ -724,13 +746,13 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
           if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) ru[e] = residue_q4(o[e], mc);   // |o| <= kMaxWeightSum * 127
+      for (int e = 0; e < 4; ++e) x4[e] = o[e];   // |o| <= kMaxWeightSum * 127
     }
 #pragma unroll
     for (int e = 0; e < 4; ++e)
       if ((emask >> e) & 1u) {
 #pragma unroll
-        for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * cl[q];
+        for (int q = 0; q < L; ++q) acc[e][q] += (long long)x4[e] * cl[q];
       }
   }
 
@@ -745,7 +767,7 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
 constexpr int kFullPlanes = 24;
 
 template <int L, int NM>
-__device__ __forceinline__ void crt_full_accumulate(unsigned long long (&acc)[4][L], const unsigned char* rowbase,
+__device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], const unsigned char* rowbase,
                                                     int64_t plane, int cmax, int nm_dyn, int tid, int col, int half,
                                                     uint8_t (*ring)[kFullPlanes][kCrtCols]) {
   const int nm = NM > 0 ? NM : nm_dyn;
@@ -762,7 +784,6 @@ __device__ __forceinline__ void crt_full_accumulate(unsigned long long (&acc)[4]
     issue(l + 2);
     cp_async_wait2();            // modulus l has landed
     __syncthreads();
-    const ModConst& mc = c_mod[l];
     const uint8_t(*slot)[kCrtCols] = ring[l & 3];
     // P_r = (T1 - T2) + i (T3 - T1 - T2); 4 Q_e = +-8 P_e +- P5 +- P6 +- P7 +- P8
     int v[8];
@@ -775,15 +796,11 @@ __device__ __forceinline__ void crt_full_accumulate(unsigned long long (&acc)[4]
         v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
     }
     const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
-    uint32_t ru[4];
-    ru[0] = residue_q4(8 * v[0] - (a + c), mc);
-    ru[1] = residue_q4(-8 * v[1] + (a - c), mc);
-    ru[2] = residue_q4(-8 * v[2] + (b + dd), mc);
-    ru[3] = residue_q4(-8 * v[3] + (b - dd), mc);
+    const int x4[4] = {8 * v[0] - (a + c), -8 * v[1] + (a - c), -8 * v[2] + (b + dd), -8 * v[3] + (b - dd)};
 #pragma unroll
     for (int e = 0; e < 4; ++e)
 #pragma unroll
-      for (int q = 0; q < L; ++q) acc[e][q] += (unsigned long long)ru[e] * c_crt[nm][l][q];
+      for (int q = 0; q < L; ++q) acc[e][q] += (long long)x4[e] * c_crt[nm][l][q];
   };
   issue(0);
   issue(1);
@@ -816,11 +833,11 @@ __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const S
   const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
   const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
   const int cmax = cavail < kCrtCols / 16 ? (int)cavail : kCrtCols / 16;
-  unsigned long long acc[4][L];
+  long long acc[4][L];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
 #pragma unroll
-    for (int q = 0; q < L; ++q) acc[e][q] = 0ull;
+    for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
   const int64_t pl = sj.res_plane;
   if (L == 4 && nm == 13) crt_full_accumulate<L, 13>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
   else if (L == 4 && nm == 14) crt_full_accumulate<L, 14>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
@@ -829,7 +846,8 @@ __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const S
 }
 
 // ------------------------------------------------------------------ launchers
-cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint32_t* crt_c, const uint32_t* crt_P) {
+cudaError_t split_upload_constants(const int* moduli, int nmod_table, const int32_t* crt_d, const uint32_t* crt_P,
+                                   const uint32_t* crt_off) {
   ModConst mc[kModTable];
   for (int l = 0; l < kModTable; ++l) {
     const int p = l < nmod_table ? moduli[l] : 255;
@@ -845,19 +863,15 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
     m.c18 = centred(1ll << 18);
     m.c36 = centred(1ll << 36);
     m.c23 = (float)((1ll << 23) % p);
-    int inv4 = 0;
-    for (int x = 1; x < p; ++x)
-      if ((4 * x) % p == 1) { inv4 = x; break; }
-    m.inv4 = inv4;
-    m.kp = p * (((1 << 21) + p - 1) / p);
-    m.magic = (uint32_t)((1ull << 32) / (unsigned long long)p + 1ull);
     m.fm = ~0ull / (unsigned long long)p + 1ull;
   }
   cudaError_t e = cudaMemcpyToSymbol(c_mod, mc, sizeof(mc));
   if (e != cudaSuccess) return e;
-  e = cudaMemcpyToSymbol(c_crt, crt_c, sizeof(uint32_t) * (kMaxModuli + 1) * kMaxModuli * kLimbs);
+  e = cudaMemcpyToSymbol(c_crt, crt_d, sizeof(int32_t) * (kMaxModuli + 1) * kMaxModuli * kLimbs);
   if (e != cudaSuccess) return e;
   e = cudaMemcpyToSymbol(c_P, crt_P, sizeof(uint32_t) * (kMaxModuli + 1) * kLimbs);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyToSymbol(c_off, crt_off, sizeof(uint32_t) * (kMaxModuli + 1) * kLimbs);
   if (e != cudaSuccess) return e;
   float pinv[kMaxModuli + 1];
   int pb[kMaxModuli + 1];
@@ -870,6 +884,15 @@ cudaError_t split_upload_constants(const int* moduli, int nmod_table, const uint
     double f = 0.0;                    // P / 2^(32 pb), then its float reciprocal
     for (int q = kLimbs - 1; q >= pb[n]; --q) f = f * 4294967296.0 + (double)P[q];
     pinv[n] = f > 0.0 ? (float)(1.0 / f) : 1.f;
+    // crt_output's quotient estimate: 2 + 2 (L - 1 - pb) + 2 float roundings
+    // of relative size 2^-24 on S / P < 2 N must stay below the 0.0796 margin
+    // (1/2 - 2^-1.25) for both limb counts that can run n moduli
+    for (int L = 4; L <= kLimbs; ++L) {
+      if (n > 14 && L == 4) continue;
+      const double rounds = 4.0 + 2.0 * (L - 1 - pb[n]);
+      if (rounds * std::ldexp(1.0, -24) * 2.0 * n * kMaxWeightSum * 127.0 >= 0.5 - std::exp2(-1.25))
+        return cudaErrorInvalidValue;
+    }
   }
   e = cudaMemcpyToSymbol(c_Pbase, pb, sizeof(pb));
   if (e != cudaSuccess) return e;
