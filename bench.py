@@ -250,12 +250,15 @@ def split_stage_work(hm, shapes, tol, opA="N", opB="N", fa=0xFF, fb=0xFF, algo="
     bytes for the exponent, encode and CRT stages (what each stage must read and write:
     the present FP64 components, the encoded factor tiles of the plan's nlf / nrf factors
     per modulus, the int8 residue of every product and modulus, C) and BF16 flops for the
-    residue GEMM (moduli x products x 2 m n k)."""
+    residue GEMM (moduli x products x 2 m n k); "split_residue_gemm_bytes" is the least
+    DRAM traffic of the residue GEMM (every encoded factor tile read once, every int8
+    residue written once), its bound on products too small to reuse their tiles."""
     P, U, V, _, _ = hm.plan_info(opA, opB, fa, fb, algo=algo)
     nlf = len({tuple(r) for r in U.tolist()})
     nrf = len({tuple(r) for r in V.tolist()})
     ca, cb = bin(fa).count("1"), bin(fb).count("1")
-    w = {"split_exponents": 0.0, "split_encode": 0.0, "split_crt": 0.0, "split_residue_gemm": 0.0}
+    w = {"split_exponents": 0.0, "split_encode": 0.0, "split_crt": 0.0, "split_residue_gemm": 0.0,
+         "split_residue_gemm_bytes": 0.0}
     for m, n, k in shapes:
         L = len(hm.split_info(k, tol)[0])
         kp = -(-k // 64) * 64
@@ -264,6 +267,7 @@ def split_stage_work(hm, shapes, tol, opA="N", opB="N", fa=0xFF, fb=0xFF, algo="
         w["split_encode"] += raw + 2.0 * L * (nlf * m + nrf * n) * kp
         w["split_crt"] += L * P * m * n + 64.0 * m * n
         w["split_residue_gemm"] += 2.0 * L * P * m * n * k
+        w["split_residue_gemm_bytes"] += 2.0 * L * (nlf * m + nrf * n) * kp + L * P * m * n
     return w
 
 
@@ -275,6 +279,9 @@ def stage_rates(stages, work, steps=1):
             continue
         if name == "split_residue_gemm":
             st["TFLOP_per_s"] = work[name] * steps / (ms * 1e-3) / 1e12
+            if "split_residue_gemm_bytes" in work:
+                st["GB_per_s"] = work["split_residue_gemm_bytes"] * steps / (ms * 1e-3) / 1e9
+                st["algorithmic_bytes_per_step"] = work["split_residue_gemm_bytes"]
         else:
             st["GB_per_s"] = work[name] * steps / (ms * 1e-3) / 1e9
             st["algorithmic_bytes_per_step"] = work[name]
@@ -680,8 +687,17 @@ def grouped(args, rank, world, local):
             errs.append(float(np.linalg.norm(C.cpu().numpy() - want) / np.linalg.norm(want)))
         cpu_base = {"value": f_or / t_or / 1e12, "unit": "TFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
                     "sample": f"the 16 sampled problems of the batch (m n k <= 2^25), {t_or:.1f} s"}
+        roof_hbm = None
         if args.mode == "split":
             stages = stage_rates(stages, split_stage_work(hm, shapes, args.tol))
+            g = stages.get("split_residue_gemm", {})
+            if g.get("GB_per_s"):
+                hbm = measured_peaks()[0].get("hbm_gbs")
+                roof_hbm = {"bound": "hbm", "achieved": g["GB_per_s"], "peak": hbm, "unit": "GB/s",
+                            "frac": g["GB_per_s"] / hbm if hbm else None, "kernel": "split_residue_gemm_kernel",
+                            "note": "the residue GEMM against the copy bandwidth for its least DRAM traffic "
+                                    "(encoded factor tiles read once, int8 residues written once): the bound "
+                                    "of products whose tiles feed one to four output tiles"}
         line = {"metric": "grouped biquaternion GEMM TFLOP/s (64-GEMM-equiv.)", "value": value, "unit": "TFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -691,7 +707,8 @@ def grouped(args, rank, world, local):
                            "tol": args.tol, "total_flops_64equiv": flops64,
                            "tile_table": args.tile_table, "workspace_bytes": ws_bytes},
                 "max_rel_fro_err_16_sampled": max(errs), "clocks": clk, "stages_one_step": stages,
-                "roofline": roof, "cpu_baseline": cpu_base, "gpu_launches": launches_per_step * args.steps}
+                "roofline": roof, "roofline_hbm": roof_hbm, "cpu_baseline": cpu_base,
+                "gpu_launches": launches_per_step * args.steps}
         emit(args, line)
     barrier(world)
     h.close()

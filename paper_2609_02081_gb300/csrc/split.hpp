@@ -43,6 +43,10 @@ constexpr int kTileK = 64;         // BF16 elements per 128-byte swizzled row
 constexpr int kChunkK = 1024;      // inner steps per exact FP32 accumulation chunk
 constexpr int kTileBins = 16;      // tile-width table: bins of ceil(log2 m) x ceil(log2 n)
 constexpr int kCrtCols = 128;      // CRT output columns per block (two threads per element)
+// CRT output rows per block: one for the full-plan kernel (launches whose
+// jobs all use the paper's full plan), kCrtRows for the others
+constexpr int kCrtRows = 4;
+inline int crt_rows_per_block(bool all_full) { return all_full ? 1 : kCrtRows; }
 // Largest sum_p |w4[e][p]| of a plan (the paper's full plan: 8 + 4 x 1 on the
 // three Gauss terms); with centred product residues |T| <= 127 every output
 // residue sum satisfies |4Q| <= 36 * 127 = 4572, which the CRT's integer
@@ -122,7 +126,7 @@ struct SplitPrep {
   std::vector<SplitJob> jobs;
   int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
   int64_t ws_needed = 0;
-  int max_bits = 0, max_nmod = 0;
+  int max_bits = 0, max_nmod = 0, max_np = 0;
   bool all_full = true;             // every job uses the paper's full plan
   // one job whose A-side exponents and encoded factor tiles are already in the
   // workspace from the previous call with the same A block and the same shape
@@ -147,7 +151,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
 // uses no heap memory (for the entry point that allocates nothing).
 struct SplitUnits {
   int64_t exp = 0, encA = 0, encB = 0, items = 0, crt = 0, ws_bytes = 0;
-  int max_bits = 0, max_nmod = 0;
+  int max_bits = 0, max_nmod = 0, max_np = 0;
   bool all_full = false;
 };
 hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
@@ -187,9 +191,11 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
                                 cudaStream_t s, unsigned char* ws, int max_bits);
 cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
                               unsigned char* ws);
-// all_full: every job uses the paper's full plan, served by the unrolled kernel
+// all_full: every job uses the paper's full plan (structured recombination);
+// else plans of at most 24 products take the packed-weight kernel with the
+// same layout, larger ones (the component-wise comparison plan) the generic one
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod, bool all_full);
+                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full);
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const int32_t* crt_d, const uint32_t* crt_P,
                                    const uint32_t* crt_off);
 

@@ -173,8 +173,10 @@ static constexpr int64_t kPlaneSkewRes = 3 * 256;
 // 16 (the residue GEMM copies whole 8-row groups of a tile and never reads the
 // rows beyond them) and the inner dimension padded to whole k-blocks (zeros)
 static inline int64_t enc_blocks(int64_t rows, int64_t nkb) { return ((rows + 15) / 16) * (nkb * kTileK / 32); }
-// CRT blocks: one per output row and kCrtCols consecutive columns
-static inline int64_t crt_blocks(int64_t m, int64_t n) { return m * ((n + kCrtCols - 1) / kCrtCols); }
+// CRT blocks: one per `rows` output rows and kCrtCols consecutive columns
+static inline int64_t crt_blocks(int64_t m, int64_t n, int rows) {
+  return ((m + rows - 1) / rows) * ((n + kCrtCols - 1) / kCrtCols);
+}
 
 // Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
 static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const int8_t* table, SplitJob* sj,
@@ -279,12 +281,17 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     const int64_t job_items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
     if (job_items >= ((int64_t)1 << 31)) return HMAT_STATUS_UNSUPPORTED;
     sp.items += job_items;
-    sj.crt_begin = sp.crt_units;
-    sp.crt_units += crt_blocks(d.m, d.n);
     sp.max_bits = std::max(sp.max_bits, sj.bits);
     sp.max_nmod = std::max(sp.max_nmod, sj.nmod);
+    sp.max_np = std::max(sp.max_np, sj.np);
     sp.all_full = sp.all_full && sj.full;
     sp.jobs.push_back(sj);
+  }
+  // the CRT kernel, and with it the rows per block, depends on every job's plan
+  const int crt_rows = crt_rows_per_block(sp.all_full);
+  for (SplitJob& sj : sp.jobs) {
+    sj.crt_begin = sp.crt_units;
+    sp.crt_units += crt_blocks(sj.d.m, sj.d.n, crt_rows);
   }
   if ((size_t)off > ws_bytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
   sp.ws_needed = off;
@@ -306,9 +313,10 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   units->encB = enc_blocks(d.n, sj.nkb);
   units->items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
   if (units->items >= ((int64_t)1 << 31)) return HMAT_STATUS_UNSUPPORTED;
-  units->crt = crt_blocks(d.m, d.n);
+  units->crt = crt_blocks(d.m, d.n, crt_rows_per_block(sj.full != 0));
   units->max_bits = sj.bits;
   units->max_nmod = sj.nmod;
+  units->max_np = sj.np;
   units->all_full = sj.full != 0;
   units->ws_bytes = off;
   *out = sj;
@@ -345,7 +353,7 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
   if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 4, stream);
-    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod, sp.all_full);
+    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod, sp.max_np, sp.all_full);
   }
   return e == cudaSuccess ? HMAT_STATUS_SUCCESS : split_cuda_error(e);
 }

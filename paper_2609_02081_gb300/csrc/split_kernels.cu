@@ -648,15 +648,17 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
     }
     wpk[e][w] = word;
   }
-  // this block: row i, columns jb*kCrtCols .. jb*kCrtCols + kCrtCols - 1 of the output
+  // this block: rows i0 .. i0 + rows - 1, columns jb*kCrtCols .. jb*kCrtCols + kCrtCols - 1
   const int64_t local = blk - sj.crt_begin;
   const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
-  const int i = (int)(local / colblocks);
+  const int i0 = (int)(local / colblocks) * kCrtRows;
+  const int rows = d.m - i0 < kCrtRows ? d.m - i0 : kCrtRows;
   const int jb = (int)(local % colblocks);
   const int j = jb * kCrtCols + col;
   const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
   const int64_t plane = sj.res_plane;
-  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
+  const unsigned char* const base0 = ws + sj.off_res + (int64_t)i0 * ncols + (int64_t)jb * kCrtCols;
+  const unsigned char* rowbase = base0;
   const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
   const int cmax = cavail < kChunksPerRow ? (int)cavail : kChunksPerRow;
 
@@ -679,15 +681,6 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
     }
     cp_async_commit();
   };
-  issue(0);
-  issue(1);
-
-  long long acc[4][L];
-#pragma unroll
-  for (int e = 0; e < 4; ++e)
-#pragma unroll
-    for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
-
   const bool structured = sj.full != 0;     // the paper's full plan
   // outputs of this half with a nonzero weight (a subalgebra plan leaves some
   // components identically zero: they skip the sums and convert to +0)
@@ -702,61 +695,114 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
       emask |= (any != 0u ? 1u : 0u) << e;
     }
   }
-  for (int l = 0; l < nm; ++l) {
-    issue(l + 2);
-    cp_async_wait2();            // modulus l has landed
-    __syncthreads();
-    int32_t cl[L];
-#pragma unroll
-    for (int q = 0; q < L; ++q) cl[q] = c_crt[nm][l][q];
-    const uint8_t(*slot)[kCrtCols] = ring[l % kStages];
-    int x4[4];
-    if (structured) {
-      // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
-      // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
-      // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); real parts
-      // in half 0, imaginary parts in half 1, in 32-bit integers
-      // (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
-      int v[8];
-      if (half == 0) {
-#pragma unroll
-        for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
-      } else {
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
-      }
-      const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
-      x4[0] = 8 * v[0] - (a + c);
-      x4[1] = -8 * v[1] + (a - c);
-      x4[2] = -8 * v[2] + (b + dd);
-      x4[3] = -8 * v[3] + (b - dd);
-    } else {
-      // np residues packed four to a word, dotted with the packed weights of
-      // this half's outputs; only the plan's words, only outputs with weights
-      int o[4] = {0, 0, 0, 0};
-#pragma unroll 2
-      for (int w = 0; emask != 0u && w < nw; ++w) {
-        uint32_t word = 0;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-          if (4 * w + b < np) word |= (uint32_t)slot[4 * w + b][col] << (8 * b);
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
-      }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) x4[e] = o[e];   // |o| <= kMaxWeightSum * 127
-    }
+  for (int rr = 0; rr < rows; ++rr) {
+    if (rr > 0) __syncthreads();      // every thread is done with the previous row's ring slots
+    rowbase = base0 + (int64_t)rr * ncols;
+    issue(0);
+    issue(1);
+    long long acc[4][L];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
-      if ((emask >> e) & 1u) {
 #pragma unroll
-        for (int q = 0; q < L; ++q) acc[e][q] += (long long)x4[e] * cl[q];
+      for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
+    for (int l = 0; l < nm; ++l) {
+      issue(l + 2);
+      cp_async_wait2();            // modulus l has landed
+      __syncthreads();
+      int32_t cl[L];
+#pragma unroll
+      for (int q = 0; q < L; ++q) cl[q] = c_crt[nm][l][q];
+      const uint8_t(*slot)[kCrtCols] = ring[l % kStages];
+      int x4[4];
+      if (structured) {
+        // the paper's recombination on residues: P_r = (T1 - T2) + i (T3 - T1 - T2),
+        // 4 Q1 = 8 P1 - (P5+P6+P7+P8), 4 Q2 = -8 P2 + (P5+P6-P7-P8),
+        // 4 Q3 = -8 P3 + (P5-P6+P7-P8), 4 Q4 = -8 P4 + (P5-P6-P7+P8); real parts
+        // in half 0, imaginary parts in half 1, in 32-bit integers
+        // (|T| <= 127, |P| <= 381, |4Q| <= 12 * 381)
+        int v[8];
+        if (half == 0) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+        } else {
+#pragma unroll
+          for (int r = 0; r < 8; ++r)
+            v[r] = (int)(int8_t)slot[3 * r + 2][col] - (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
+        }
+        const int a = v[4] + v[5], b = v[4] - v[5], c = v[6] + v[7], dd = v[6] - v[7];
+        x4[0] = 8 * v[0] - (a + c);
+        x4[1] = -8 * v[1] + (a - c);
+        x4[2] = -8 * v[2] + (b + dd);
+        x4[3] = -8 * v[3] + (b - dd);
+      } else {
+        // np residues packed four to a word, dotted with the packed weights of
+        // this half's outputs; only the plan's words, only outputs with weights
+        int o[4] = {0, 0, 0, 0};
+#pragma unroll 2
+        for (int w = 0; emask != 0u && w < nw; ++w) {
+          uint32_t word = 0;
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (4 * w + b < np) word |= (uint32_t)slot[4 * w + b][col] << (8 * b);
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if ((emask >> e) & 1u) o[e] = __dp4a((int)wpk[4 * half + e][w], (int)word, o[e]);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) x4[e] = o[e];   // |o| <= kMaxWeightSum * 127
       }
-  }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if ((emask >> e) & 1u) {
+#pragma unroll
+          for (int q = 0; q < L; ++q) acc[e][q] += (long long)x4[e] * cl[q];
+        }
+    }
 
-  crt_output<L>(acc, emask, sj, d, ws, nm, i, j, half, col, xch);
+    crt_output<L>(acc, emask, sj, d, ws, nm, i0 + rr, j, half, col, xch);
+  }
+}
+
+// The pipeline of split_crt_plan_kernel: steps (r, l) over `rows` output rows
+// x nm moduli.  issue(r, l, slot) starts the cp.async copies of row r's
+// modulus-l planes into ring slot `slot` (only a commit past the last row),
+// step(l, slot) consumes them, flush(r) finishes row r.  Step s uses slot
+// s mod 4 and the copies run two steps ahead, across row boundaries: the slot
+// refilled at step s was read at step s - 2, which every thread finished
+// before the barrier of step s - 1.
+template <int NM, class Issue, class Step, class Flush>
+__device__ __forceinline__ void crt_pipeline(int rows, int nm_dyn, Issue&& issue, Step&& step, Flush&& flush) {
+  const int nm = NM > 0 ? NM : nm_dyn;
+  int pr = 0, pl = 0, ps = 0;                // the next step to prefetch
+  auto prefetch = [&]() {
+    issue(pr, pl, ps & 3);
+    ++ps;
+    if (++pl == nm) {
+      pl = 0;
+      ++pr;
+    }
+  };
+  prefetch();
+  prefetch();
+  int s = 0;
+  for (int r = 0; r < rows; ++r) {
+    if constexpr (NM > 0) {
+#pragma unroll
+      for (int l = 0; l < NM; ++l) {
+        prefetch();
+        step(l, s & 3);
+        ++s;
+      }
+    } else {
+#pragma unroll 1
+      for (int l = 0; l < nm; ++l) {
+        prefetch();
+        step(l, s & 3);
+        ++s;
+      }
+    }
+    flush(r);
+  }
 }
 
 // CRT of the paper's full plan, for launches whose jobs all use it: the 24
@@ -845,6 +891,123 @@ __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const S
   crt_output<L>(acc, 0xFu, sj, d, ws, nm, i, j, half, col, xch);
 }
 
+// CRT of any plan of at most 24 products (the subalgebra plans, and grouped
+// calls that mix them with the full plan): the layout of split_crt_full_kernel
+// (two threads per element, a 12 KB ring, rows pipelined, the modulus loop
+// unrolled for 13 and 14 moduli), with each output residue formed as the dot
+// product of the plan's int8 weights (packed four to a word, held in
+// registers) with the packed product residues (__dp4a); outputs without a
+// weight skip their sums.
+constexpr int kPlanWords = kFullPlanes / 4;
+
+template <int L, int NM>
+__device__ __forceinline__ void crt_plan_rows(long long (&acc)[4][L], const uint32_t (&wr)[4][kPlanWords],
+                                              uint32_t emask, int np, const unsigned char* base0, int64_t ncols,
+                                              int64_t plane, int cmax, int rows, int nm_dyn, int tid, int col,
+                                              int half, uint8_t (*ring)[kFullPlanes][kCrtCols],
+                                              const SplitJob& sj, const JobDesc& d, const unsigned char* ws, int i0,
+                                              int j, double (*xch)[kCrtCols]) {
+  const int nm = NM > 0 ? NM : nm_dyn;
+  const int nw = (np + 3) >> 2;
+  // thread tid < 8 np prefetches 16-byte chunk tid % 8 of plane tid / 8
+  const int pc = tid >> 3, cc = tid & 7;
+  const bool has = pc < np && cc < cmax;
+  const int64_t src0 = (int64_t)pc * plane + cc * 16;
+  const int dst0 = pc * kCrtCols + cc * 16;
+  const int64_t mstride = (int64_t)np * plane;
+  auto issue = [&](int r, int l, int slot) {
+    if (r < rows && has) cp_async16(&ring[slot][0][0] + dst0, base0 + (int64_t)r * ncols + (int64_t)l * mstride + src0);
+    cp_async_commit();
+  };
+  auto step = [&](int l, int slot) {
+    cp_async_wait2();            // this step's copies have landed
+    __syncthreads();
+    const uint8_t(*sl)[kCrtCols] = ring[slot];
+    int o[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int w = 0; w < kPlanWords; ++w) {
+      if (w < nw) {              // planes past np (stale bytes) meet zero weights
+        const uint32_t word = (uint32_t)sl[4 * w][col] | ((uint32_t)sl[4 * w + 1][col] << 8) |
+                              ((uint32_t)sl[4 * w + 2][col] << 16) | ((uint32_t)sl[4 * w + 3][col] << 24);
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if ((emask >> e) & 1u) o[e] = __dp4a((int)wr[e][w], (int)word, o[e]);
+      }
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if ((emask >> e) & 1u) {
+#pragma unroll
+        for (int q = 0; q < L; ++q) acc[e][q] += (long long)o[e] * c_crt[nm][l][q];
+      }
+  };
+  auto flush = [&](int r) {
+    crt_output<L>(acc, emask, sj, d, ws, nm, i0 + r, j, half, col, xch);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+      for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
+  };
+  crt_pipeline<NM>(rows, nm, issue, step, flush);
+}
+
+template <int L>
+__global__ void __launch_bounds__(2 * kCrtCols, 3) split_crt_plan_kernel(const SplitJob* __restrict__ jobs, int njobs,
+                                                                         const KPlan* __restrict__ plans,
+                                                                         unsigned char* __restrict__ ws) {
+  __shared__ __align__(16) uint8_t ring[4][kFullPlanes][kCrtCols];
+  __shared__ double xch[8][kCrtCols];
+  const int64_t blk = blockIdx.x;
+  const SplitJob& sj = jobs[find_split_job(jobs, njobs, blk, 4)];
+  const JobDesc& d = sj.d;
+  const KPlan& P = plans[d.plan];
+  const int nm = sj.nmod, np = sj.np;
+  const int tid = threadIdx.x;
+  const int col = tid % kCrtCols, half = tid / kCrtCols;   // half 0: M1..M4, half 1: M5..M8
+  // this half's weights, four int8 to a word (w4 rows are 64 bytes, word aligned)
+  uint32_t wr[4][kPlanWords];
+  uint32_t emask = 0;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const uint32_t* row = reinterpret_cast<const uint32_t*>(&P.w4[4 * half + e][0]);
+    uint32_t any = 0;
+#pragma unroll
+    for (int w = 0; w < kPlanWords; ++w) {
+      // bytes of planes >= np are zero in the plan, but mask them all the same
+      const int valid = np - 4 * w;
+      const uint32_t mask = valid >= 4 ? 0xFFFFFFFFu : valid <= 0 ? 0u : (1u << (8 * valid)) - 1u;
+      wr[e][w] = __ldg(row + w) & mask;
+      any |= wr[e][w];
+    }
+    emask |= (any != 0u ? 1u : 0u) << e;
+  }
+  const int64_t local = blk - sj.crt_begin;
+  const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
+  const int i0 = (int)(local / colblocks) * kCrtRows;
+  const int rows = d.m - i0 < kCrtRows ? d.m - i0 : kCrtRows;
+  const int jb = (int)(local % colblocks);
+  const int j = jb * kCrtCols + col;
+  const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
+  const unsigned char* base0 = ws + sj.off_res + (int64_t)i0 * ncols + (int64_t)jb * kCrtCols;
+  const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
+  const int cmax = cavail < kCrtCols / 16 ? (int)cavail : kCrtCols / 16;
+  long long acc[4][L];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
+  const int64_t pl = sj.res_plane;
+  if (L == 4 && nm == 13)
+    crt_plan_rows<L, 13>(acc, wr, emask, np, base0, ncols, pl, cmax, rows, nm, tid, col, half, ring, sj, d, ws, i0, j,
+                         xch);
+  else if (L == 4 && nm == 14)
+    crt_plan_rows<L, 14>(acc, wr, emask, np, base0, ncols, pl, cmax, rows, nm, tid, col, half, ring, sj, d, ws, i0, j,
+                         xch);
+  else
+    crt_plan_rows<L, 0>(acc, wr, emask, np, base0, ncols, pl, cmax, rows, nm, tid, col, half, ring, sj, d, ws, i0, j,
+                        xch);
+}
+
 // ------------------------------------------------------------------ launchers
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const int32_t* crt_d, const uint32_t* crt_P,
                                    const uint32_t* crt_off) {
@@ -916,13 +1079,16 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
 }
 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod, bool all_full) {
+                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full) {
   if (units <= 0) return cudaSuccess;
   // 4 limbs hold sum_l r_l c_l < nmod * 255 * P below 2^128 (nmod <= 14)
   const unsigned grid = (unsigned)units, block = 2 * kCrtCols;
   if (all_full) {
     if (max_nmod <= 14) split_crt_full_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
     else split_crt_full_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+  } else if (max_np <= kFullPlanes) {
+    if (max_nmod <= 14) split_crt_plan_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
+    else split_crt_plan_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
   } else {
     if (max_nmod <= 14) split_crt_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
     else split_crt_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);

@@ -1,6 +1,7 @@
 """Host-side checks (no GPU): the C-ABI library, the product plans, split-mode parameters."""
 import itertools
 import math
+import random
 import os
 import re
 
@@ -161,7 +162,8 @@ def test_split_crt_margin_every_k():
 
 def test_plan_weight_sums_within_the_crt_bound():
     """Every plan's output weights satisfy sum_p |4 w| <= 36, the bound behind
-    the CRT's integer residue step (|4Q| <= 36 * 127 with centred residues)."""
+    the CRT's sums (|4Q| <= 36 * 127 with centred residues), which sizes their
+    offset N P and the quotient estimate."""
     flags = [bi.REAL, bi.COMPLEX, bi.TRS, bi.TRA, bi.BQ, 0x03, 0x55, 0x81]
     worst = 0.0
     for algo in ("bilinear", "standard"):
@@ -317,3 +319,65 @@ def test_c_client_compiles_against_the_header(tmp_path):
     """The header is valid C11 and a C program links against libhmat.so (run on the GPU in test_gpu_c_abi)."""
     hm.lib()
     assert os.path.exists(_build_c_client(tmp_path))
+
+
+def test_crt_signed_digit_quotient_is_exact():
+    """The CRT kernels' arithmetic, restated on the host: x_l (any integer in
+    [-36 * 127, 36 * 127] congruent to 4 X modulo p_l) times the signed 32-bit
+    digits of d_l = (P/p_l) ((P/p_l)^-1 4^-1 mod p_l), summed into L 64-bit limb
+    sums started at N P (N = nmod * 36 * 127); signed carries; the quotient as
+    the float32 round of the leading limbs (from the limb below P's top one)
+    times fl(2^(32 pb) / P); X = S - q P.  Every modulus count the library uses,
+    both limb counts that can run it, outputs at the margin |X| = P / 2^1.25 and
+    the extreme representatives of every x_l give back X exactly."""
+    W = 36 * 127
+    lists = [hm.split_info(k, tol)[0] for k in (1, 64, 8192, 127 * 1024)
+             for tol in (1e-3, 1e-6, 1e-9, 1e-12, 1e-14)]
+    longest = max(lists, key=len)
+    assert all(lst == longest[:len(lst)] for lst in lists)
+    rng = random.Random(11)
+
+    def digits(v, L):
+        out, c = [], 0
+        for q in range(L):
+            w = ((v >> (32 * q)) & 0xFFFFFFFF) + c
+            c = 1 if w >= 2 ** 31 else 0
+            out.append(w - (c << 32))
+        assert c == 0
+        return out
+
+    for nm in range(1, len(longest) + 1):
+        mods = longest[:nm]
+        P = math.prod(mods)
+        top = (P.bit_length() - 1) // 32
+        pb = max(top - 1, 0)
+        for L in ((4, 5) if nm <= 14 else (5,)):
+            f = 0.0
+            for q in range(L - 1, pb - 1, -1):
+                f = f * 2.0 ** 32 + float((P >> (32 * q)) & 0xFFFFFFFF)
+            pinv = np.float32(1.0 / f)
+            d = [digits((P // p) * (pow((P // p) % p, -1, p) * pow(4, -1, p) % p), L) for p in mods]
+            off = nm * W * P
+            lim = int(P / 2 ** 1.25)
+            for trial in range(300):
+                X = rng.choice([lim, -lim, rng.randrange(-lim, lim + 1), rng.randrange(-min(lim, 99), min(lim, 99) + 1)])
+                acc = [(off >> (32 * q)) & 0xFFFFFFFF for q in range(L)]
+                for p, dl in zip(mods, d):
+                    r = (4 * X) % p
+                    lo, hi = -W + (r + W) % p, W - (W - r) % p
+                    xl = rng.choice([lo, hi, lo + p * rng.randrange(0, (hi - lo) // p + 1)])
+                    for q in range(L):
+                        acc[q] += xl * dl[q]
+                x = [0] * L
+                t = acc[0]
+                x[0] = t & 0xFFFFFFFF
+                for q in range(1, L):
+                    t = acc[q] + (t >> 32)
+                    x[q] = t & 0xFFFFFFFF
+                sf = np.float32(np.float32(t >> 32) * np.float32(2.0 ** 32) + np.float32(x[L - 1]))
+                for q in range(L - 2, pb - 1, -1):
+                    sf = np.float32(sf * np.float32(2.0 ** 32) + np.float32(x[q]))
+                qq = int(np.rint(np.float32(sf * pinv)))
+                S = (t << (32 * (L - 1))) + sum(x[q] << (32 * q) for q in range(L - 1))
+                assert 0 < S < 2 * nm * W * P
+                assert S - qq * P == X, (nm, L, X)
