@@ -224,10 +224,20 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // (Three 16-bit limbs with one reduction would take two fewer instructions per
 // residue but a third staged float per value; measured slower: spills, fewer
 // resident blocks.)
+// The encoder works on two k positions at once with paired FP32 instructions
+// (__ffma2_rn / __fadd2_rn), each lane rounding exactly as the scalar form.
+__device__ __forceinline__ float2 f2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ float2 fmod_c2(float2 v, const ModConst& mc) {
+  const float2 q = __fadd2_rn(__ffma2_rn(v, f2(mc.inv), f2(12582912.0f)), f2(-12582912.0f));
+  return __ffma2_rn(q, f2(-mc.pf), v);
+}
 template <int LIMBS>
-__device__ __forceinline__ float residue_of(const float* x, const ModConst& mc) {
-  if (LIMBS == 2) return fmod_c(fmaf(fmod_c(x[1], mc), mc.c23, x[0]), mc);
-  return fmod_c(fmaf(fmod_c(x[2], mc), mc.c36, fmaf(fmod_c(x[1], mc), mc.c18, fmod_c(x[0], mc))), mc);
+__device__ __forceinline__ float2 residue_of2(const float* x, const float* y, const ModConst& mc) {
+  auto lane2 = [&](int i) { return make_float2(x[i], y[i]); };
+  if (LIMBS == 2) return fmod_c2(__ffma2_rn(fmod_c2(lane2(1), mc), f2(mc.c23), lane2(0)), mc);
+  return fmod_c2(__ffma2_rn(fmod_c2(lane2(2), mc), f2(mc.c36),
+                            __ffma2_rn(fmod_c2(lane2(1), mc), f2(mc.c18), fmod_c2(lane2(0), mc))),
+                 mc);
 }
 
 template <int LIMBS>
@@ -340,46 +350,55 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
     // reduced: re and im are residues already (the single-coefficient groups);
     // otherwise (Hadamard sums) they are reduced first.  Re + Im is reduced
     // from the two residues.
-    auto put = [&](int f, const float (&v)[4], int l) {
+    // four k positions as two lane pairs
+    auto put = [&](int f, const float2 (&v)[2], int l) {
       if (f < 0) return;
-      const uint2 pkd = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
-                                   __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
+      const uint2 pkd = make_uint2(__byte_perm(__float_as_uint(v[0].x), __float_as_uint(v[0].y), 0x7632),
+                                   __byte_perm(__float_as_uint(v[1].x), __float_as_uint(v[1].y), 0x7632));
       *reinterpret_cast<uint2*>(enc + (uint64_t)(uint32_t)(l * nf + f) * plane_bytes) = pkd;
     };
-    auto emit = [&](int gi, const float (&re)[4], const float (&im)[4], int l, const ModConst& mc, bool reduced) {
-      float v0[4], v1[4], v2[4];
+    auto emit = [&](int gi, const float2 (&re)[2], const float2 (&im)[2], int l, const ModConst& mc, bool reduced) {
+      float2 v0[2], v1[2], v2[2];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v0[q] = reduced ? re[q] : fmod_c(re[q], mc);
+      for (int h = 0; h < 2; ++h) v0[h] = reduced ? re[h] : fmod_c2(re[h], mc);
       put(s_slot[gi][0], v0, l);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v1[q] = reduced ? im[q] : fmod_c(im[q], mc);
+      for (int h = 0; h < 2; ++h) v1[h] = reduced ? im[h] : fmod_c2(im[h], mc);
       put(s_slot[gi][1], v1, l);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) v2[q] = fmod_c(v0[q] + v1[q], mc);
+      for (int h = 0; h < 2; ++h) v2[h] = fmod_c2(__fadd2_rn(v0[h], v1[h]), mc);
       put(s_slot[gi][2], v2, l);
     };
     for (int l = 0; l < sj.nmod; ++l) {
       const ModConst& mc = c_mod[l];
-      float xr[4][4], xi[4][4];      // [component][k]
+      float2 xr[4][2], xi[4][2];     // [component][k pair]
 #pragma unroll
       for (int e = 0; e < 4; ++e)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          xr[e][q] = residue_of<LIMBS>(xs[e][k4 * 4 + q][rr], mc);
-          xi[e][q] = residue_of<LIMBS>(xs[e + 4][k4 * 4 + q][rr], mc);
+        for (int h = 0; h < 2; ++h) {
+          const int k = k4 * 4 + 2 * h;
+          xr[e][h] = residue_of2<LIMBS>(xs[e][k][rr], xs[e][k + 1][rr], mc);
+          xi[e][h] = residue_of2<LIMBS>(xs[e + 4][k][rr], xs[e + 4][k + 1][rr], mc);
         }
       const int pk[4] = {pick0, pick1, pick2, pick3};
 #pragma unroll
       for (int g = 0; g < 4; ++g) emit(g, xr[pk[g]], xi[pk[g]], l, mc, true);
       // Hadamard rows by two butterfly stages, in place
+      const float2 m1 = f2(-1.0f);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float sr01 = xr[0][q] + xr[1][q], dr01 = xr[0][q] - xr[1][q];
-        const float sr23 = xr[2][q] + xr[3][q], dr23 = xr[2][q] - xr[3][q];
-        xr[0][q] = sr01 + sr23; xr[1][q] = sr01 - sr23; xr[2][q] = dr01 + dr23; xr[3][q] = dr01 - dr23;
-        const float si01 = xi[0][q] + xi[1][q], di01 = xi[0][q] - xi[1][q];
-        const float si23 = xi[2][q] + xi[3][q], di23 = xi[2][q] - xi[3][q];
-        xi[0][q] = si01 + si23; xi[1][q] = si01 - si23; xi[2][q] = di01 + di23; xi[3][q] = di01 - di23;
+      for (int h = 0; h < 2; ++h) {
+        const float2 sr01 = __fadd2_rn(xr[0][h], xr[1][h]), dr01 = __ffma2_rn(xr[1][h], m1, xr[0][h]);
+        const float2 sr23 = __fadd2_rn(xr[2][h], xr[3][h]), dr23 = __ffma2_rn(xr[3][h], m1, xr[2][h]);
+        xr[0][h] = __fadd2_rn(sr01, sr23);
+        xr[1][h] = __ffma2_rn(sr23, m1, sr01);
+        xr[2][h] = __fadd2_rn(dr01, dr23);
+        xr[3][h] = __ffma2_rn(dr23, m1, dr01);
+        const float2 si01 = __fadd2_rn(xi[0][h], xi[1][h]), di01 = __ffma2_rn(xi[1][h], m1, xi[0][h]);
+        const float2 si23 = __fadd2_rn(xi[2][h], xi[3][h]), di23 = __ffma2_rn(xi[3][h], m1, xi[2][h]);
+        xi[0][h] = __fadd2_rn(si01, si23);
+        xi[1][h] = __ffma2_rn(si23, m1, si01);
+        xi[2][h] = __fadd2_rn(di01, di23);
+        xi[3][h] = __ffma2_rn(di23, m1, di01);
       }
 #pragma unroll
       for (int g = 0; g < 4; ++g) emit(4 + g, xr[g], xi[g], l, mc, false);
@@ -389,34 +408,37 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
 
   for (int l = 0; l < sj.nmod; ++l) {
     const ModConst& mc = c_mod[l];
-    float rc[8][4];
+    float2 rc[8][2];               // [component][k pair]
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        rc[c][q] = ((flags >> c) & 1u) ? residue_of<LIMBS>(xs[c][k4 * 4 + q][rr], mc) : 0.f;
+      for (int h = 0; h < 2; ++h) {
+        const int k = k4 * 4 + 2 * h;
+        rc[c][h] = ((flags >> c) & 1u) ? residue_of2<LIMBS>(xs[c][k][rr], xs[c][k + 1][rr], mc) : f2(0.f);
+      }
     }
     for (int gi = 0; gi < ng; ++gi) {
-      float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+      float2 re[2] = {f2(0.f), f2(0.f)}, im[2] = {f2(0.f), f2(0.f)};
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const float a = s_coef[gi][e], b = s_coef[gi][e + 4];   // +-1 or 0: exact products
+        const float2 a = f2(s_coef[gi][e]), b = f2(s_coef[gi][e + 4]);   // +-1 or 0: exact products
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          re[q] = fmaf(a, rc[e][q], re[q]);
-          im[q] = fmaf(b, rc[e + 4][q], im[q]);
+        for (int h = 0; h < 2; ++h) {
+          re[h] = __ffma2_rn(a, rc[e][h], re[h]);
+          im[h] = __ffma2_rn(b, rc[e + 4][h], im[h]);
         }
       }
 #pragma unroll
       for (int part = 0; part < 3; ++part) {
         const int f = s_slot[gi][part];
         if (f < 0) continue;
-        float v[4];
+        float2 v[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = fmod_c(part == 0 ? re[q] : (part == 1 ? im[q] : re[q] + im[q]), mc);
+        for (int h = 0; h < 2; ++h)
+          v[h] = fmod_c2(part == 0 ? re[h] : (part == 1 ? im[h] : __fadd2_rn(re[h], im[h])), mc);
         // |v| <= 128 is exact in BF16, whose bits are the upper half of the float's
-        const uint2 pk = make_uint2(__byte_perm(__float_as_uint(v[0]), __float_as_uint(v[1]), 0x7632),
-                                    __byte_perm(__float_as_uint(v[2]), __float_as_uint(v[3]), 0x7632));
+        const uint2 pk = make_uint2(__byte_perm(__float_as_uint(v[0].x), __float_as_uint(v[0].y), 0x7632),
+                                    __byte_perm(__float_as_uint(v[1].x), __float_as_uint(v[1].y), 0x7632));
         *reinterpret_cast<uint2*>(enc + (uint64_t)(uint32_t)(l * nf + f) * plane_bytes) = pk;
       }
     }
