@@ -47,7 +47,9 @@ def parse(argv=None):
     ap.add_argument("--n", type=int, default=8192, help="output columns (and m, k unless given)")
     ap.add_argument("--m", type=int, default=None, help="output rows (default: n)")
     ap.add_argument("--k", type=int, default=None, help="inner dimension (default: n)")
-    ap.add_argument("--mode", choices=["split", "fp64"], default="split")
+    ap.add_argument("--mode", choices=["split", "fp64", "mixed"], default="split",
+                    help="mixed (grouped workload only): every fourth problem in FP64 mode, the rest in split "
+                         "mode, in one hmat_bq_gemm_grouped_modes call")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--sample-rows", type=int, default=8)
     ap.add_argument("--no-fp64-compare", action="store_true")
@@ -76,7 +78,10 @@ def parse(argv=None):
     ap.add_argument("--algo", choices=["bilinear", "standard", "isomorph"], default="bilinear",
                     help="product algorithm: the bilinear scheme, component-wise (HMAT-standard) "
                          "or the complex isomorph (CMAT)")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.mode == "mixed" and args.workload != "grouped":
+        ap.error("--mode mixed applies to the grouped workload only")
+    return args
 
 
 def dims(args):
@@ -624,12 +629,21 @@ def grouped(args, rank, world, local):
         fp = autotune.load_fp64(args.tile_table)
         if fp is not None:
             h.set_fp64_splitk_table(fp)
-    ws_bytes = hm.hmat_workspace_size(h, descs, args.mode, args.tol)
+    modes = ["fp64" if i % 4 == 3 else "split" for i in range(len(descs))] if args.mode == "mixed" else None
+    if modes:
+        ws_bytes = hm.hmat_workspace_size_modes(h, descs, modes, args.tol)
+    else:
+        ws_bytes = hm.hmat_workspace_size(h, descs, args.mode, args.tol)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        hm.hmat_bq_gemm_grouped(h, descs, args.mode, args.tol, workspace=ws, stream=stream, use_graph=args.graph)
+        if modes:
+            hm.hmat_bq_gemm_grouped_modes(h, descs, modes, args.tol, workspace=ws, stream=stream,
+                                          use_graph=args.graph)
+        else:
+            hm.hmat_bq_gemm_grouped(h, descs, args.mode, args.tol, workspace=ws, stream=stream,
+                                    use_graph=args.graph)
 
     for _ in range(args.warmup):
         step()
@@ -648,16 +662,20 @@ def grouped(args, rank, world, local):
     # per-stage kernel times (one extra eager step with event brackets)
     h.set_profiling(True)
     h.reset_profile()
-    hm.hmat_bq_gemm_grouped(h, descs, args.mode, args.tol, workspace=ws, stream=stream, use_graph=False)
+    if modes:
+        hm.hmat_bq_gemm_grouped_modes(h, descs, modes, args.tol, workspace=ws, stream=stream, use_graph=False)
+    else:
+        hm.hmat_bq_gemm_grouped(h, descs, args.mode, args.tol, workspace=ws, stream=stream, use_graph=False)
     torch.cuda.synchronize()
     stages = {k: {"launches": v[0], "ms": v[1]} for k, v in ((k, h.profile(k)) for k in hm.KERNEL_IDS) if v[0]}
     h.set_profiling(False)
     flops64 = sum(64 * 2.0 * m * n * k for m, n, k in shapes)
     value = world * flops64 / (ms * 1e-3) / 1e12
     launches_per_step = sum(v["launches"] for v in stages.values())
-    if args.mode == "split":
+    split_shapes = [sh for i, sh in enumerate(shapes) if modes is None or modes[i] == "split"]
+    if args.mode in ("split", "mixed"):
         P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ)[0]
-        gemm_flops = sum(len(hm.split_info(k, args.tol)[0]) * P * 2.0 * m * n * k for m, n, k in shapes)
+        gemm_flops = sum(len(hm.split_info(k, args.tol)[0]) * P * 2.0 * m * n * k for m, n, k in split_shapes)
         gst = stages.get("split_residue_gemm", {"launches": 1, "ms": float("nan")})
         ach = gemm_flops / (gst["ms"] / gst["launches"] * 1e-3) / 1e12
         peaks, src = measured_peaks()
@@ -688,8 +706,8 @@ def grouped(args, rank, world, local):
         cpu_base = {"value": f_or / t_or / 1e12, "unit": "TFLOP/s", "cores": oracle.max_threads(), "kind": "oracle",
                     "sample": f"the 16 sampled problems of the batch (m n k <= 2^25), {t_or:.1f} s"}
         roof_hbm = None
-        if args.mode == "split":
-            stages = stage_rates(stages, split_stage_work(hm, shapes, args.tol))
+        if args.mode in ("split", "mixed"):
+            stages = stage_rates(stages, split_stage_work(hm, split_shapes, args.tol))
             g = stages.get("split_residue_gemm", {})
             if g.get("GB_per_s"):
                 hbm = measured_peaks()[0].get("hbm_gbs")
@@ -701,7 +719,7 @@ def grouped(args, rank, world, local):
         line = {"metric": "grouped biquaternion GEMM TFLOP/s (64-GEMM-equiv.)", "value": value, "unit": "TFLOP/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "bf16" if args.mode == "split" else "f64", "data": "synthetic",
+                "dtype": {"split": "bf16", "fp64": "f64", "mixed": "bf16+f64"}[args.mode], "data": "synthetic",
                 "config": {"workload": f"{len(shapes)} products, m,n,k log-uniform in [32,1024] (seed 104), "
                                        f"iid U[-1,1], full biquaternions", "mode": args.mode, "graph": args.graph,
                            "tol": args.tol, "total_flops_64equiv": flops64,

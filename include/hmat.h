@@ -224,6 +224,35 @@ hmat_status hmat_bq_gemm_grouped(hmat_handle handle, int32_t count,
                                  size_t workspace_bytes, void *stream,
                                  int32_t use_graph);
 
+/* hmat_bq_gemm_grouped with a mode per product: modes is a HOST array of
+ * `count` hmat_mode values, modes[i] for descs[i].  The split products run
+ * through the split stages (one grouped launch per stage) and the FP64
+ * products through the FP64 kernel (one grouped launch), on `stream` in that
+ * order; each product's result is the one its mode gives on its own (FP64
+ * products may split their inner dimension differently from a call holding
+ * only them: the built-in split-k rule counts the call's FP64 tiles).
+ * workspace: at least hmat_workspace_size_modes() bytes.  use_graph as for
+ * hmat_bq_gemm_grouped (the per-product modes are part of the graph's key).
+ * Errors as hmat_bq_gemm_grouped; a mode other than HMAT_MODE_FP64 or
+ * HMAT_MODE_SPLIT is INVALID_VALUE (its index in hmat_last_bad_index()).
+ * The paper runs one mode per call; mixing them in one launch sequence is
+ * this library's. */
+HMAT_API
+hmat_status hmat_bq_gemm_grouped_modes(hmat_handle handle, int32_t count,
+                                       const hmat_gemm_desc *descs,
+                                       const int32_t *modes, double tol,
+                                       void *workspace, size_t workspace_bytes,
+                                       void *stream, int32_t use_graph);
+
+/* Workspace bytes of hmat_bq_gemm_grouped_modes for these products and modes
+ * (host arrays of `count`; only op, flags, m, n, k of the descriptors are
+ * read).  Errors: NOT_INITIALIZED, INVALID_VALUE. */
+HMAT_API
+hmat_status hmat_workspace_size_modes(hmat_handle handle, int32_t count,
+                                      const hmat_gemm_desc *descs,
+                                      const int32_t *modes, double tol,
+                                      size_t *bytes);
+
 /* Split-mode product that allocates nothing: C <- alpha op(A) op(B) + beta C
  * exactly as hmat_bq_gemm with mode HMAT_MODE_SPLIT (the same kernels, the
  * same result bits), but its workspace is a fixed array compiled into this

@@ -78,6 +78,10 @@ SIGNATURES = {
                                     _i32, _dbl, _ptr, _sz, _ptr]),
     "hmat_bq_gemm_grouped": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc), _i32, _dbl, _ptr, _sz,
                                             _ptr, _i32]),
+    "hmat_bq_gemm_grouped_modes": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc),
+                                                  ctypes.POINTER(_i32), _dbl, _ptr, _sz, _ptr, _i32]),
+    "hmat_workspace_size_modes": (ctypes.c_int, [_ptr, _i32, ctypes.POINTER(hmat_gemm_desc), ctypes.POINTER(_i32),
+                                                 _dbl, ctypes.POINTER(_sz)]),
     "hmat_bq_gemm_split_noalloc": (ctypes.c_int, [_ptr, _i32, _i32, _u32, _u32, _i64, _i64, _i64, _dbl, _dbl,
                                                   _ptr, _i64, _i64, _ptr, _i64, _i64, _dbl, _dbl, _ptr, _i64, _i64,
                                                   _dbl, _ptr]),
@@ -362,6 +366,38 @@ def hmat_bq_gemm_grouped(handle: Handle, descs, mode="fp64", tol=0.0, workspace=
         raise HmatError(st, f"hmat_bq_gemm_grouped (descriptor {bad})")
 
 
+def hmat_workspace_size_modes(handle: Handle, descs, modes, tol=0.0) -> int:
+    """Workspace bytes of hmat_bq_gemm_grouped_modes (one mode per descriptor)."""
+    if len(modes) != len(descs):
+        raise ValueError("one mode per descriptor")
+    arr = (hmat_gemm_desc * len(descs))(*descs)
+    marr = (_i32 * len(modes))(*[_mode(m) for m in modes])
+    out = _sz()
+    _check(lib().hmat_workspace_size_modes(handle.value, len(descs), arr, marr, float(tol), ctypes.byref(out)),
+           "hmat_workspace_size_modes")
+    return out.value
+
+
+def hmat_bq_gemm_grouped_modes(handle: Handle, descs, modes, tol=0.0, workspace=None, stream=None,
+                               use_graph=False, device=None):
+    """Grouped products with a mode per product (hmat_bq_gemm_grouped_modes)."""
+    if len(modes) != len(descs):
+        raise ValueError("one mode per descriptor")
+    arr = (hmat_gemm_desc * len(descs))(*descs)
+    marr = (_i32 * len(modes))(*[_mode(m) for m in modes])
+    ws = workspace
+    if ws is None:
+        import torch
+        ws, _ = _workspace(hmat_workspace_size_modes(handle, descs, modes, tol), device or torch.device("cuda"))
+    ws_ptr = ws.data_ptr() if ws is not None else None
+    ws_bytes = ws.numel() if ws is not None else 0
+    st = lib().hmat_bq_gemm_grouped_modes(handle.value, len(descs), arr, marr, float(tol), ws_ptr, ws_bytes,
+                                          _stream_ptr(stream), 1 if use_graph else 0)
+    if st != 0:
+        bad = lib().hmat_last_bad_index(handle.value)
+        raise HmatError(st, f"hmat_bq_gemm_grouped_modes (descriptor {bad})")
+
+
 def hmat_bq_gemm_split_noalloc(handle: Handle, A, B, C, opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ,
                                alpha=1.0, beta=0.0, tol=0.0, stream=None):
     """Split-mode product whose workspace is the library's fixed scratch array
@@ -575,6 +611,7 @@ def hmat_bq_hadamard_block(handle: Handle, X, alpha, flags=0xCC, Z=None, offdiag
 
 
 __all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gemm_grouped", "hmat_workspace_size",
+           "hmat_bq_gemm_grouped_modes", "hmat_workspace_size_modes",
            "hmat_bq_gemm_split_noalloc", "hmat_bq_gemm_streamed", "streamed_plan", "streamed_traffic", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
            "hmat_complex_to_bq", "hmat_bq_hermiticity", "hmat_bq_hadamard_block",
            "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",

@@ -111,14 +111,20 @@ struct SplitReuse {
 };
 
 // Validate, plan and launch `count` products on `stream_ptr` (hmat_bq_gemm and
-// hmat_bq_gemm_grouped without a graph).
+// hmat_bq_gemm_grouped without a graph).  modes: null (every product in
+// `mode`) or one hmat_mode per product.
 hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse = SplitReuse{});
+                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse = SplitReuse{},
+                const int32_t* modes = nullptr);
+hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
+                      void* workspace, size_t ws_bytes, void* stream_ptr, const int32_t* modes = nullptr);
 
 // Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule);
-// with a handle, FP64 mode includes the split-k partials the handle would use.
+// with a handle, the FP64 products include the split-k partials the handle would use.
+// modes: as for run.
 hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
-                            double tol, size_t* bytes, const hmat_context* h = nullptr);
+                            double tol, size_t* bytes, const hmat_context* h = nullptr,
+                            const int32_t* modes = nullptr);
 
 // One stderr line per product call when HMAT_LOG is set.
 void log_call(const hmat_context* h, const char* fn, const hmat_gemm_desc& d, int32_t mode, hmat_status st);

@@ -411,9 +411,12 @@ void fp64_layout(hmat_context* h, Prepared* out, unsigned char* ws, size_t ws_by
 }
 
 hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                    void* workspace, size_t ws_bytes, cudaStream_t stream, Prepared* out, bool allow_splitk = true) {
+                    void* workspace, size_t ws_bytes, cudaStream_t stream, Prepared* out, bool allow_splitk = true,
+                    const int32_t* modes = nullptr) {
   if (count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
-  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
+  if (!modes && mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
+  for (int32_t i = 0; modes && i < count; ++i)
+    if (modes[i] != HMAT_MODE_FP64 && modes[i] != HMAT_MODE_SPLIT) { h->last_bad = i; return HMAT_STATUS_INVALID_VALUE; }
   if (tol < 0 || !std::isfinite(tol)) return HMAT_STATUS_INVALID_VALUE;
   int cur = -1;
   if (cudaGetDevice(&cur) != cudaSuccess || cur != h->device) return HMAT_STATUS_INVALID_VALUE;
@@ -462,7 +465,7 @@ hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs,
     // k == 0 or an all-absent operand: the product vanishes; the FP64 kernel applies beta.
     const int np = h->h_plans[slot].np;
     const bool trivial = (j.k == 0) || np == 0;
-    if (mode == HMAT_MODE_SPLIT && !trivial) {
+    if ((modes ? modes[i] : mode) == HMAT_MODE_SPLIT && !trivial) {
       split_jobs.push_back(j);
     } else if (np <= fp64_max_products()) {
       add_fp64_job(out, j, 0);
@@ -529,14 +532,14 @@ hmat_status launch_iso_out(hmat_context* h, const Prepared& pr, cudaStream_t str
 }
 
 hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse) {
+                void* workspace, size_t ws_bytes, void* stream_ptr, SplitReuse reuse, const int32_t* modes) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
   std::lock_guard<std::mutex> lock(h->mu);
   h->last_bad = -1;
   if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
   Prepared pr;
-  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr, !reuse.fp64_whole_k);
+  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr, !reuse.fp64_whole_k, modes);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (pr.has_split && pr.sp.jobs.size() == 1 && h->algo != HMAT_ALGO_ISOMORPH) {
     pr.sp.reuse_a = reuse.a;
@@ -567,17 +570,18 @@ hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int
 
 // Grouped call replayed from a CUDA graph keyed by the exact call arguments.
 hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
-                      void* workspace, size_t ws_bytes, void* stream_ptr) {
+                      void* workspace, size_t ws_bytes, void* stream_ptr, const int32_t* modes) {
   if (!h) return HMAT_STATUS_NOT_INITIALIZED;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_ptr);
   if (stream == nullptr)   // the legacy default stream cannot be captured: run eagerly
-    return run(h, count, descs, mode, tol, workspace, ws_bytes, stream_ptr);
+    return run(h, count, descs, mode, tol, workspace, ws_bytes, stream_ptr, SplitReuse{}, modes);
   std::lock_guard<std::mutex> lock(h->mu);
   h->last_bad = -1;
-  // key: descriptors + mode + tol + workspace + algorithm + tile table
+  // key: descriptors + mode (or the per-product modes) + tol + workspace + algorithm + tile table
   const size_t tbl = sizeof(h->split.tile_table);
+  const size_t nmodes = modes ? (size_t)std::max(count, 0) : 0;
   std::vector<unsigned char> key(sizeof(int32_t) * 3 + sizeof(double) + sizeof(void*) + sizeof(size_t) + 1 + tbl +
-                                 (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc));
+                                 (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc) + nmodes * sizeof(int32_t));
   {
     unsigned char* k = key.data();
     std::memcpy(k, &count, 4); k += 4;
@@ -589,13 +593,15 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
     *k++ = h->split.has_table ? 1 : 0;
     std::memcpy(k, h->split.tile_table, tbl); k += tbl;
     if (count > 0 && descs) std::memcpy(k, descs, (size_t)count * sizeof(hmat_gemm_desc));
+    k += (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc);
+    if (nmodes) std::memcpy(k, modes, nmodes * sizeof(int32_t));
   }
   for (auto& g : h->graphs) {
     if (g.key == key) return cuda_status(cudaGraphLaunch(g.exec, stream));
   }
   if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
   Prepared pr;
-  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr);
+  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr, true, modes);
   if (st != HMAT_STATUS_SUCCESS) return st;
   hmat_context::GraphEntry ge;
   ge.key = key;
@@ -825,16 +831,23 @@ namespace hmat {
 
 // Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule).
 hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
-                            double tol, size_t* bytes, const hmat_context* h) {
+                            double tol, size_t* bytes, const hmat_context* h, const int32_t* modes) {
   if (!bytes || count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
-  if (mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
+  if (!modes && mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
+  for (int32_t i = 0; modes && i < count; ++i)
+    if (modes[i] != HMAT_MODE_FP64 && modes[i] != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
   *bytes = 0;
   int64_t iso = 0;
   std::vector<SplitShape> shapes;
+  // the products that run in the FP64 kernel, as prepare routes them: FP64 mode,
+  // or split mode with k = 0 or an empty plan
+  std::vector<char> fp64(count > 0 ? count : 0, 0);
   for (int32_t i = 0; i < count; ++i) {
     const hmat_gemm_desc& d = descs[i];
     if (d.m < 0 || d.n < 0 || d.k < 0 || d.flagsA > 0xFFu || d.flagsB > 0xFFu) return HMAT_STATUS_INVALID_VALUE;
-    if (d.m == 0 || d.n == 0 || d.k == 0) continue;
+    if (d.m == 0 || d.n == 0) continue;
+    if (d.k == 0 || (modes ? modes[i] : mode) == HMAT_MODE_FP64) fp64[i] = 1;
+    if (d.k == 0) continue;
     int64_t m = d.m, n = d.n, k = d.k;
     unsigned fa = d.flagsA, fb = d.flagsB;
     if (algo == HMAT_ALGO_ISOMORPH) {
@@ -842,11 +855,14 @@ hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const 
       m *= 2; n *= 2; k *= 2;
       fa = HMAT_COMPLEX; fb = HMAT_COMPLEX;
     }
-    if (mode == HMAT_MODE_FP64) continue;
+    if (fp64[i]) continue;
     KPlan p;
     if (!build_plan(fa, fb, &p, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
       return HMAT_STATUS_INTERNAL;
-    if (p.np == 0) continue;
+    if (p.np == 0) {
+      fp64[i] = 1;
+      continue;
+    }
     shapes.push_back({m, n, k, p.np, p.nlf, p.nrf, p.bilinear_full});
   }
   size_t split = 0;
@@ -855,22 +871,23 @@ hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const 
     if (st != HMAT_STATUS_SUCCESS) return st;
   }
   *bytes = (size_t)align_up256(iso) + split;
-  if (h && mode == HMAT_MODE_FP64 && algo != HMAT_ALGO_STANDARD) {
-    // the split-k partials of a call whose products all run in one FP64 pass
-    // (every bilinear plan has at most 24 products), as fp64_layout places them
+  if (h && algo != HMAT_ALGO_STANDARD && (modes || mode == HMAT_MODE_FP64)) {
+    // the split-k partials of the FP64 products when they all run in one FP64
+    // pass (every bilinear plan has at most 24 products), as fp64_layout places
+    // them (a split-mode call leaves its few trivial products unsplit)
     const int tm = fp64_tile_m(), tn = fp64_tile_n(), tk = fp64_tile_k();
+    const int64_t sc = algo == HMAT_ALGO_ISOMORPH ? 2 : 1;
     int64_t tiles = 0;
     for (int32_t i = 0; i < count; ++i) {
-      const int64_t m = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].m : descs[i].m;
-      const int64_t n = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].n : descs[i].n;
-      if (m > 0 && n > 0) tiles += ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
+      if (!fp64[i]) continue;
+      const int64_t m = sc * descs[i].m, n = sc * descs[i].n;
+      tiles += ((m + tm - 1) / tm) * ((n + tn - 1) / tn);
     }
     int64_t off = (int64_t)align_up256((int64_t)*bytes);
     for (int32_t i = 0; i < count; ++i) {
-      const int64_t m = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].m : descs[i].m;
-      const int64_t n = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].n : descs[i].n;
-      const int64_t k = algo == HMAT_ALGO_ISOMORPH ? 2 * descs[i].k : descs[i].k;
-      if (m <= 0 || n <= 0 || k <= 0) continue;
+      if (!fp64[i]) continue;
+      const int64_t m = sc * descs[i].m, n = sc * descs[i].n, k = sc * descs[i].k;
+      if (k <= 0) continue;
       const int s = fp64_kslices(h, tiles, k);
       if (s <= 1) continue;
       const int64_t chunk = ((k + s - 1) / s + tk - 1) / tk * tk;
@@ -917,6 +934,29 @@ hmat_status hmat_bq_gemm_grouped(hmat_handle h, int32_t count, const hmat_gemm_d
   if (h && h->log) {
     for (int32_t i = 0; i < count && descs; ++i) log_call(h, use_graph ? "hmat_bq_gemm_grouped[graph]" :
                                                                "hmat_bq_gemm_grouped", descs[i], mode, st);
+  }
+  return st;
+}
+
+hmat_status hmat_workspace_size_modes(hmat_handle h, int32_t count, const hmat_gemm_desc* descs, const int32_t* modes,
+                                      double tol, size_t* bytes) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (count > 0 && !modes) return HMAT_STATUS_INVALID_VALUE;
+  return workspace_bytes(h->algo, split_table(h), count, descs, HMAT_MODE_FP64, tol, bytes, h, modes);
+}
+
+hmat_status hmat_bq_gemm_grouped_modes(hmat_handle h, int32_t count, const hmat_gemm_desc* descs,
+                                       const int32_t* modes, double tol, void* workspace, size_t workspace_bytes,
+                                       void* stream, int32_t use_graph) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (count > 0 && !modes) return HMAT_STATUS_INVALID_VALUE;
+  const hmat_status st =
+      use_graph ? run_graph(h, count, descs, HMAT_MODE_FP64, tol, workspace, workspace_bytes, stream, modes)
+                : run(h, count, descs, HMAT_MODE_FP64, tol, workspace, workspace_bytes, stream, SplitReuse{}, modes);
+  if (h->log) {
+    for (int32_t i = 0; i < count && descs; ++i)
+      log_call(h, use_graph ? "hmat_bq_gemm_grouped_modes[graph]" : "hmat_bq_gemm_grouped_modes", descs[i],
+               modes[i], st);
   }
   return st;
 }

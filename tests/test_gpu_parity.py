@@ -272,6 +272,72 @@ def test_grouped_full_plans_of_different_widths(handle, use_graph):
             np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
 
 
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_grouped_modes_mixed(handle, use_graph):
+    """One grouped call whose products run in different modes
+    (hmat_bq_gemm_grouped_modes): split and FP64 products with mixed shapes,
+    ops, flags and scalars.  On small integers every product equals the
+    oracle bit for bit; on uniform inputs each split product equals the same
+    product called alone in split mode bit for bit, each FP64 product the FP64
+    call alone within 1e-14 (the built-in FP64 split-k rule counts the call's
+    FP64 tiles, so the inner-dimension slicing may differ); the graph replays
+    the same bits."""
+    dev = torch.device("cuda")
+    shapes = [(33, 70, 129), (128, 64, 64), (5, 300, 17), (260, 100, 1100), (64, 64, 1), (96, 40, 300)]
+    flags = [(bi.BQ, bi.BQ), (bi.TRS, bi.TRA), (bi.BQ, bi.COMPLEX), (bi.TRS, bi.BQ), (bi.REAL, bi.BQ),
+             (bi.BQ, bi.BQ)]
+    ops = [("N", "N"), ("H", "N"), ("T", "QC"), ("N", "C"), ("C", "T"), ("N", "H")]
+    modes = ["split", "fp64", "split", "fp64", "split", "fp64"]
+    scal = [(1.0, 0.0), (2 - 3j, -1 + 2j), (1.0, 0.0), (0.5, 1.0), (-1j, 0.0), (1.0, 0.25)]
+    for gen in ("small_int", "uniform"):
+        probs, descs = [], []
+        for i, ((m, n, k), (fa, fb), (oa, ob), (al, be)) in enumerate(zip(shapes, flags, ops, scal)):
+            make = getattr(bi, gen)
+            A = make(180 + i, *stored(oa, m, k), flags=fa)
+            B = make(190 + i, *stored(ob, k, n), flags=fb)
+            C0 = bi.small_int(200 + i, m, n)
+            C = C0.to(dev)
+            dA, dB = A.to(dev), B.to(dev)          # kept alive: the descriptors hold their addresses
+            probs.append((A, B, C0, C, dA, dB, oa, ob, fa, fb, al, be))
+            descs.append(hm.make_desc(dA, dB, C, oa, ob, fa, fb, al, be))
+        results = []
+        for _ in range(2):                          # the second call replays the graph
+            for p in probs:
+                p[3].copy_(p[2])
+            hm.hmat_bq_gemm_grouped_modes(handle, descs, modes, tol=TOL, use_graph=use_graph,
+                                          stream=torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            results.append([p[3].cpu().numpy().copy() for p in probs])
+        for a, b in zip(*results):
+            np.testing.assert_array_equal(a, b)
+        for (A, B, C0, C, dA, dB, oa, ob, fa, fb, al, be), md, got in zip(probs, modes, results[0]):
+            if gen == "small_int":
+                want = oracle.bq_gemm(A.numpy(), B.numpy(), oa, ob, alpha=al, beta=be, C=C0.numpy())
+                np.testing.assert_array_equal(got, want)
+            else:
+                ref = C0.to(dev)
+                hm.hmat_bq_gemm(handle, dA, dB, ref, oa, ob, fa, fb, alpha=al, beta=be, mode=md, tol=TOL)
+                torch.cuda.synchronize()
+                if md == "split":
+                    np.testing.assert_array_equal(got, ref.cpu().numpy())
+                else:
+                    r = ref.cpu().numpy()
+                    assert np.linalg.norm(got - r) <= 1e-14 * np.linalg.norm(r)
+
+
+def test_grouped_modes_rejects_an_unknown_mode(handle):
+    dev = torch.device("cuda")
+    A, B = bi.small_int(210, 8, 8).to(dev), bi.small_int(211, 8, 8).to(dev)
+    C = torch.zeros((8, 8, 8), dtype=torch.float64, device=dev)
+    descs = [hm.make_desc(A, B, C), hm.make_desc(A, B, C)]
+    with pytest.raises(hm.HmatError):              # the size query refuses it too
+        hm.hmat_workspace_size_modes(handle, descs, ["split", 7], tol=TOL)
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device=dev)
+    with pytest.raises(hm.HmatError) as e:
+        hm.hmat_bq_gemm_grouped_modes(handle, descs, ["split", 7], tol=TOL, workspace=ws)
+    assert "descriptor 1" in str(e.value)
+
+
 def _splitk_table(code):
     t = np.zeros((16, 16), dtype=np.int8)
     t[:, :] = code
