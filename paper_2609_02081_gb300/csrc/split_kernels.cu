@@ -86,20 +86,30 @@ __device__ __forceinline__ float residue_i64(long long X, const ModConst& mc) {
   return fmod_c(fmaf(r2, mc.c36, fmaf(r1, mc.c18, r0)), mc);
 }
 
+// The job holding unit u of a stage: the last job whose prefix count of that
+// stage (`which`: exponents, encoder A, encoder B, GEMM items, CRT blocks) is
+// at most u.  Every lane of a full warp calls it with the same u (each
+// kernel's block index); the warp probes 32 jobs per round and narrows by a
+// ballot, so a call of 1024 jobs takes two dependent rounds of loads instead
+// of ten.
 __device__ __forceinline__ int find_split_job(const SplitJob* jobs, int njobs, int64_t u, int which) {
-  int lo = 0, hi = njobs - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    int64_t b;
+  const int lane = threadIdx.x & 31;
+  auto begin = [&](int g) -> int64_t {
     switch (which) {
-      case 0: b = jobs[mid].exp_begin; break;
-      case 1: b = jobs[mid].encA_begin; break;
-      case 2: b = jobs[mid].encB_begin; break;
-      case 3: b = jobs[mid].item_begin; break;
-      default: b = jobs[mid].crt_begin; break;
+      case 0: return jobs[g].exp_begin;
+      case 1: return jobs[g].encA_begin;
+      case 2: return jobs[g].encB_begin;
+      case 3: return jobs[g].item_begin;
+      default: return jobs[g].crt_begin;
     }
-    if (b <= u) lo = mid;
-    else hi = mid - 1;
+  };
+  int lo = 0, hi = njobs - 1;               // the answer lies in [lo, hi]; begin(lo) <= u
+  while (lo < hi) {
+    const int step = (hi - lo + 32) / 32;   // lane l probes lo + l step
+    const int g = lo + lane * step;
+    const unsigned le = __ballot_sync(0xffffffffu, g <= hi && begin(g) <= u);
+    lo += (31 - __clz(le)) * step;          // lane 0 (begin(lo) <= u) is always set
+    hi = min(hi, lo + step - 1);
   }
   return lo;
 }
