@@ -3,8 +3,9 @@ the FP64 split-k slice count (hmat_set_fp64_splitk_table).
 
 Tile width: for every (ceil(log2 m), ceil(log2 n)) bin that a set of problem
 shapes touches, the tuner times one representative product of that bin on the
-GPU with each tile width (128 x 64, 128 x 128, 128 x 256) and keeps the
-fastest.  The result is a 16 x 16 table of codes (0 = built-in rule, 1/2/3 =
+GPU with the built-in rule (the fewest tiles of at most 256 columns, each a
+multiple of 32 wide) and with each fixed tile width (128 x 64, 128 x 128,
+128 x 256), and keeps the fastest.  The result is a 16 x 16 table of codes (0 = built-in rule, 1/2/3 =
 64/128/256 columns) that :meth:`Handle.set_tile_table` installs.
 
 Split-k (--fp64): for every (ceil(log2 tiles), ceil(log2 k)) bin of the FP64
@@ -30,7 +31,7 @@ import numpy as np
 from . import Handle, hmat_bq_gemm, hmat_workspace_size, make_desc
 
 BINS = 16
-CODES = {1: 64, 2: 128, 3: 256}
+CODES = {0: "rule", 1: 64, 2: 128, 3: 256}
 
 
 def _bin(x: int) -> int:
@@ -78,7 +79,7 @@ def tune(shapes, tol: float = 1e-12, reps: int = 5, seed: int = 0):
                 times[width] = _time_call(h, A, B, C, ws, tol, reps)
                 del ws
             best = min(times, key=times.get)
-            table[bm, bn_] = {64: 1, 128: 2, 256: 3}[best]
+            table[bm, bn_] = {"rule": 0, 64: 1, 128: 2, 256: 3}[best]
             report[f"{bm},{bn_}"] = {"shape": [m, n, k], "ms": times, "best": best, "members": len(members)}
     return table, report
 

@@ -1,0 +1,57 @@
+"""The autotuner (paper_2609_02081_gb300.autotune): its tables are 16 x 16 codes
+that the library installs (split-mode tile width: 0 = built-in rule, 1/2/3 =
+64/128/256 columns; FP64 split-k: 1..4 = 1/2/4/8 slices), saved in the JSON
+format HMAT_TUNE_TABLE and bench.py --tile-table read.  A tuned table only
+chooses among layouts that compute the same exact integers, so a product on
+small integers gives the oracle's bits with or without it."""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+import bq_inputs as bi
+import oracle
+import paper_2609_02081_gb300 as hm
+from paper_2609_02081_gb300 import autotune
+
+
+def test_save_and_load_round_trip(tmp_path):
+    t = np.zeros((16, 16), dtype=np.int8)
+    t[3, 5], t[10, 10] = 2, 3
+    f = np.zeros((16, 16), dtype=np.int8)
+    f[6, 8] = 4
+    path = tmp_path / "tuned.json"
+    autotune.save(t, {"3,5": {"best": 128}}, str(path), f, {"6,8": {"best_slices": 8}})
+    np.testing.assert_array_equal(autotune.load(str(path)), t)
+    np.testing.assert_array_equal(autotune.load_fp64(str(path)), f)
+    assert json.loads(path.read_text())["report"]["3,5"]["best"] == 128
+    autotune.save(t, {}, str(path))
+    assert autotune.load_fp64(str(path)) is None
+
+
+def test_bins_follow_ceil_log2():
+    assert [autotune._bin(x) for x in (0, 1, 2, 3, 32, 33, 1024, 1 << 20)] == [0, 0, 1, 2, 5, 6, 10, 15]
+
+
+@pytest.mark.gpu
+def test_tuned_tables_install_and_keep_the_bits():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    shapes = [(96, 200, 130), (300, 64, 70)]
+    table, report = autotune.tune(shapes, reps=1)
+    ftable, freport = autotune.tune_fp64([(256, 256, 256)], reps=1)
+    assert table.shape == (16, 16) and set(np.unique(table)) <= {0, 1, 2, 3}
+    assert len(report) == 2 and all(set(r["ms"]) == {"rule", 64, 128, 256} for r in report.values())
+    assert set(np.unique(ftable)) <= {0, 1, 2, 3, 4} and len(freport) == 1
+    dev = torch.device("cuda")
+    with hm.Handle() as h:
+        h.set_tile_table(table)
+        h.set_fp64_splitk_table(ftable)
+        for (m, n, k), mode in [(shapes[0], "split"), (shapes[1], "split"), ((256, 256, 256), "fp64")]:
+            A, B = bi.small_int(300 + m, m, k), bi.small_int(301 + n, k, n)
+            C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+            hm.hmat_bq_gemm(h, A.to(dev), B.to(dev), C, mode=mode, tol=1e-12)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+        assert h.device_error() == 0
