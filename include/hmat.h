@@ -334,7 +334,9 @@ hmat_status hmat_split_info(int64_t k, double tol, int32_t *n_moduli,
 
 /* Read and clear the device error word (0 = none; otherwise a bit mask:
  * 0x1 producer, 0x2 MMA issuer, 0x4 epilogue wait of the residue GEMM gave
- * up; 0x10 split mode met an Inf/NaN input; 0x20 the self-test wait gave up).
+ * up; 0x10 split mode met an Inf/NaN input; 0x20 the self-test wait gave up;
+ * 0x40 the residue GEMM met a work item its launched form does not take, a
+ * library fault).
  * Synchronises the device.  The word is one per device and process, shared by
  * all handles on that device: a handle reads (and clears) bits that work of
  * any handle set.  Errors: NOT_INITIALIZED, INVALID_VALUE (NULL code, or

@@ -15,6 +15,7 @@ enum : uint32_t {
   kErrWaitTmem = 1u << 3,
   kErrNonFinite = 1u << 4,   // split mode met an Inf/NaN input
   kErrWaitSelfTest = 1u << 5,  // hmat_debug_wait_selftest gave up (expected)
+  kErrItemForm = 1u << 6,      // a residue-GEMM item the launched kernel form does not take
 };
 
 // Device address of the library's error word (defined in hmat_capi.cu); kernels

@@ -1004,7 +1004,8 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 0, u.encA, stream, a.scratch, u.max_bits);
   if (e == cudaSuccess) e = launch_split_encode(a.job, 1, h->d_plans, 1, u.encB, stream, a.scratch, u.max_bits);
   if (e == cudaSuccess)
-    e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch);
+    e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch,
+                          u.max_nkb);
   if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod, u.max_np, u.all_full);
   return cuda_status(e);
 }

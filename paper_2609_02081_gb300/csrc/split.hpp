@@ -126,7 +126,7 @@ struct SplitPrep {
   std::vector<SplitJob> jobs;
   int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
   int64_t ws_needed = 0;
-  int max_bits = 0, max_nmod = 0, max_np = 0;
+  int max_bits = 0, max_nmod = 0, max_np = 0, max_nkb = 0;
   bool all_full = true;             // every job uses the paper's full plan
   // one job whose A-side exponents and encoded factor tiles are already in the
   // workspace from the previous call with the same A block and the same shape
@@ -151,7 +151,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
 // uses no heap memory (for the entry point that allocates nothing).
 struct SplitUnits {
   int64_t exp = 0, encA = 0, encB = 0, items = 0, crt = 0, ws_bytes = 0;
-  int max_bits = 0, max_nmod = 0, max_np = 0;
+  int max_bits = 0, max_nmod = 0, max_np = 0, max_nkb = 0;
   bool all_full = false;
 };
 hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
@@ -189,8 +189,10 @@ cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t un
 // units are blocks: encode tiles of 32 rows x 32 k, CRT blocks of 256 elements
 cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int side, int64_t units,
                                 cudaStream_t s, unsigned char* ws, int max_bits);
+// max_nkb: the most 64-deep k-blocks of any job (the one-chunk kernel form
+// serves launches whose jobs all have at most 16)
 cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
-                              unsigned char* ws);
+                              unsigned char* ws, int max_nkb);
 // all_full: every job uses the paper's full plan (structured recombination);
 // else plans of at most 24 products take the packed-weight kernel with the
 // same layout, larger ones (the component-wise comparison plan) the generic one

@@ -244,6 +244,11 @@ struct GemmModConst {
 };
 __constant__ GemmModConst c_gmod[kModTable];
 
+// kOneChunk: every item of the launch has an inner dimension of one chunk
+// (k <= 1024), so the multi-chunk epilogue and its 128 running sums per
+// thread are compiled out (the register budget then holds the single-chunk
+// drain without spills).
+template <bool kOneChunk>
 __global__ void __launch_bounds__(kThreads, 1)
 split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t total_items, uint8_t* ws,
                           uint32_t* err) {
@@ -431,6 +436,15 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         ++chunk_ctr;
         continue;
       }
+      if constexpr (kOneChunk) {
+        // the host launches this form only when every item fits one chunk
+        if (lane == 0) {
+          *abort_flag = 1;
+          atomicOr(err, kErrItemForm);
+        }
+        ok = false;
+        break;
+      } else {
       // running sum of chunk residues (each |r| <= 129, at most 127 chunks:
       // exact in float)
       float acc[kBnMax / 2];
@@ -487,6 +501,7 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
           }
         }
       }
+      }
     }
   }
 
@@ -530,15 +545,22 @@ cudaError_t split_gemm_configure(const int* moduli, int n) {
   }
   cudaError_t e = cudaMemcpyToSymbol(c_gmod, g, sizeof(g));
   if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(split_residue_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  e = cudaFuncSetAttribute(split_residue_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)split_gemm_smem_bytes());
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(split_residue_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)split_gemm_smem_bytes());
 }
 
 cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
-                              unsigned char* ws) {
+                              unsigned char* ws, int max_nkb) {
   if (items <= 0) return cudaSuccess;
-  split_residue_gemm_kernel<<<grid, kThreads, split_gemm_smem_bytes(), s>>>(d_jobs, njobs, items, ws,
-                                                                             device_error_ptr());
+  if (max_nkb <= kKbPerChunk)
+    split_residue_gemm_kernel<true><<<grid, kThreads, split_gemm_smem_bytes(), s>>>(d_jobs, njobs, items, ws,
+                                                                                   device_error_ptr());
+  else
+    split_residue_gemm_kernel<false><<<grid, kThreads, split_gemm_smem_bytes(), s>>>(d_jobs, njobs, items, ws,
+                                                                                    device_error_ptr());
   return cudaGetLastError();
 }
 

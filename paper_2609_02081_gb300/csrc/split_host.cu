@@ -284,6 +284,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     sp.max_bits = std::max(sp.max_bits, sj.bits);
     sp.max_nmod = std::max(sp.max_nmod, sj.nmod);
     sp.max_np = std::max(sp.max_np, sj.np);
+    sp.max_nkb = std::max(sp.max_nkb, sj.nkb);
     sp.all_full = sp.all_full && sj.full;
     sp.jobs.push_back(sj);
   }
@@ -317,6 +318,7 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   units->max_bits = sj.bits;
   units->max_nmod = sj.nmod;
   units->max_np = sj.np;
+  units->max_nkb = sj.nkb;
   units->all_full = sj.full != 0;
   units->ws_bytes = off;
   *out = sj;
@@ -348,7 +350,7 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
   {
     ProfScope ps(h, 3, stream);
     const int grid = (int)std::min<int64_t>(sp.items, handle_sm_count(h));
-    e = launch_split_gemm(d_jobs, njobs, sp.items, grid, stream, ws);
+    e = launch_split_gemm(d_jobs, njobs, sp.items, grid, stream, ws, sp.max_nkb);
   }
   if (e != cudaSuccess) return split_cuda_error(e);
   {
