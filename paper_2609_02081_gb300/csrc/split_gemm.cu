@@ -146,6 +146,13 @@ __device__ __forceinline__ uint32_t instr_desc(int n) {
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])    \
       : "r"(taddr))
 
+#define TMEM_LD16(taddr, r)                                                                                        \
+  asm volatile(                                                                                                    \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"     \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),          \
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])      \
+      : "r"(taddr))
+
 struct Item {
   const uint8_t* a;   // first k-block tile of the left factor
   const uint8_t* b;   // first k-block tile of the right factor
@@ -460,18 +467,19 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         if (!got) { ok = false; break; }
         tc_fence_after();
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * kBnMax + (uint32_t)col0;
+        // 16 columns per load: the running sums already hold 128 registers
 #pragma unroll
-        for (int g = 0; g < kBnMax / 2 / 32; ++g) {
-          if (g * 32 < cols) {
-            uint32_t r[32];
-            TMEM_LD32(taddr + (uint32_t)(g * 32), r);
+        for (int g = 0; g < kBnMax / 2 / 16; ++g) {
+          if (g * 16 < cols) {
+            uint32_t r[16];
+            TMEM_LD16(taddr + (uint32_t)(g * 16), r);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int i = 0; i < 32; i += 2) {
+            for (int i = 0; i < 16; i += 2) {
               const float2 t = fmod_centred2(make_float2(__uint_as_float(r[i]), __uint_as_float(r[i + 1])), npf2, inv2);
-              const float2 a = __fadd2_rn(make_float2(acc[g * 32 + i], acc[g * 32 + i + 1]), t);
-              acc[g * 32 + i] = a.x;
-              acc[g * 32 + i + 1] = a.y;
+              const float2 a = __fadd2_rn(make_float2(acc[g * 16 + i], acc[g * 16 + i + 1]), t);
+              acc[g * 16 + i] = a.x;
+              acc[g * 16 + i + 1] = a.y;
             }
           }
         }
