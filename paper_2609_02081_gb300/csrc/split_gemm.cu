@@ -404,40 +404,62 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * kBnMax + (uint32_t)col0;
         const bool twice = it.nkb > 8;
         int8_t* dst = it.out + (int64_t)row * it.ncols + col0;
-        // 32 columns at a time; the buffer goes back to the MMA issuer right
-        // after the last load, before that group's arithmetic and stores
+        // reduce and store the 32 columns of group g held in rr
+        auto drain32 = [&](int g, const uint32_t* rr) {
 #pragma unroll
-        for (int g = 0; g < kBnMax / 2 / 32; ++g) {
-          if (g * 32 >= cols) break;
-          uint32_t r[32];
-          TMEM_LD32(taddr + (uint32_t)(g * 32), r);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if ((g + 1) * 32 >= cols) {                // last load: release the buffer
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&s.tempty[buf]));
-          }
-          if (row < it.rows) {
+          for (int h = 0; h < 2; ++h) {
+            const int c16 = g * 32 + h * 16;
+            if (c16 < cols && col0 + c16 < it.cols) {
+              uint32_t w[4];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int c16 = g * 32 + h * 16;
-              if (c16 < cols && col0 + c16 < it.cols) {
-                uint32_t w[4];
-#pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                  const int b = h * 16 + v * 4;
-                  float2 t01 = fmod_centred2(make_float2(__uint_as_float(r[b]), __uint_as_float(r[b + 1])), npf2, inv2);
-                  float2 t23 =
-                      fmod_centred2(make_float2(__uint_as_float(r[b + 2]), __uint_as_float(r[b + 3])), npf2, inv2);
-                  if (twice) {
-                    t01 = fmod_centred2(t01, npf2, inv2);
-                    t23 = fmod_centred2(t23, npf2, inv2);
-                  }
-                  w[v] = pack4_residues(t01, t23);
+              for (int v = 0; v < 4; ++v) {
+                const int b = h * 16 + v * 4;
+                float2 t01 = fmod_centred2(make_float2(__uint_as_float(rr[b]), __uint_as_float(rr[b + 1])), npf2, inv2);
+                float2 t23 =
+                    fmod_centred2(make_float2(__uint_as_float(rr[b + 2]), __uint_as_float(rr[b + 3])), npf2, inv2);
+                if (twice) {
+                  t01 = fmod_centred2(t01, npf2, inv2);
+                  t23 = fmod_centred2(t23, npf2, inv2);
                 }
-                *reinterpret_cast<uint4*>(dst + c16) = make_uint4(w[0], w[1], w[2], w[3]);
+                w[v] = pack4_residues(t01, t23);
               }
+              *reinterpret_cast<uint4*>(dst + c16) = make_uint4(w[0], w[1], w[2], w[3]);
             }
+          }
+        };
+        auto release = [&]() {
+          tc_fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(&s.tempty[buf]));
+        };
+        // the buffer goes back to the MMA issuer right after the last load,
+        // before that group's arithmetic and stores
+        if constexpr (kOneChunk) {
+          // two 32-column loads per wait (registers this form leaves free)
+#pragma unroll
+          for (int g = 0; g < kBnMax / 2 / 32; g += 2) {
+            if (g * 32 >= cols) break;
+            const bool two = (g + 1) * 32 < cols;
+            uint32_t r[64];
+            TMEM_LD32(taddr + (uint32_t)(g * 32), r);
+            if (two) TMEM_LD32(taddr + (uint32_t)((g + 1) * 32), (r + 32));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if ((g + (two ? 2 : 1)) * 32 >= cols) release();
+            if (row < it.rows) {
+              drain32(g, r);
+              if (two) drain32(g + 1, r + 32);
+            }
+          }
+        } else {
+          // 32 columns at a time
+#pragma unroll
+          for (int g = 0; g < kBnMax / 2 / 32; ++g) {
+            if (g * 32 >= cols) break;
+            uint32_t r[32];
+            TMEM_LD32(taddr + (uint32_t)(g * 32), r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if ((g + 1) * 32 >= cols) release();
+            if (row < it.rows) drain32(g, r);
           }
         }
         ++chunk_ctr;
