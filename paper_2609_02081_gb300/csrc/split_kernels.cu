@@ -524,6 +524,7 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait4() { asm volatile("cp.async.wait_group 4;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait6() { asm volatile("cp.async.wait_group 6;\n" ::: "memory"); }
 
 // |X| = [x3 x2 x1 x0] (below 2^127) times 2^scale_exp as a double, rounded
 // to nearest even: the top 64 significant bits from the two 64-bit halves and
@@ -839,13 +840,14 @@ __device__ __forceinline__ void crt_pipeline(int rows, int nm_dyn, Issue&& issue
 }
 
 // CRT of the paper's full plan, for launches whose jobs all use it: the 24
-// product planes per modulus in an eight-slot ring (24 KB) four moduli ahead,
-// one barrier per pair of moduli, the modulus loop unrolled for the usual
+// product planes per modulus in a twelve-slot ring (36 KB) six moduli ahead,
+// one barrier per three moduli, the modulus loop unrolled for the usual
 // modulus counts (13 and 14: k up to 8192 at tol 1e-12) so that the CRT
 // digits and the modulus constants are compile-time addresses, and 64
 // registers a thread for four resident blocks per SM.
 constexpr int kFullPlanes = 24;
-constexpr int kFullSlots = 8;
+constexpr int kFullSlots = 12;
+constexpr int kFullGroup = 3;                   // moduli per barrier
 
 template <int L, int NM>
 __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], const unsigned char* rowbase,
@@ -859,11 +861,11 @@ __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], cons
   const int dst0 = pc * kCrtCols + cc * 16;
   auto issue = [&](int l) {
     if (l < nm && has)
-      cp_async16(&ring[l & (kFullSlots - 1)][0][0] + dst0, rowbase + (int64_t)l * kFullPlanes * plane + src0);
+      cp_async16(&ring[l % kFullSlots][0][0] + dst0, rowbase + (int64_t)l * kFullPlanes * plane + src0);
     cp_async_commit();
   };
   auto compute = [&](int l) {
-    const uint8_t(*slot)[kCrtCols] = ring[l & (kFullSlots - 1)];
+    const uint8_t(*slot)[kCrtCols] = ring[l % kFullSlots];
     // P_r = (T1 - T2) + i (T3 - T1 - T2); 4 Q_e = +-8 P_e +- P5 +- P6 +- P7 +- P8
     int v[8];
     if (half == 0) {
@@ -881,26 +883,26 @@ __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], cons
 #pragma unroll
       for (int q = 0; q < L; ++q) acc[e][q] += (long long)x4[e] * c_crt[nm][l][q];
   };
-  // moduli l and l + 1: the slots refilled here held moduli l - 4 and l - 3,
-  // which every thread finished before the barrier of the previous pair
-  auto pair = [&](int l) {
-    issue(l + 4);
-    issue(l + 5);
-    cp_async_wait4();            // moduli l and l + 1 have landed
+  // moduli l .. l + 2: the slots refilled here held moduli l - 6 .. l - 4,
+  // which every thread finished before the barrier of the previous group
+  auto group = [&](int l) {
+    issue(l + 6);
+    issue(l + 7);
+    issue(l + 8);
+    cp_async_wait6();            // moduli l .. l + 2 have landed
     __syncthreads();
     compute(l);
     if (l + 1 < nm) compute(l + 1);
+    if (l + 2 < nm) compute(l + 2);
   };
-  issue(0);
-  issue(1);
-  issue(2);
-  issue(3);
+#pragma unroll
+  for (int l = 0; l < 2 * kFullGroup; ++l) issue(l);
   if constexpr (NM > 0) {
 #pragma unroll
-    for (int l = 0; l < NM; l += 2) pair(l);
+    for (int l = 0; l < NM; l += kFullGroup) group(l);
   } else {
 #pragma unroll 1
-    for (int l = 0; l < nm; l += 2) pair(l);
+    for (int l = 0; l < nm; l += kFullGroup) group(l);
   }
 }
 

@@ -338,6 +338,36 @@ def test_grouped_modes_rejects_an_unknown_mode(handle):
     assert "descriptor 1" in str(e.value)
 
 
+def test_one_chunk_and_general_gemm_forms_agree(handle):
+    """The residue GEMM has two forms: calls whose products all have k <= 1024
+    launch one without the multi-chunk drain, others the general one.  The
+    same products (k = 200 and 1024, ops and scalars) called alone (one-chunk
+    form) and grouped with a product of k = 1100 (general form) give the same
+    bits; the k = 1100 product matches the oracle on small integers."""
+    dev = torch.device("cuda")
+    cases = [((96, 130, 200), ("N", "H"), 2 - 1j, 0.5), ((70, 260, 1024), ("T", "N"), 1.0, 0.0)]
+    big = (40, 50, 1100)
+    probs = []
+    for i, ((m, n, k), (oa, ob), al, be) in enumerate(cases):
+        A = bi.uniform(220 + i, *stored(oa, m, k)).to(dev)
+        B = bi.uniform(230 + i, *stored(ob, k, n)).to(dev)
+        C0 = bi.uniform(240 + i, m, n).to(dev)
+        alone = C0.clone()
+        hm.hmat_bq_gemm(handle, A, B, alone, oa, ob, alpha=al, beta=be, mode="split", tol=TOL)
+        probs.append((A, B, C0, alone, oa, ob, al, be))
+    Ab, Bb = bi.small_int(250, big[0], big[2]), bi.small_int(251, big[2], big[1])
+    dAb, dBb = Ab.to(dev), Bb.to(dev)
+    Cb = torch.full((8, big[0], big[1]), float("nan"), dtype=torch.float64, device=dev)
+    grouped = [p[2].clone() for p in probs]
+    descs = [hm.make_desc(p[0], p[1], g, p[4], p[5], alpha=p[6], beta=p[7]) for p, g in zip(probs, grouped)]
+    descs.append(hm.make_desc(dAb, dBb, Cb))
+    hm.hmat_bq_gemm_grouped(handle, descs, mode="split", tol=TOL, stream=torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    for p, g in zip(probs, grouped):
+        assert torch.equal(g, p[3])
+    np.testing.assert_array_equal(Cb.cpu().numpy(), oracle.bq_gemm(Ab.numpy(), Bb.numpy()))
+
+
 def _splitk_table(code):
     t = np.zeros((16, 16), dtype=np.int8)
     t[:, :] = code
