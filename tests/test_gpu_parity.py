@@ -325,6 +325,37 @@ def test_grouped_modes_mixed(handle, use_graph):
                     assert np.linalg.norm(got - r) <= 1e-14 * np.linalg.norm(r)
 
 
+@pytest.mark.parametrize("algo", ["standard", "isomorph"])
+def test_grouped_modes_mixed_comparison_algorithms(handle, algo):
+    """A mode per product under the comparison algorithms: HMAT-standard (FP64
+    products in several passes, the 64-product plan through the generic CRT)
+    and CMAT (complex images mapped in and out around the products).  Small
+    integers: every product equals the oracle bit for bit."""
+    dev = torch.device("cuda")
+    shapes = [(40, 70, 90), (64, 33, 130), (20, 100, 64)]
+    flags = [(bi.BQ, bi.BQ), (bi.TRS, bi.BQ), (bi.COMPLEX, bi.TRA)]
+    ops = [("N", "N"), ("H", "T"), ("C", "N")]
+    modes = ["split", "fp64", "split"]
+    handle.set_algorithm(algo)
+    try:
+        probs, descs = [], []
+        for i, ((m, n, k), (fa, fb), (oa, ob)) in enumerate(zip(shapes, flags, ops)):
+            A = bi.small_int(260 + i, *stored(oa, m, k), flags=fa)
+            B = bi.small_int(270 + i, *stored(ob, k, n), flags=fb)
+            C0 = bi.small_int(280 + i, m, n)
+            C = C0.to(dev)
+            dA, dB = A.to(dev), B.to(dev)
+            probs.append((A, B, C0, C, dA, dB, oa, ob))
+            descs.append(hm.make_desc(dA, dB, C, oa, ob, fa, fb, 2 - 1j, -1 + 0.5j))
+        hm.hmat_bq_gemm_grouped_modes(handle, descs, modes, tol=TOL, stream=torch.cuda.current_stream())
+        torch.cuda.synchronize()
+        for A, B, C0, C, _, _, oa, ob in probs:
+            want = oracle.bq_gemm(A.numpy(), B.numpy(), oa, ob, alpha=2 - 1j, beta=-1 + 0.5j, C=C0.numpy())
+            np.testing.assert_array_equal(C.cpu().numpy(), want)
+    finally:
+        handle.set_algorithm("bilinear")
+
+
 def test_grouped_modes_rejects_an_unknown_mode(handle):
     dev = torch.device("cuda")
     A, B = bi.small_int(210, 8, 8).to(dev), bi.small_int(211, 8, 8).to(dev)
