@@ -428,6 +428,8 @@ def ours(args, rank, world, local):
         fp = autotune.load_fp64(args.tile_table)
         if fp is not None:
             h.set_fp64_splitk_table(fp)
+        for (ta, tb), t in autotune.load_flag_tables(args.tile_table).items():
+            h.set_tile_table_flags(ta, tb, t)
     d = hm.make_desc(A, B, C, args.opA, "N", fa, fb)
     ws_bytes = hm.hmat_workspace_size(h, [d], args.mode, args.tol)
     ws = torch.empty(max(ws_bytes, 1), dtype=torch.uint8, device=dev)
@@ -629,6 +631,8 @@ def grouped(args, rank, world, local):
         fp = autotune.load_fp64(args.tile_table)
         if fp is not None:
             h.set_fp64_splitk_table(fp)
+        for (ta, tb), t in autotune.load_flag_tables(args.tile_table).items():
+            h.set_tile_table_flags(ta, tb, t)
     modes = ["fp64" if i % 4 == 3 else "split" for i in range(len(descs))] if args.mode == "mixed" else None
     if modes:
         ws_bytes = hm.hmat_workspace_size_modes(h, descs, modes, args.tol)

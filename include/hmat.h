@@ -147,8 +147,11 @@ typedef struct {
  *                         256 codes 0..3 after a "table" key) on the new
  *                         handle, as hmat_set_tile_table would, and, when the
  *                         file has an "fp64_splitk" key, its 256 codes 0..4
- *                         as hmat_set_fp64_splitk_table would; an unreadable
- *                         file keeps the built-in rules and prints a warning. */
+ *                         as hmat_set_fp64_splitk_table would, and for each
+ *                         "table_flags_AA_BB" key (flags in hexadecimal) its
+ *                         256 codes as hmat_set_tile_table_flags would; an
+ *                         unreadable file keeps the built-in rules and prints
+ *                         a warning. */
 
 /* Library version as major*10000 + minor*100 + patch. */
 HMAT_API
@@ -352,6 +355,17 @@ hmat_status hmat_get_device_error(hmat_handle handle, uint32_t *code);
  * Errors: NOT_INITIALIZED, INVALID_VALUE (a code outside 0..3). */
 HMAT_API
 hmat_status hmat_set_tile_table(hmat_handle handle, const int8_t *table);
+
+/* Tile-width table for the split-mode products of one flag pair: codes as in
+ * hmat_set_tile_table; for products whose component flags are exactly
+ * (flagsA, flagsB) the pair's table wins over the general one (under the CMAT
+ * algorithm the products are complex: flags 0x11, 0x11).  NULL removes the
+ * pair's table.  At most 16 pairs per handle.  Affects later calls and
+ * hmat_workspace_size on this handle.  Errors: NOT_INITIALIZED, INVALID_VALUE
+ * (a code outside 0..3, flags above 0xFF, or a 17th pair). */
+HMAT_API
+hmat_status hmat_set_tile_table_flags(hmat_handle handle, uint32_t flagsA,
+                                      uint32_t flagsB, const int8_t *table);
 
 /* FP64 throughput of the current device, measured: one launch of a probe
  * kernel that fills every SM with independent FP64 operations for

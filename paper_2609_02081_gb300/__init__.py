@@ -93,6 +93,7 @@ SIGNATURES = {
     "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
     "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
+    "hmat_set_tile_table_flags": (ctypes.c_int, [_ptr, _u32, _u32, ctypes.c_void_p]),
     "hmat_set_fp64_splitk_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
     "hmat_debug_wait_selftest": (ctypes.c_int, [_ptr, _i64, _ptr]),
     "hmat_measure_fp64_peak": (ctypes.c_int, [_i32, _i64, ctypes.POINTER(_dbl), ctypes.POINTER(_dbl)]),
@@ -252,6 +253,16 @@ class Handle:
             return
         t = np.ascontiguousarray(table, dtype=np.int8).reshape(16, 16)
         _check(lib().hmat_set_tile_table(self._h, t.ctypes.data), "hmat_set_tile_table")
+
+    def set_tile_table_flags(self, flagsA, flagsB, table):
+        """Install a tile-width code table for products of one flag pair (None removes it)."""
+        if table is None:
+            _check(lib().hmat_set_tile_table_flags(self._h, int(flagsA), int(flagsB), None),
+                   "hmat_set_tile_table_flags")
+            return
+        t = np.ascontiguousarray(table, dtype=np.int8).reshape(16, 16)
+        _check(lib().hmat_set_tile_table_flags(self._h, int(flagsA), int(flagsB), t.ctypes.data),
+               "hmat_set_tile_table_flags")
 
     def set_fp64_splitk_table(self, table):
         """Install a 16 x 16 FP64 split-k code table (None: built-in rule); see autotune.py."""

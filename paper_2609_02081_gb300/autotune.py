@@ -11,13 +11,19 @@ multiple of 32 wide) and with each fixed tile width (128 x 64, 128 x 128,
 Split-k (--fp64): for every (ceil(log2 tiles), ceil(log2 k)) bin of the FP64
 shapes, one representative product is timed in FP64 mode with its inner
 dimension in 1, 2, 4 and 8 slices; the fastest code (1..4) goes into a second
-16 x 16 table that :meth:`Handle.set_fp64_splitk_table` installs.  Both are
-saved in one JSON file ("table", "fp64_splitk"), the format HMAT_TUNE_TABLE
-reads.
+16 x 16 table that :meth:`Handle.set_fp64_splitk_table` installs.
+
+Per flag pair (--flags FA,FB): the tile widths are tuned on products with
+those component flags and saved as that pair's table
+("table_flags_AA_BB", installed by :meth:`Handle.set_tile_table_flags`),
+which the library uses for products of exactly that pair.  All tables go into
+one JSON file ("table", "fp64_splitk", "table_flags_AA_BB"), the format
+HMAT_TUNE_TABLE reads.
 
     python -m paper_2609_02081_gb300.autotune --out tile_table.json          # the 512-shape batch
     python -m paper_2609_02081_gb300.autotune --shapes 256x256x256,1024x64x512
     python -m paper_2609_02081_gb300.autotune --fp64 256x256x256,128x128x2048 --out tuned.json
+    python -m paper_2609_02081_gb300.autotune --flags 0x0f,0xff --shapes 4096x4096x4096 --out tuned.json
 """
 from __future__ import annotations
 
@@ -38,21 +44,23 @@ def _bin(x: int) -> int:
     return min(BINS - 1, max(0, math.ceil(math.log2(max(x, 1)))))
 
 
-def _time_call(h, A, B, C, ws, tol, reps):
+def _time_call(h, A, B, C, ws, tol, reps, flags=(0xFF, 0xFF)):
     import torch
     stream = torch.cuda.current_stream()
-    hmat_bq_gemm(h, A, B, C, mode="split", tol=tol, workspace=ws, stream=stream)   # warm
+    kw = dict(flagsA=flags[0], flagsB=flags[1], mode="split", tol=tol, workspace=ws, stream=stream)
+    hmat_bq_gemm(h, A, B, C, **kw)   # warm
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(reps):
-        hmat_bq_gemm(h, A, B, C, mode="split", tol=tol, workspace=ws, stream=stream)
+        hmat_bq_gemm(h, A, B, C, **kw)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1) / reps
 
 
-def tune(shapes, tol: float = 1e-12, reps: int = 5, seed: int = 0):
-    """Return (table, report) for the given (m, n, k) shapes."""
+def tune(shapes, tol: float = 1e-12, reps: int = 5, seed: int = 0, flags=(0xFF, 0xFF)):
+    """Return (table, report) for the given (m, n, k) shapes of products with
+    component flags `flags` = (flagsA, flagsB)."""
     import torch
     dev = torch.device("cuda")
     groups = {}
@@ -73,10 +81,13 @@ def tune(shapes, tol: float = 1e-12, reps: int = 5, seed: int = 0):
             for code, width in CODES.items():
                 t = np.zeros((BINS, BINS), dtype=np.int8)
                 t[bm, bn_] = code
-                h.set_tile_table(t)
-                nbytes = hmat_workspace_size(h, [make_desc(A, B, C)], "split", tol)
+                if flags == (0xFF, 0xFF):
+                    h.set_tile_table(t)
+                else:
+                    h.set_tile_table_flags(flags[0], flags[1], t)
+                nbytes = hmat_workspace_size(h, [make_desc(A, B, C, flagsA=flags[0], flagsB=flags[1])], "split", tol)
                 ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=dev)
-                times[width] = _time_call(h, A, B, C, ws, tol, reps)
+                times[width] = _time_call(h, A, B, C, ws, tol, reps, flags)
                 del ws
             best = min(times, key=times.get)
             table[bm, bn_] = {"rule": 0, 64: 1, 128: 2, 256: 3}[best]
@@ -130,11 +141,14 @@ def tune_fp64(shapes, reps: int = 5, seed: int = 0):
     return table, report
 
 
-def save(table, report, path, fp64_table=None, fp64_report=None):
+def save(table, report, path, fp64_table=None, fp64_report=None, flag_tables=None):
+    """Write the tables as JSON; flag_tables: {(flagsA, flagsB): 16 x 16 codes}."""
     out = {"table": np.asarray(table).astype(int).tolist(), "report": report}
     if fp64_table is not None:
         out["fp64_splitk"] = np.asarray(fp64_table).astype(int).tolist()
         out["fp64_report"] = fp64_report
+    for (fa, fb), t in (flag_tables or {}).items():
+        out["table_flags_%02x_%02x" % (fa, fb)] = np.asarray(t).astype(int).tolist()
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
 
@@ -142,6 +156,18 @@ def save(table, report, path, fp64_table=None, fp64_report=None):
 def load(path):
     with open(path) as f:
         return np.asarray(json.load(f)["table"], dtype=np.int8)
+
+
+def load_flag_tables(path):
+    """The per flag pair tile tables of a tuned JSON file: {(flagsA, flagsB): table}."""
+    with open(path) as f:
+        data = json.load(f)
+    out = {}
+    for key, t in data.items():
+        if key.startswith("table_flags_"):
+            fa, fb = (int(x, 16) for x in key[len("table_flags_"):].split("_"))
+            out[(fa, fb)] = np.asarray(t, dtype=np.int8)
+    return out
 
 
 def load_fp64(path):
@@ -158,6 +184,9 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--fp64", default=None, help="'MxNxK,...': also tune the FP64 split-k table on these shapes")
+    ap.add_argument("--flags", default=None,
+                    help="'FA,FB' (e.g. 0x0f,0xff): tune the tile widths of products with these component flags "
+                         "and save them as that pair's table")
     ap.add_argument("--out", default="tile_table.json")
     args = ap.parse_args()
     if args.shapes == "batch512":
@@ -167,12 +196,19 @@ def main():
         shapes = bq_inputs.batch_shapes(104, 512)
     else:
         shapes = [tuple(int(x) for x in s.split("x")) for s in args.shapes.split(",")]
-    table, report = tune(shapes, args.tol, args.reps)
+    flag_tables = None
+    if args.flags:
+        fa, fb = (int(x, 0) for x in args.flags.split(","))
+        ftab, report = tune(shapes, args.tol, args.reps, flags=(fa, fb))
+        flag_tables = {(fa, fb): ftab}
+        table = np.zeros((BINS, BINS), dtype=np.int8)      # other products keep the built-in rule
+    else:
+        table, report = tune(shapes, args.tol, args.reps)
     ftable = freport = None
     if args.fp64:
         fshapes = [tuple(int(x) for x in s.split("x")) for s in args.fp64.split(",")]
         ftable, freport = tune_fp64(fshapes, args.reps)
-    save(table, report, args.out, ftable, freport)
+    save(table, report, args.out, ftable, freport, flag_tables)
     print(json.dumps({"bins": len(report), "fp64_bins": len(freport or {}), "out": args.out}))
 
 

@@ -91,7 +91,7 @@ hmat_status cuda_status(cudaError_t e);
 hmat_status validate(const hmat_gemm_desc& d, JobDesc* out);
 
 // The handle's split tile-width table, or null for the built-in rule.
-const int8_t* split_table(hmat_context* h);
+TileTables split_table(const hmat_context* h);
 
 int64_t align_up256(int64_t x);
 
@@ -122,7 +122,7 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
 // Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule);
 // with a handle, the FP64 products include the split-k partials the handle would use.
 // modes: as for run.
-hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
+hmat_status workspace_bytes(int algo, const TileTables& tables, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
                             double tol, size_t* bytes, const hmat_context* h = nullptr,
                             const int32_t* modes = nullptr);
 

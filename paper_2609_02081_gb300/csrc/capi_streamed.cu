@@ -38,7 +38,7 @@ struct StreamedPlan {
   int64_t total = 0;
 };
 
-hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d, int32_t mode, double tol,
+hmat_status plan_streamed(int algo, const TileTables& tables, const hmat_gemm_desc& d, int32_t mode, double tol,
                           size_t budget, bool a_host, bool b_host, bool c_host, StreamedPlan* out) {
   if (d.m <= 0 || d.n <= 0) { *out = StreamedPlan{}; return HMAT_STATUS_SUCCESS; }
   const int64_t m = d.m, n = d.n, k = std::max<int64_t>(d.k, 1);
@@ -70,7 +70,7 @@ hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d
   // (Only under the built-in tile rule, whose width depends on n alone: a tuned
   // table could give a ragged last block row another width than the cached B.)
   if (mode == HMAT_MODE_SPLIT && algo != HMAT_ALGO_ISOMORPH && (a_host || b_host || c_host) && d.k > 0 &&
-      std::min(m, n) >= 512 && table == nullptr) {
+      std::min(m, n) >= 512 && tables.lookup(d.flagsA, d.flagsB) == nullptr) {
     KPlan kp;
     if (!build_plan(d.flagsA, d.flagsB, &kp, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
       return HMAT_STATUS_INTERNAL;
@@ -85,11 +85,14 @@ hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d
       hmat_gemm_desc bd = d;
       bd.m = p.mb; bd.n = p.nb; bd.k = p.kb;
       size_t ws = 0;
-      hmat_status st = workspace_bytes(algo, table, 1, &bd, mode, tol, &ws);
+      hmat_status st = workspace_bytes(algo, tables, 1, &bd, mode, tol, &ws);
       if (st == HMAT_STATUS_UNSUPPORTED) continue;
       if (st != HMAT_STATUS_SUCCESS) return st;
       int64_t region = 0;
-      st = split_b_region_bytes(SplitShape{p.mb, p.nb, p.kb, kp.np, kp.nlf, kp.nrf}, tol, table, &region);
+      SplitShape bsh{p.mb, p.nb, p.kb, kp.np, kp.nlf, kp.nrf};
+      bsh.fa = d.flagsA;
+      bsh.fb = d.flagsB;
+      st = split_b_region_bytes(bsh, tol, tables, &region);
       if (st != HMAT_STATUS_SUCCESS) return st;
       p.ws = align_up256((int64_t)ws);
       p.b_region = align_up256(region);
@@ -110,7 +113,7 @@ hmat_status plan_streamed(int algo, const int8_t* table, const hmat_gemm_desc& d
       hmat_gemm_desc bd = d;
       bd.m = p.mb; bd.n = p.nb; bd.k = d.k > 0 ? p.kb : 0;
       size_t ws = 0;
-      hmat_status st = workspace_bytes(algo, table, 1, &bd, mode, tol, &ws);
+      hmat_status st = workspace_bytes(algo, tables, 1, &bd, mode, tol, &ws);
       if (st == HMAT_STATUS_UNSUPPORTED) continue;    // a block too large for one split product
       if (st != HMAT_STATUS_SUCCESS) return st;
       p.ws = align_up256((int64_t)ws);
@@ -159,7 +162,7 @@ hmat_status plan_args(hmat_handle h, int32_t opA, int32_t opB, uint32_t flagsA, 
   hmat_gemm_desc d;
   std::memset(&d, 0, sizeof(d));
   d.opA = opA; d.opB = opB; d.flagsA = flagsA; d.flagsB = flagsB; d.m = m; d.n = n; d.k = k;
-  return plan_streamed(h ? h->algo : HMAT_ALGO_BILINEAR, h ? split_table(h) : nullptr, d, mode, tol, budget, r.a,
+  return plan_streamed(h ? h->algo : HMAT_ALGO_BILINEAR, h ? split_table(h) : TileTables{}, d, mode, tol, budget, r.a,
                        r.b, r.c, p);
 }
 

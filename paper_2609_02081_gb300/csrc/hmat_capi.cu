@@ -303,7 +303,14 @@ SplitState& handle_split(hmat_context* h) { return h->split; }
 // ----------------------------------------------------------------- dispatch
 namespace hmat {
 
-const int8_t* split_table(hmat_context* h) { return h->split.has_table ? h->split.tile_table : nullptr; }
+TileTables split_table(const hmat_context* h) {
+  TileTables t;
+  t.general = h->split.has_table ? h->split.tile_table : nullptr;
+  t.by_flags = &h->split.flag_tables[0][0];
+  t.keys = h->split.flag_keys;
+  t.n_flags = h->split.n_flag_tables;
+  return t;
+}
 
 // A validated call: FP64 launch groups (a plan with more products than one
 // pass holds adds later groups that accumulate into C), split jobs (with
@@ -579,8 +586,10 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
   h->last_bad = -1;
   // key: descriptors + mode (or the per-product modes) + tol + workspace + algorithm + tile table
   const size_t tbl = sizeof(h->split.tile_table);
+  const size_t ftbl = (size_t)h->split.n_flag_tables * (sizeof(uint16_t) + sizeof(h->split.flag_tables[0]));
   const size_t nmodes = modes ? (size_t)std::max(count, 0) : 0;
   std::vector<unsigned char> key(sizeof(int32_t) * 3 + sizeof(double) + sizeof(void*) + sizeof(size_t) + 1 + tbl +
+                                 sizeof(int32_t) + ftbl +
                                  (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc) + nmodes * sizeof(int32_t));
   {
     unsigned char* k = key.data();
@@ -592,6 +601,11 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
     std::memcpy(k, &ws_bytes, sizeof(size_t)); k += sizeof(size_t);
     *k++ = h->split.has_table ? 1 : 0;
     std::memcpy(k, h->split.tile_table, tbl); k += tbl;
+    std::memcpy(k, &h->split.n_flag_tables, sizeof(int32_t)); k += sizeof(int32_t);
+    for (int f = 0; f < h->split.n_flag_tables; ++f) {
+      std::memcpy(k, &h->split.flag_keys[f], sizeof(uint16_t)); k += sizeof(uint16_t);
+      std::memcpy(k, h->split.flag_tables[f], sizeof(h->split.flag_tables[f])); k += sizeof(h->split.flag_tables[f]);
+    }
     if (count > 0 && descs) std::memcpy(k, descs, (size_t)count * sizeof(hmat_gemm_desc));
     k += (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc);
     if (nmodes) std::memcpy(k, modes, nmodes * sizeof(int32_t));
@@ -711,12 +725,10 @@ cudaError_t configure_device(int device) {
 // key followed by 16 x 16 integer codes 0..3) installed on every new handle.
 // A file that cannot be read or parsed leaves the built-in rule and prints one
 // warning line.
-// 16 x 16 integer codes 0..max_code following `key` in text; false if absent or malformed.
-static bool read_codes(const std::string& text, const char* key, int max_code, int8_t* table) {
-  const size_t at = text.find(key);
-  if (at == std::string::npos) return false;
+// 16 x 16 integer codes 0..max_code from position `from` of text; false if malformed.
+static bool read_codes_at(const std::string& text, size_t from, int max_code, int8_t* table) {
   int count = 0;
-  for (size_t i = at + std::strlen(key); i < text.size() && count < kTileBins * kTileBins; ++i) {
+  for (size_t i = from; i < text.size() && count < kTileBins * kTileBins; ++i) {
     const char c = text[i];
     if (c >= '0' && c <= '9') {
       int v = 0;
@@ -729,6 +741,13 @@ static bool read_codes(const std::string& text, const char* key, int max_code, i
     }
   }
   return count == kTileBins * kTileBins;
+}
+
+// The codes following `key` in text; false if absent or malformed.
+static bool read_codes(const std::string& text, const char* key, int max_code, int8_t* table) {
+  const size_t at = text.find(key);
+  if (at == std::string::npos) return false;
+  return read_codes_at(text, at + std::strlen(key), max_code, table);
 }
 
 void load_env_tile_table(hmat_context* h) {
@@ -761,6 +780,22 @@ void load_env_tile_table(hmat_context* h) {
       std::fprintf(stderr, "hmat: HMAT_TUNE_TABLE %s: expected %d codes 0..4 after \"fp64_splitk\"; using the "
                    "built-in split-k rule\n", path, kTileBins * kTileBins);
     }
+  }
+  // optional: per flag pair tile tables, keys "table_flags_AA_BB" (hexadecimal flags)
+  const char* pre = "\"table_flags_";
+  for (size_t at = text.find(pre); at != std::string::npos; at = text.find(pre, at + 1)) {
+    unsigned fa = 0, fb = 0;
+    int used = 0;
+    if (std::sscanf(text.c_str() + at, "\"table_flags_%2x_%2x\"%n", &fa, &fb, &used) != 2 || used == 0 ||
+        !read_codes_at(text, at + (size_t)used, 3, table) ||
+        h->split.n_flag_tables >= kMaxFlagTables) {
+      std::fprintf(stderr, "hmat: HMAT_TUNE_TABLE %s: a malformed or surplus \"table_flags_\" entry is ignored\n",
+                   path);
+      continue;
+    }
+    const int idx = h->split.n_flag_tables++;
+    h->split.flag_keys[idx] = (uint16_t)((fa << 8) | fb);
+    std::memcpy(h->split.flag_tables[idx], table, sizeof(table));
   }
 }
 
@@ -830,7 +865,7 @@ hmat_status hmat_destroy(hmat_handle h) {
 namespace hmat {
 
 // Workspace of a call under algorithm `algo` and split tile table `table` (null: built-in rule).
-hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
+hmat_status workspace_bytes(int algo, const TileTables& tables, int32_t count, const hmat_gemm_desc* descs, int32_t mode,
                             double tol, size_t* bytes, const hmat_context* h, const int32_t* modes) {
   if (!bytes || count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
   if (!modes && mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
@@ -863,11 +898,11 @@ hmat_status workspace_bytes(int algo, const int8_t* table, int32_t count, const 
       fp64[i] = 1;
       continue;
     }
-    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf, p.bilinear_full});
+    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf, p.bilinear_full, fa, fb});
   }
   size_t split = 0;
   if (!shapes.empty()) {
-    hmat_status st = split_workspace_bytes(shapes, tol, table, &split);
+    hmat_status st = split_workspace_bytes(shapes, tol, tables, &split);
     if (st != HMAT_STATUS_SUCCESS) return st;
   }
   *bytes = (size_t)align_up256(iso) + split;
@@ -1087,6 +1122,35 @@ hmat_status hmat_set_tile_table(hmat_handle h, const int8_t* table) {
     if (table[i] < 0 || table[i] > 3) return HMAT_STATUS_INVALID_VALUE;
   std::memcpy(h->split.tile_table, table, sizeof(h->split.tile_table));
   h->split.has_table = true;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_set_tile_table_flags(hmat_handle h, uint32_t flagsA, uint32_t flagsB, const int8_t* table) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (flagsA > 0xFFu || flagsB > 0xFFu) return HMAT_STATUS_INVALID_VALUE;
+  std::lock_guard<std::mutex> lock(h->mu);
+  SplitState& sp = h->split;
+  const uint16_t key = (uint16_t)((flagsA << 8) | flagsB);
+  int at = -1;
+  for (int i = 0; i < sp.n_flag_tables; ++i)
+    if (sp.flag_keys[i] == key) at = i;
+  if (!table) {
+    if (at >= 0) {                    // keep the used entries contiguous
+      const int last = sp.n_flag_tables - 1;
+      sp.flag_keys[at] = sp.flag_keys[last];
+      std::memcpy(sp.flag_tables[at], sp.flag_tables[last], sizeof(sp.flag_tables[0]));
+      sp.n_flag_tables = last;
+    }
+    return HMAT_STATUS_SUCCESS;
+  }
+  for (int i = 0; i < kTileBins * kTileBins; ++i)
+    if (table[i] < 0 || table[i] > 3) return HMAT_STATUS_INVALID_VALUE;
+  if (at < 0) {
+    if (sp.n_flag_tables >= kMaxFlagTables) return HMAT_STATUS_INVALID_VALUE;
+    at = sp.n_flag_tables++;
+    sp.flag_keys[at] = key;
+  }
+  std::memcpy(sp.flag_tables[at], table, sizeof(sp.flag_tables[0]));
   return HMAT_STATUS_SUCCESS;
 }
 

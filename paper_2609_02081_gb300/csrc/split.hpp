@@ -67,6 +67,24 @@ struct SplitShape {
   int64_t m, n, k;
   int np, nlf, nrf;
   int full = 0;                     // the plan is the paper's full 24-product plan (KPlan::bilinear_full)
+  uint32_t fa = 0xFFu, fb = 0xFFu;  // component flags of op(A), op(B) (the tile table may depend on them)
+};
+
+// Split-mode tile-width tables: kTileBins x kTileBins codes (0 = built-in
+// rule, 1/2/3 = 64/128/256 columns) for every product and, optionally, per
+// (flagsA, flagsB) pair; a pair's own table wins for its products.
+constexpr int kMaxFlagTables = 16;
+struct TileTables {
+  const int8_t* general = nullptr;  // null: the built-in rule
+  const int8_t* by_flags = nullptr; // n_flags tables, kTileBins^2 codes each
+  const uint16_t* keys = nullptr;   // (flagsA << 8) | flagsB of each
+  int n_flags = 0;
+  const int8_t* lookup(uint32_t fa, uint32_t fb) const {
+    const uint16_t key = (uint16_t)(((fa & 0xFFu) << 8) | (fb & 0xFFu));
+    for (int i = 0; i < n_flags; ++i)
+      if (keys[i] == key) return by_flags + (size_t)i * kTileBins * kTileBins;
+    return general;
+  }
 };
 
 // Per-problem layout inside the caller's workspace.
@@ -89,7 +107,7 @@ struct SplitJob {
 };
 
 // Workspace bytes for a set of problems (sum of the per-problem layouts).
-hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const int8_t* table,
+hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const TileTables& tables,
                                   size_t* bytes);
 // Bin index of a dimension in the tile-width table.
 int tile_bin(int64_t x);
@@ -116,6 +134,9 @@ struct SplitState {
   cudaStream_t upload = nullptr;    // job-table copies, issued when the call is made
   bool has_table = false;
   int8_t tile_table[kTileBins * kTileBins] = {};   // tuned tile widths (0: default rule)
+  int n_flag_tables = 0;                            // per flag pair tables, first n_flag_tables used
+  uint16_t flag_keys[kMaxFlagTables] = {};
+  int8_t flag_tables[kMaxFlagTables][kTileBins * kTileBins] = {};
 };
 
 cudaError_t split_configure();
@@ -139,14 +160,14 @@ struct SplitPrep {
 
 // Bytes of a job's B side (column exponents and encoded right factors), the
 // region split_place_b points a job at.
-hmat_status split_b_region_bytes(const SplitShape& sh, double tol, const int8_t* table, int64_t* bytes);
+hmat_status split_b_region_bytes(const SplitShape& sh, double tol, const TileTables& tables, int64_t* bytes);
 // Point the job's B side at `offset` (bytes into the split workspace) instead
 // of its own layout slot.
 void split_place_b(SplitJob& sj, int64_t offset);
 
 // Lay the jobs out in a workspace of ws_bytes (WORKSPACE_TOO_SMALL if it does not fit).
 hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
-                          const int8_t* table, SplitPrep* out);
+                          const TileTables& tables, SplitPrep* out);
 // Layout of one job at workspace offset 0 with its per-stage unit counts;
 // uses no heap memory (for the entry point that allocates nothing).
 struct SplitUnits {
@@ -154,7 +175,7 @@ struct SplitUnits {
   int max_bits = 0, max_nmod = 0, max_np = 0, max_nkb = 0;
   bool all_full = false;
 };
-hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
+hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const TileTables& tables, SplitJob* out,
                                 SplitUnits* units);
 // Launch the four stages reading the device job table d_jobs.
 hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d_jobs, const KPlan* d_plans,

@@ -179,7 +179,7 @@ static inline int64_t crt_blocks(int64_t m, int64_t n, int rows) {
 }
 
 // Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
-static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const int8_t* table, SplitJob* sj,
+static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const TileTables& tables, SplitJob* sj,
                               int64_t* offset) {
   if (plan) {                      // the CRT's integer residue step needs |4Q| <= kMaxWeightSum * 127
     for (int e = 0; e < 8; ++e) {
@@ -193,7 +193,7 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
   if (st != HMAT_STATUS_SUCCESS) return st;
   sj->nmod = sp.nmod;
   sj->bits = sp.bits;
-  sj->bn = choose_bn(table, sh.m, sh.n);
+  sj->bn = choose_bn(tables.lookup(sh.fa, sh.fb), sh.m, sh.n);
   sj->tiles_m = (int32_t)((sh.m + kTileM - 1) / kTileM);
   sj->tiles_n = (int32_t)((sh.n + sj->bn - 1) / sj->bn);
   sj->nkb = (int32_t)((sh.k + kTileK - 1) / kTileK);
@@ -230,11 +230,11 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
   return HMAT_STATUS_SUCCESS;
 }
 
-hmat_status split_b_region_bytes(const SplitShape& sh, double tol, const int8_t* table, int64_t* bytes) {
+hmat_status split_b_region_bytes(const SplitShape& sh, double tol, const TileTables& tables, int64_t* bytes) {
   SplitJob sj;
   std::memset(&sj, 0, sizeof(sj));
   int64_t off = 0;
-  hmat_status st = layout_job(sh, nullptr, tol, table, &sj, &off);
+  hmat_status st = layout_job(sh, nullptr, tol, tables, &sj, &off);
   if (st != HMAT_STATUS_SUCCESS) return st;
   *bytes = align256(4 * sh.n) + align256((int64_t)sj.nmod * sj.nrf * sj.encB_plane);
   return HMAT_STATUS_SUCCESS;
@@ -245,13 +245,13 @@ void split_place_b(SplitJob& sj, int64_t offset) {
   sj.off_encB = offset + align256(4 * (int64_t)sj.d.n);
 }
 
-hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const int8_t* table,
+hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double tol, const TileTables& tables,
                                   size_t* bytes) {
   int64_t off = 0;
   for (const SplitShape& sh : shapes) {
     SplitJob sj;
     std::memset(&sj, 0, sizeof(sj));
-    hmat_status st = layout_job(sh, nullptr, tol, table, &sj, &off);
+    hmat_status st = layout_job(sh, nullptr, tol, tables, &sj, &off);
     if (st != HMAT_STATUS_SUCCESS) return st;
   }
   *bytes = (size_t)off;
@@ -259,7 +259,7 @@ hmat_status split_workspace_bytes(const std::vector<SplitShape>& shapes, double 
 }
 
 hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans, double tol, size_t ws_bytes,
-                          const int8_t* table, SplitPrep* out) {
+                          const TileTables& tables, SplitPrep* out) {
   SplitPrep sp;
   int64_t off = 0;
   for (const JobDesc& d : jobs) {
@@ -267,8 +267,8 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     SplitJob sj;
     std::memset(&sj, 0, sizeof(sj));
     sj.d = d;
-    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full};
-    hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
+    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full, d.fa, d.fb};
+    hmat_status st = layout_job(sh, &P, tol, tables, &sj, &off);
     if (st != HMAT_STATUS_SUCCESS) return st;
     sj.exp_begin = sp.exp_units;
     sp.exp_units += (d.m + 31) / 32 + (d.n + 31) / 32;
@@ -300,14 +300,14 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
   return HMAT_STATUS_SUCCESS;
 }
 
-hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const int8_t* table, SplitJob* out,
+hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const TileTables& tables, SplitJob* out,
                                 SplitUnits* units) {
   SplitJob sj;
   std::memset(&sj, 0, sizeof(sj));
   sj.d = d;
-  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full};
+  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full, d.fa, d.fb};
   int64_t off = 0;
-  hmat_status st = layout_job(sh, &P, tol, table, &sj, &off);
+  hmat_status st = layout_job(sh, &P, tol, tables, &sj, &off);
   if (st != HMAT_STATUS_SUCCESS) return st;
   units->exp = (d.m + 31) / 32 + (d.n + 31) / 32;
   units->encA = enc_blocks(d.m, sj.nkb);

@@ -27,7 +27,15 @@ def test_save_and_load_round_trip(tmp_path):
     np.testing.assert_array_equal(autotune.load_fp64(str(path)), f)
     assert json.loads(path.read_text())["report"]["3,5"]["best"] == 128
     autotune.save(t, {}, str(path))
-    assert autotune.load_fp64(str(path)) is None
+    assert autotune.load_fp64(str(path)) is None and autotune.load_flag_tables(str(path)) == {}
+    g = np.zeros((16, 16), dtype=np.int8)
+    g[8, 9] = 1
+    autotune.save(t, {}, str(path), flag_tables={(0x0F, 0xFF): g, (0x11, 0x11): t})
+    ft = autotune.load_flag_tables(str(path))
+    assert set(ft) == {(0x0F, 0xFF), (0x11, 0x11)}
+    np.testing.assert_array_equal(ft[(0x0F, 0xFF)], g)
+    np.testing.assert_array_equal(ft[(0x11, 0x11)], t)
+    assert "table_flags_0f_ff" in json.loads(path.read_text())
 
 
 def test_bins_follow_ceil_log2():
@@ -54,4 +62,35 @@ def test_tuned_tables_install_and_keep_the_bits():
             hm.hmat_bq_gemm(h, A.to(dev), B.to(dev), C, mode=mode, tol=1e-12)
             torch.cuda.synchronize()
             np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+        assert h.device_error() == 0
+
+
+@pytest.mark.gpu
+def test_flag_pair_table_applies_to_its_pair_only():
+    """A tile table installed for one flag pair changes the layout (hence the
+    workspace size) of products with exactly those flags, leaves others on the
+    general rule, keeps the oracle's bits, and is removed again by None."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    dev = torch.device("cuda")
+    m, n, k = 200, 300, 150
+    code1 = np.full((16, 16), 2, dtype=np.int8)       # 128-wide tiles: 384 padded columns of n = 300, not 320
+    with hm.Handle() as h:
+        def ws(fa, fb):
+            A = torch.zeros((8, m, k), dtype=torch.float64, device=dev)
+            B = torch.zeros((8, k, n), dtype=torch.float64, device=dev)
+            C = torch.zeros((8, m, n), dtype=torch.float64, device=dev)
+            return hm.hmat_workspace_size(h, [hm.make_desc(A, B, C, flagsA=fa, flagsB=fb)], "split", 1e-12)
+        base_trs, base_bq = ws(bi.TRS, bi.BQ), ws(bi.BQ, bi.BQ)
+        h.set_tile_table_flags(bi.TRS, bi.BQ, code1)
+        assert ws(bi.TRS, bi.BQ) != base_trs and ws(bi.BQ, bi.BQ) == base_bq
+        A, B = bi.small_int(320, m, k, flags=bi.TRS), bi.small_int(321, k, n)
+        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+        hm.hmat_bq_gemm(h, A.to(dev), B.to(dev), C, flagsA=bi.TRS, flagsB=bi.BQ, mode="split", tol=1e-12)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+        h.set_tile_table_flags(bi.TRS, bi.BQ, None)
+        assert ws(bi.TRS, bi.BQ) == base_trs
+        with pytest.raises(hm.HmatError):
+            h.set_tile_table_flags(0x100, bi.BQ, code1)
         assert h.device_error() == 0
