@@ -42,6 +42,72 @@ def test_bins_follow_ceil_log2():
     assert [autotune._bin(x) for x in (0, 1, 2, 3, 32, 33, 1024, 1 << 20)] == [0, 0, 1, 2, 5, 6, 10, 15]
 
 
+def test_greedy_bins_keeps_only_clear_gains():
+    """The grouped tuner's coordinate search: a bin takes the width whose
+    whole-call time is lowest, only when that beats the bin's current code by
+    more than the gain fraction; later bins are timed on top of the earlier
+    choices."""
+    base = 100.0
+    # fake call time: bin (9, 9) is 5 % faster with 128 columns, bin (7, 8)
+    # 0.2 % faster with 64 (noise-sized), bin (5, 5) 3 % faster with 256 but
+    # only once (9, 9) has taken 128
+    def timed(t):
+        ms = base
+        if t[9, 9] == 2:
+            ms -= 5.0
+        if t[7, 8] == 1:
+            ms -= 0.2
+        if t[5, 5] == 3 and t[9, 9] == 2:
+            ms -= 3.0
+        return ms
+    calls = []
+
+    def counted(t):
+        calls.append(t.copy())
+        return timed(t)
+    table, report = autotune.greedy_bins([(9, 9), (7, 8), (5, 5)], counted, gain=0.01)
+    assert table[9, 9] == 2 and table[7, 8] == 0 and table[5, 5] == 3
+    assert int(np.count_nonzero(table)) == 2
+    assert len(calls) == 3 * 4
+    assert report["9,9"]["kept"] == 128 and report["7,8"]["kept"] == "rule" and report["5,5"]["kept"] == 256
+    assert report["7,8"]["ms"][64] == pytest.approx(94.8)
+    # a start table is taken as given, and a zero gain keeps any improvement
+    start = np.zeros((16, 16), dtype=np.int8)
+    start[9, 9] = 2
+    table2, _ = autotune.greedy_bins([(7, 8)], timed, table=start, gain=0.0)
+    assert table2[9, 9] == 2 and table2[7, 8] == 1
+    assert start[7, 8] == 0                                   # the caller's table is not modified
+
+
+@pytest.mark.gpu
+def test_grouped_tuner_runs_and_keeps_the_bits():
+    """tune_grouped times candidate tables on one grouped call and returns a
+    table the library installs; products keep the oracle's bits under it."""
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    shapes = [(96, 200, 130), (300, 64, 70), (40, 40, 2000)]
+    table, report = autotune.tune_grouped(shapes, reps=1, gain=0.0)
+    assert table.shape == (16, 16) and set(np.unique(table)) <= {0, 1, 2, 3}
+    assert report["grouped"]["problems"] == 3 and report["grouped"]["rule_ms"] > 0
+    assert {k for k in report if k != "grouped"} == {"%d,%d" % (autotune._bin(m), autotune._bin(n))
+                                                    for m, n, _ in shapes}
+    dev = torch.device("cuda")
+    with hm.Handle() as h:
+        h.set_tile_table(table)
+        descs, outs = [], []
+        for i, (m, n, k) in enumerate(shapes):
+            A, B = bi.small_int(340 + i, m, k), bi.small_int(350 + i, k, n)
+            C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+            Ad, Bd = A.to(dev), B.to(dev)
+            descs.append(hm.make_desc(Ad, Bd, C))
+            outs.append((A, B, C, Ad, Bd))
+        hm.hmat_bq_gemm_grouped(h, descs, "split", 1e-12)
+        torch.cuda.synchronize()
+        for A, B, C, _, _ in outs:
+            np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+        assert h.device_error() == 0
+
+
 @pytest.mark.gpu
 def test_tuned_tables_install_and_keep_the_bits():
     if not torch.cuda.is_available():
