@@ -65,6 +65,9 @@ def parse(argv=None):
     ap.add_argument("--budget-gb", type=float, default=64.0, help="streamed: device budget in GB")
     ap.add_argument("--graph", action="store_true", help="grouped: replay a CUDA graph")
     ap.add_argument("--groups", type=int, default=512, help="grouped: the first G of the 512 problems")
+    ap.add_argument("--complex-form", choices=["auto", "gauss", "four_m"], default="auto",
+                    help="split mode, full biquaternions: complex products as Gauss's three real products, as two "
+                         "over twice the inner dimension, or the library's default (four_m for k <= 512)")
     ap.add_argument("--tile-table", default=None,
                     help="tuned tables (tile width, FP64 split-k) JSON written by the autotuner")
     ap.add_argument("--results", default=None,
@@ -106,7 +109,7 @@ def workload_config(args):
                         f"{FLAG_WORDS[flags]}, op {opA},N, C=op(A)B",
             "m": m, "n": n, "k": k, "mode": args.mode, "tol": args.tol,
             "flags": flags, "opA": opA, "row_scale": scaled, "seed": args.seed,
-            "algo": getattr(args, "algo", "bilinear"),
+            "algo": getattr(args, "algo", "bilinear"), "complex_form": getattr(args, "complex_form", "auto"),
             "l2": "inputs larger than L2 (8 x n^2 x 8 B per operand), no flush"}
 
 
@@ -213,7 +216,7 @@ def recorded_traffic(kernel_file, workload_key, record="split_residue_gemm_traff
 def run_key(args):
     """The configuration a result line belongs to (for --results resume)."""
     keys = ["impl", "workload", "n", "mode", "tol", "flags", "opA", "algo", "seed", "gpus", "no_row_scale",
-            "budget_gb", "graph", "tile_table"]
+            "budget_gb", "graph", "tile_table", "complex_form"]
     return {k: getattr(args, k, None) for k in keys}
 
 
@@ -250,28 +253,34 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def split_stage_work(hm, shapes, tol, opA="N", opB="N", fa=0xFF, fb=0xFF, algo="bilinear"):
+def split_stage_work(hm, shapes, tol, opA="N", opB="N", fa=0xFF, fb=0xFF, algo="bilinear", complex_form="auto"):
     """Algorithmic work of one split-mode step per stage, summed over (m, n, k) shapes:
     bytes for the exponent, encode and CRT stages (what each stage must read and write:
     the present FP64 components, the encoded factor tiles of the plan's nlf / nrf factors
     per modulus, the int8 residue of every product and modulus, C) and BF16 flops for the
-    residue GEMM (moduli x products x 2 m n k); "split_residue_gemm_bytes" is the least
+    residue GEMM (moduli x product terms x 2 m n k); "split_residue_gemm_bytes" is the least
     DRAM traffic of the residue GEMM (every encoded factor tile read once, every int8
-    residue written once), its bound on products too small to reuse their tiles."""
-    P, U, V, _, _ = hm.plan_info(opA, opB, fa, fb, algo=algo)
-    nlf = len({tuple(r) for r in U.tolist()})
-    nrf = len({tuple(r) for r in V.tolist()})
+    residue written once), its bound on products too small to reuse their tiles.  Full
+    biquaternion products in the four-multiplication form (complex_form "four_m", or
+    "auto" at k <= 512) count its 16 factors per side, 16 products and 32 terms."""
+    def form(a):
+        T, U, V, _, _ = hm.plan_info(opA, opB, fa, fb, algo=a)
+        P = T // 2 if a == "four_m" else T
+        return T, P, len({tuple(r) for r in U.tolist()}), len({tuple(r) for r in V.tolist()})
+    gauss = form(algo)
+    four = form("four_m") if algo == "bilinear" and fa == 0xFF and fb == 0xFF else gauss
     ca, cb = bin(fa).count("1"), bin(fb).count("1")
     w = {"split_exponents": 0.0, "split_encode": 0.0, "split_crt": 0.0, "split_residue_gemm": 0.0,
          "split_residue_gemm_bytes": 0.0}
     for m, n, k in shapes:
+        T, P, nlf, nrf = four if complex_form == "four_m" or (complex_form == "auto" and k <= 512) else gauss
         L = len(hm.split_info(k, tol)[0])
         kp = -(-k // 64) * 64
         raw = 8.0 * (ca * m * k + cb * k * n)
         w["split_exponents"] += raw
         w["split_encode"] += raw + 2.0 * L * (nlf * m + nrf * n) * kp
         w["split_crt"] += L * P * m * n + 64.0 * m * n
-        w["split_residue_gemm"] += 2.0 * L * P * m * n * k
+        w["split_residue_gemm"] += 2.0 * L * T * m * n * k
         w["split_residue_gemm_bytes"] += 2.0 * L * (nlf * m + nrf * n) * kp + L * P * m * n
     return w
 
@@ -422,6 +431,7 @@ def ours(args, rank, world, local):
     C = torch.empty((8, m, n), dtype=torch.float64, device=dev)
     h = hm.Handle()
     h.set_algorithm(args.algo)
+    h.set_complex_form(args.complex_form)
     if args.tile_table:
         from paper_2609_02081_gb300 import autotune
         h.set_tile_table(autotune.load(args.tile_table))
@@ -473,6 +483,9 @@ def ours(args, rank, world, local):
     else:
         P = hm.plan_info(args.opA, "N", fa, fb, algo=args.algo)[0]
         size, kin = 1, k
+        if (args.mode == "split" and args.algo == "bilinear" and fa == fb == 0xFF and
+                (args.complex_form == "four_m" or (args.complex_form == "auto" and k <= 512))):
+            P = hm.plan_info(args.opA, "N", fa, fb, algo="four_m")[0]   # product terms (two per product)
     mods, bits = hm.split_info(kin, args.tol)
     if rank == 0:
         rng = np.random.default_rng(args.seed + 7)
@@ -581,8 +594,8 @@ def ours(args, rank, world, local):
             roof = fp64_roofline(ach, fp64_peaks(hm), algorithmic_flops_per_launch=alg, avg_launch_ms=avg)
         stages = {k: {"launches": v[0], "ms_total": v[1]} for k, v in kernels.items() if v[0] > 0}
         if args.mode == "split" and args.algo == "bilinear":
-            stages = stage_rates(stages, split_stage_work(hm, [(m, n, k)], args.tol, args.opA, "N", fa, fb),
-                                 args.steps)
+            stages = stage_rates(stages, split_stage_work(hm, [(m, n, k)], args.tol, args.opA, "N", fa, fb,
+                                                          complex_form=args.complex_form), args.steps)
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "bf16" if args.mode == "split" else "f64", "data": "synthetic",
@@ -625,6 +638,7 @@ def grouped(args, rank, world, local):
         mats.append((A, B, C))
         descs.append(hm.make_desc(A, B, C))
     h = hm.Handle()
+    h.set_complex_form(args.complex_form)
     if args.tile_table:
         from paper_2609_02081_gb300 import autotune
         h.set_tile_table(autotune.load(args.tile_table))
@@ -678,8 +692,8 @@ def grouped(args, rank, world, local):
     launches_per_step = sum(v["launches"] for v in stages.values())
     split_shapes = [sh for i, sh in enumerate(shapes) if modes is None or modes[i] == "split"]
     if args.mode in ("split", "mixed"):
-        P = hm.plan_info("N", "N", hm.HMAT_BQ, hm.HMAT_BQ)[0]
-        gemm_flops = sum(len(hm.split_info(k, args.tol)[0]) * P * 2.0 * m * n * k for m, n, k in split_shapes)
+        gemm_flops = split_stage_work(hm, split_shapes, args.tol,
+                                      complex_form=args.complex_form)["split_residue_gemm"]
         gst = stages.get("split_residue_gemm", {"launches": 1, "ms": float("nan")})
         ach = gemm_flops / (gst["ms"] / gst["launches"] * 1e-3) / 1e12
         peaks, src = measured_peaks()
@@ -711,7 +725,7 @@ def grouped(args, rank, world, local):
                     "sample": f"the 16 sampled problems of the batch (m n k <= 2^25), {t_or:.1f} s"}
         roof_hbm = None
         if args.mode in ("split", "mixed"):
-            stages = stage_rates(stages, split_stage_work(hm, split_shapes, args.tol))
+            stages = stage_rates(stages, split_stage_work(hm, split_shapes, args.tol, complex_form=args.complex_form))
             g = stages.get("split_residue_gemm", {})
             if g.get("GB_per_s"):
                 hbm = measured_peaks()[0].get("hbm_gbs")
@@ -727,7 +741,8 @@ def grouped(args, rank, world, local):
                 "config": {"workload": f"{len(shapes)} products, m,n,k log-uniform in [32,1024] (seed 104), "
                                        f"iid U[-1,1], full biquaternions", "mode": args.mode, "graph": args.graph,
                            "tol": args.tol, "total_flops_64equiv": flops64,
-                           "tile_table": args.tile_table, "workspace_bytes": ws_bytes},
+                           "tile_table": args.tile_table, "complex_form": args.complex_form,
+                           "workspace_bytes": ws_bytes},
                 "max_rel_fro_err_16_sampled": max(errs), "clocks": clk, "stages_one_step": stages,
                 "roofline": roof, "roofline_hbm": roof_hbm, "cpu_baseline": cpu_base,
                 "gpu_launches": launches_per_step * args.steps}

@@ -124,6 +124,13 @@ typedef enum {
  * STANDARD and ISOMORPH exist for comparison with BILINEAR on the same GPU. */
 typedef enum { HMAT_ALGO_BILINEAR = 0, HMAT_ALGO_STANDARD = 1, HMAT_ALGO_ISOMORPH = 2 } hmat_algo;
 
+/* Form of the complex products in split mode (hmat_set_complex_form). */
+typedef enum { HMAT_CFORM_AUTO = 0, HMAT_CFORM_GAUSS = 1, HMAT_CFORM_FOUR_M = 2 } hmat_complex_form;
+
+/* hmat_plan_info's algo value for the split mode's four-multiplication form
+ * of the bilinear plan (not an hmat_algo: hmat_set_algorithm rejects it). */
+#define HMAT_PLAN_INFO_FOUR_M 3
+
 typedef struct hmat_context *hmat_handle;
 
 /* One product C <- alpha op(A) op(B) + beta C for the grouped call. */
@@ -310,8 +317,36 @@ int32_t hmat_last_bad_index(hmat_handle handle);
 HMAT_API
 hmat_status hmat_set_algorithm(hmat_handle handle, int32_t algo);
 
+/* Form of the complex products of split-mode products whose operands are
+ * both full biquaternions (flags 0xFF) under the BILINEAR algorithm.
+ *   HMAT_CFORM_GAUSS:  each of the eight complex products P_r of Eq.
+ *                      bilinearH as Gauss's three real products (Eq.
+ *                      cmplx-3-real-mult), as in the paper: 24 residue
+ *                      GEMMs per modulus, 24 encoded factor planes per side;
+ *   HMAT_CFORM_FOUR_M: Re P_r = Re X Re Y - Im X Im Y and
+ *                      Im P_r = Re X Im Y + Im X Re Y, each one real GEMM
+ *                      over twice the inner dimension (the second term's
+ *                      sign through the MMA's negate bit): 16 residue GEMMs
+ *                      and 16 factor planes per side, 4/3 of the
+ *                      multiplications, 2/3 of the bytes of the encoded
+ *                      planes and the product residues;
+ *   HMAT_CFORM_AUTO:   (default) FOUR_M for inner dimensions up to 512,
+ *                      where a product's two terms fit one exact FP32
+ *                      accumulation chunk of the residue GEMM, GAUSS above.
+ * Every residue is exact in both forms, so both give the same bits.
+ * Other flag pairs, FP64 mode, streamed products and
+ * hmat_bq_gemm_split_noalloc always use Gauss's form.  hmat_workspace_size
+ * and hmat_workspace_size_modes follow the setting (FOUR_M needs less).
+ * Errors: NOT_INITIALIZED, INVALID_VALUE (unknown form). */
+HMAT_API
+hmat_status hmat_set_complex_form(hmat_handle handle, int32_t form);
+
 /* The product plan of algorithm algo (BILINEAR or STANDARD) for (opA, opB,
- * flagsA, flagsB) — host only, for tests and tools.  On return
+ * flagsA, flagsB) — host only, for tests and tools.  algo
+ * HMAT_PLAN_INFO_FOUR_M gives the split mode's four-multiplication form of
+ * the BILINEAR plan (hmat_set_complex_form) as 2 P terms, term 2q + t being
+ * term t of product q (its W negated when that term is subtracted); flag
+ * pairs without that form give the BILINEAR plan.  On return
  * *n_products = P (<= 64) and, for p < P,
  *   U[p*8 + c]  in {-1,0,1}: coefficient of STORED component c of A in the
  *               left factor of real product p (op signs folded in);

@@ -37,6 +37,9 @@ HMAT_REAL, HMAT_COMPLEX, HMAT_TRS, HMAT_TRA, HMAT_BQ = 0x01, 0x11, 0x0F, 0xF0, 0
 HMAT_MODE_FP64, HMAT_MODE_SPLIT = 0, 1
 HMAT_ALGO_BILINEAR, HMAT_ALGO_STANDARD, HMAT_ALGO_ISOMORPH = 0, 1, 2
 ALGOS = {"bilinear": HMAT_ALGO_BILINEAR, "standard": HMAT_ALGO_STANDARD, "isomorph": HMAT_ALGO_ISOMORPH}
+HMAT_CFORM_AUTO, HMAT_CFORM_GAUSS, HMAT_CFORM_FOUR_M = 0, 1, 2
+CFORMS = {"auto": HMAT_CFORM_AUTO, "gauss": HMAT_CFORM_GAUSS, "four_m": HMAT_CFORM_FOUR_M}
+HMAT_PLAN_INFO_FOUR_M = 3       # plan_info only: the split mode's four-multiplication form, two terms per product
 MODES = {"fp64": HMAT_MODE_FP64, "split": HMAT_MODE_SPLIT}
 KERNEL_IDS = {"fp64_bilinear": 0, "split_exponents": 1, "split_encode": 2, "split_residue_gemm": 3,
               "split_crt": 4, "beta_scale": 5, "iso_map_in": 6, "iso_map_out": 7, "add": 8, "to_complex": 9,
@@ -90,6 +93,7 @@ SIGNATURES = {
     "hmat_plan_info": (ctypes.c_int, [_i32, _i32, _i32, _u32, _u32, ctypes.POINTER(_i32), ctypes.c_void_p,
                                       ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_set_algorithm": (ctypes.c_int, [_ptr, _i32]),
+    "hmat_set_complex_form": (ctypes.c_int, [_ptr, _i32]),
     "hmat_split_info": (ctypes.c_int, [_i64, _dbl, ctypes.POINTER(_i32), ctypes.c_void_p, ctypes.POINTER(_i32)]),
     "hmat_get_device_error": (ctypes.c_int, [_ptr, ctypes.POINTER(_u32)]),
     "hmat_set_tile_table": (ctypes.c_int, [_ptr, ctypes.c_void_p]),
@@ -154,14 +158,15 @@ def _check(status: int, what: str):
 
 # ----------------------------------------------------------------------------- host-only queries
 def plan_info(opA="N", opB="N", flagsA=HMAT_BQ, flagsB=HMAT_BQ, algo="bilinear"):
-    """(n_products, U[P,8], V[P,8], W[8,P], strategy) of the product plan (hmat_plan_info)."""
+    """(n_products, U[P,8], V[P,8], W[8,P], strategy) of the product plan (hmat_plan_info);
+    algo "four_m" lists the split mode's four-multiplication form as two terms per product."""
     L = lib()
     n = _i32()
     st = _i32()
     U = np.zeros((64, 8), dtype=np.int8)
     V = np.zeros((64, 8), dtype=np.int8)
     W = np.zeros((8, 64), dtype=np.float64)
-    a = ALGOS[algo] if isinstance(algo, str) else int(algo)
+    a = (HMAT_PLAN_INFO_FOUR_M if algo == "four_m" else ALGOS[algo]) if isinstance(algo, str) else int(algo)
     _check(L.hmat_plan_info(a, _op(opA), _op(opB), flagsA, flagsB, ctypes.byref(n), U.ctypes.data, V.ctypes.data,
                             W.ctypes.data, ctypes.byref(st)), "hmat_plan_info")
     P = n.value
@@ -245,6 +250,13 @@ class Handle:
         """'bilinear' (default), 'standard' (component-wise, HMAT-standard) or 'isomorph' (CMAT)."""
         a = ALGOS[algo] if isinstance(algo, str) else int(algo)
         _check(lib().hmat_set_algorithm(self._h, a), "hmat_set_algorithm")
+
+    def set_complex_form(self, form):
+        """Complex-product form of split-mode full-biquaternion products: 'auto' (default: the
+        four-multiplication form for k <= 512), 'gauss' (three real products, as in the paper)
+        or 'four_m' (two real products over 2 k)."""
+        f = CFORMS[form] if isinstance(form, str) else int(form)
+        _check(lib().hmat_set_complex_form(self._h, f), "hmat_set_complex_form")
 
     def set_tile_table(self, table):
         """Install a 16 x 16 tile-width code table (None: built-in rule); see autotune.py."""
@@ -626,4 +638,4 @@ __all__ = ["Handle", "HmatError", "hmat_gemm_desc", "hmat_bq_gemm", "hmat_bq_gem
            "hmat_bq_gemm_split_noalloc", "hmat_bq_gemm_streamed", "streamed_plan", "streamed_traffic", "hmat_bq_add", "hmat_bq_scale", "hmat_bq_trace", "hmat_bq_to_complex",
            "hmat_complex_to_bq", "hmat_bq_hermiticity", "hmat_bq_hadamard_block",
            "bq_gemm_host", "make_desc", "plan_info", "split_info", "lib", "library_path", "OPS", "MODES",
-           "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]
+           "CFORMS", "HMAT_REAL", "HMAT_COMPLEX", "HMAT_TRS", "HMAT_TRA", "HMAT_BQ"]

@@ -69,6 +69,7 @@ struct hmat_context {
     }
   };
   int32_t algo = HMAT_ALGO_BILINEAR;
+  int32_t cform = HMAT_CFORM_AUTO;     // complex-product form of split-mode full plans (hmat_set_complex_form)
   std::vector<GraphEntry> graphs;
   // streamed products: copy-in / copy-out streams and the slot events, created on first use
   cudaStream_t s_in = nullptr, s_out = nullptr;
@@ -108,7 +109,16 @@ struct SplitReuse {
   // FP64 mode: never split the inner dimension (the streamed blocks, so that
   // they compute exactly what the in-core product computes)
   bool fp64_whole_k = false;
+  // split mode: Gauss's three-product form whatever the handle's setting (the
+  // streamed blocks, whose workspace is planned without the handle)
+  bool gauss = false;
 };
+
+// Plan algorithm of one split-mode product: kAlgoBilinear4M for full
+// biquaternion operands under the bilinear algorithm when the form `cform`
+// (hmat_complex_form) asks for it (AUTO: inner dimension k <= kFourMMaxK),
+// else palgo.
+int split_plan_algo(int32_t cform, int palgo, uint32_t fa, uint32_t fb, int64_t k);
 
 // Validate, plan and launch `count` products on `stream_ptr` (hmat_bq_gemm and
 // hmat_bq_gemm_grouped without a graph).  modes: null (every product in

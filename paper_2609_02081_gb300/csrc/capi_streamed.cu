@@ -397,6 +397,7 @@ hmat_status streamed_impl(hmat_handle h, int32_t opA, int32_t opB, uint32_t flag
         const int64_t key[5] = {i0, k0, mb, nb, kb};
         SplitReuse reuse;
         reuse.fp64_whole_k = true;
+        reuse.gauss = true;          // the blocks' workspace was planned in Gauss's form
         reuse.a = mode == HMAT_MODE_SPLIT && need_ab && flagsA && std::equal(key, key + 5, prev);
         if (b_cache) {
           reuse.b_offset = p.ws + (j0 / p.nb) * p.b_region;

@@ -417,9 +417,15 @@ void fp64_layout(hmat_context* h, Prepared* out, unsigned char* ws, size_t ws_by
   }
 }
 
+int split_plan_algo(int32_t cform, int palgo, uint32_t fa, uint32_t fb, int64_t k) {
+  if (palgo != kAlgoBilinear || (fa & 0xFFu) != 0xFFu || (fb & 0xFFu) != 0xFFu) return palgo;
+  if (cform == HMAT_CFORM_FOUR_M || (cform == HMAT_CFORM_AUTO && k <= kFourMMaxK)) return kAlgoBilinear4M;
+  return palgo;
+}
+
 hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int32_t mode, double tol,
                     void* workspace, size_t ws_bytes, cudaStream_t stream, Prepared* out, bool allow_splitk = true,
-                    const int32_t* modes = nullptr) {
+                    const int32_t* modes = nullptr, bool gauss = false) {
   if (count < 0 || (count > 0 && !descs)) return HMAT_STATUS_INVALID_VALUE;
   if (!modes && mode != HMAT_MODE_FP64 && mode != HMAT_MODE_SPLIT) return HMAT_STATUS_INVALID_VALUE;
   for (int32_t i = 0; modes && i < count; ++i)
@@ -473,6 +479,12 @@ hmat_status prepare(hmat_context* h, int32_t count, const hmat_gemm_desc* descs,
     const int np = h->h_plans[slot].np;
     const bool trivial = (j.k == 0) || np == 0;
     if ((modes ? modes[i] : mode) == HMAT_MODE_SPLIT && !trivial) {
+      const int salgo = gauss ? palgo : split_plan_algo(h->cform, palgo, j.fa, j.fb, j.k);
+      if (salgo != palgo) {
+        st = plan_slot(h, j.fa, j.fb, salgo, stream, &slot);
+        if (st != HMAT_STATUS_SUCCESS) { h->last_bad = i; return st; }
+        j.plan = slot;
+      }
       split_jobs.push_back(j);
     } else if (np <= fp64_max_products()) {
       add_fp64_job(out, j, 0);
@@ -546,7 +558,8 @@ hmat_status run(hmat_context* h, int32_t count, const hmat_gemm_desc* descs, int
   h->last_bad = -1;
   if (reinterpret_cast<uintptr_t>(workspace) & 255u) return HMAT_STATUS_MISALIGNED;
   Prepared pr;
-  hmat_status st = prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr, !reuse.fp64_whole_k, modes);
+  hmat_status st =
+      prepare(h, count, descs, mode, tol, workspace, ws_bytes, stream, &pr, !reuse.fp64_whole_k, modes, reuse.gauss);
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (pr.has_split && pr.sp.jobs.size() == 1 && h->algo != HMAT_ALGO_ISOMORPH) {
     pr.sp.reuse_a = reuse.a;
@@ -584,11 +597,11 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
     return run(h, count, descs, mode, tol, workspace, ws_bytes, stream_ptr, SplitReuse{}, modes);
   std::lock_guard<std::mutex> lock(h->mu);
   h->last_bad = -1;
-  // key: descriptors + mode (or the per-product modes) + tol + workspace + algorithm + tile table
+  // key: descriptors + mode (or the per-product modes) + tol + workspace + algorithm + complex form + tile table
   const size_t tbl = sizeof(h->split.tile_table);
   const size_t ftbl = (size_t)h->split.n_flag_tables * (sizeof(uint16_t) + sizeof(h->split.flag_tables[0]));
   const size_t nmodes = modes ? (size_t)std::max(count, 0) : 0;
-  std::vector<unsigned char> key(sizeof(int32_t) * 3 + sizeof(double) + sizeof(void*) + sizeof(size_t) + 1 + tbl +
+  std::vector<unsigned char> key(sizeof(int32_t) * 4 + sizeof(double) + sizeof(void*) + sizeof(size_t) + 1 + tbl +
                                  sizeof(int32_t) + ftbl +
                                  (size_t)std::max(count, 0) * sizeof(hmat_gemm_desc) + nmodes * sizeof(int32_t));
   {
@@ -596,6 +609,7 @@ hmat_status run_graph(hmat_context* h, int32_t count, const hmat_gemm_desc* desc
     std::memcpy(k, &count, 4); k += 4;
     std::memcpy(k, &mode, 4); k += 4;
     std::memcpy(k, &h->algo, 4); k += 4;
+    std::memcpy(k, &h->cform, 4); k += 4;
     std::memcpy(k, &tol, 8); k += 8;
     std::memcpy(k, &workspace, sizeof(void*)); k += sizeof(void*);
     std::memcpy(k, &ws_bytes, sizeof(size_t)); k += sizeof(size_t);
@@ -892,13 +906,15 @@ hmat_status workspace_bytes(int algo, const TileTables& tables, int32_t count, c
     }
     if (fp64[i]) continue;
     KPlan p;
-    if (!build_plan(fa, fb, &p, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
-      return HMAT_STATUS_INTERNAL;
+    const int palgo = algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear;
+    // without a handle (the streamed path's planning): Gauss's form, as its blocks run
+    const int salgo = h ? split_plan_algo(h->cform, palgo, fa, fb, k) : palgo;
+    if (!build_plan(fa, fb, &p, salgo)) return HMAT_STATUS_INTERNAL;
     if (p.np == 0) {
       fp64[i] = 1;
       continue;
     }
-    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf, p.bilinear_full, fa, fb});
+    shapes.push_back({m, n, k, p.np, p.nlf, p.nrf, p.bilinear_full, fa, fb, p.four_m});
   }
   size_t split = 0;
   if (!shapes.empty()) {
@@ -1041,7 +1057,8 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   if (e == cudaSuccess)
     e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch,
                           u.max_nkb);
-  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod, u.max_np, u.all_full);
+  if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod, u.max_np, u.all_full,
+                                                u.four_m ? 1 : 0);
   return cuda_status(e);
 }
 
@@ -1053,12 +1070,39 @@ hmat_status hmat_plan_info(int32_t algo, int32_t opA, int32_t opB, uint32_t flag
                            int32_t* n_products, int8_t* U, int8_t* V, double* W, int32_t* strategy) {
   if (!n_products || opA < 0 || opA > 4 || opB < 0 || opB > 4 || flagsA > 0xFFu || flagsB > 0xFFu)
     return HMAT_STATUS_INVALID_VALUE;
-  if (algo != HMAT_ALGO_BILINEAR && algo != HMAT_ALGO_STANDARD) return HMAT_STATUS_INVALID_VALUE;
+  if (algo != HMAT_ALGO_BILINEAR && algo != HMAT_ALGO_STANDARD && algo != HMAT_PLAN_INFO_FOUR_M)
+    return HMAT_STATUS_INVALID_VALUE;
   KPlan p;
-  if (!build_plan(flagsA, flagsB, &p, algo == HMAT_ALGO_STANDARD ? kAlgoStandard : kAlgoBilinear))
-    return HMAT_STATUS_INTERNAL;
-  *n_products = p.np;
+  const int palgo = algo == HMAT_ALGO_STANDARD ? kAlgoStandard
+                    : algo == HMAT_PLAN_INFO_FOUR_M ? kAlgoBilinear4M : kAlgoBilinear;
+  if (!build_plan(flagsA, flagsB, &p, palgo)) return HMAT_STATUS_INTERNAL;
   if (strategy) *strategy = p.strategy;
+  if (p.four_m) {
+    // two terms per product: term 2q + t is term t of product q
+    *n_products = 2 * p.np;
+    for (int q = 0; q < p.np; ++q) {
+      const bool neg = ((p.neg2 >> q) & 1ull) != 0;
+      for (int t = 0; t < 2; ++t) {
+        const int r = 2 * q + t;
+        int8_t row[8];
+        if (U) {
+          factor_row(p, 0, t ? p.pl2[q] : p.pl[q], opA, row);
+          std::memcpy(U + r * 8, row, 8);
+        }
+        if (V) {
+          factor_row(p, 1, t ? p.pr2[q] : p.pr[q], opB, row);
+          std::memcpy(V + r * 8, row, 8);
+        }
+        if (W)
+          for (int e = 0; e < 8; ++e) W[e * kMaxProducts + r] = 0.25 * p.w4[e][q] * ((t && neg) ? -1.0 : 1.0);
+      }
+    }
+    if (W)
+      for (int e = 0; e < 8; ++e)
+        for (int r = 2 * p.np; r < kMaxProducts; ++r) W[e * kMaxProducts + r] = 0.0;
+    return HMAT_STATUS_SUCCESS;
+  }
+  *n_products = p.np;
   for (int q = 0; q < p.np; ++q) {
     int8_t row[8];
     if (U) {
@@ -1107,6 +1151,14 @@ hmat_status hmat_set_algorithm(hmat_handle h, int32_t algo) {
     return HMAT_STATUS_INVALID_VALUE;
   std::lock_guard<std::mutex> lock(h->mu);
   h->algo = algo;
+  return HMAT_STATUS_SUCCESS;
+}
+
+hmat_status hmat_set_complex_form(hmat_handle h, int32_t form) {
+  if (!h) return HMAT_STATUS_NOT_INITIALIZED;
+  if (form != HMAT_CFORM_AUTO && form != HMAT_CFORM_GAUSS && form != HMAT_CFORM_FOUR_M) return HMAT_STATUS_INVALID_VALUE;
+  std::lock_guard<std::mutex> lock(h->mu);
+  h->cform = form;
   return HMAT_STATUS_SUCCESS;
 }
 

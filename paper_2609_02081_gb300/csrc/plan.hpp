@@ -48,6 +48,10 @@ struct Comb8 {
 // written to a factor slot: Re = sum_e re[e] X_e, Im = sum_e im[e] X_{e+4},
 // and Re+Im (the Gauss factor).  Product p multiplies left slot pl[p] by right
 // slot pr[p]; its result enters output component e with weight w4[e][p] / 4.
+// In the four-multiplication form (four_m = 1, split mode only) every product
+// has a second term: product p is pl[p] pr[p] + s pl2[p] pr2[p], s = -1 when
+// bit p of neg2 is set, else +1 (one real GEMM over twice the inner
+// dimension).
 struct KPlan {
   int32_t np = 0;            // real products (<= kMaxProducts)
   int32_t strategy = 0;      // 0 bilinear (Eq. bilinearH + Gauss), 1 component-wise + Gauss, 2 standard
@@ -64,6 +68,11 @@ struct KPlan {
   // 1 when the products are the 24 of Eq. bilinearH with Gauss, in the order
   // (P1: T1, T2, T3), (P2: ...), ..., (P8: ...), with the paper's weights
   int32_t bilinear_full = 0;
+  // the four-multiplication form of the full plan (four_m_plan): 16 products
+  // Re P_r = Re X Re Y - Im X Im Y, Im P_r = Re X Im Y + Im X Re Y
+  int32_t four_m = 0;
+  int8_t pl2[kMaxProducts], pr2[kMaxProducts];
+  uint64_t neg2 = 0;
 };
 
 namespace detail {
@@ -324,8 +333,60 @@ inline std::vector<Product> standard_products(unsigned fa, unsigned fb) {
 
 // Algorithms: 0 = the paper's bilinear scheme (or, when cheaper for mixed
 // subalgebras, component-wise terms with Gauss's rule); 1 = the component-wise
-// ("standard") algorithm with four real products per complex term.
-enum { kAlgoBilinear = 0, kAlgoStandard = 1 };
+// ("standard") algorithm with four real products per complex term; 2 = the
+// bilinear scheme with each complex product of the full plan formed by four
+// real multiplications summed in pairs (four_m_plan; other flag pairs keep
+// algorithm 0's plan).
+enum { kAlgoBilinear = 0, kAlgoStandard = 1, kAlgoBilinear4M = 2 };
+
+// The four-multiplication form of the paper's full plan g (bilinear_full):
+// the same eight complex products P_r of Eq. bilinearH, each as two real
+// products of twice the inner dimension instead of Gauss's three (Eq.
+// cmplx-3-real-mult):
+//   product 2r:     Re P_r = Re X_r Re Y_r - Im X_r Im Y_r,
+//   product 2r + 1: Im P_r = Re X_r Im Y_r + Im X_r Re Y_r,
+// with P_r's weights w4[r][e] on output components e (real part) and e + 4
+// (imaginary part).  Factor slots: group g's Re in slot 2g, its Im in 2g + 1
+// (16 per side); no Re + Im factors.  Fewer factor and product planes (16
+// instead of 24) for 4/3 of the multiplications.
+inline bool four_m_plan(const KPlan& g, KPlan* out) {
+  if (!g.bilinear_full || g.nlg != 8 || g.nrg != 8) return false;
+  int w4t[8][4];
+  detail::CComb X[8], Y[8];
+  detail::bilinear_tables(X, Y, w4t);
+  KPlan p = g;
+  std::memset(p.pl, 0, sizeof(p.pl));
+  std::memset(p.pr, 0, sizeof(p.pr));
+  std::memset(p.pl2, 0, sizeof(p.pl2));
+  std::memset(p.pr2, 0, sizeof(p.pr2));
+  std::memset(p.w4, 0, sizeof(p.w4));
+  for (int gi = 0; gi < 8; ++gi) {
+    p.lslot[gi][0] = (int8_t)(2 * gi);
+    p.lslot[gi][1] = (int8_t)(2 * gi + 1);
+    p.lslot[gi][2] = -1;
+    p.rslot[gi][0] = (int8_t)(2 * gi);
+    p.rslot[gi][1] = (int8_t)(2 * gi + 1);
+    p.rslot[gi][2] = -1;
+  }
+  p.nlf = p.nrf = 16;
+  p.np = 16;
+  p.neg2 = 0;
+  for (int r = 0; r < 8; ++r) {
+    const int re = 2 * r, im = 2 * r + 1;
+    p.pl[re] = (int8_t)(2 * r);       p.pr[re] = (int8_t)(2 * r);         // Re X Re Y
+    p.pl2[re] = (int8_t)(2 * r + 1);  p.pr2[re] = (int8_t)(2 * r + 1);    // - Im X Im Y
+    p.neg2 |= 1ull << re;
+    p.pl[im] = (int8_t)(2 * r);       p.pr[im] = (int8_t)(2 * r + 1);     // Re X Im Y
+    p.pl2[im] = (int8_t)(2 * r + 1);  p.pr2[im] = (int8_t)(2 * r);        // + Im X Re Y
+    for (int e = 0; e < 4; ++e) {
+      p.w4[e][re] = (int8_t)w4t[r][e];
+      p.w4[e + 4][im] = (int8_t)w4t[r][e];
+    }
+  }
+  p.four_m = 1;
+  *out = p;
+  return true;
+}
 
 // Build the kernel plan for component activity flags fa (of A) and fb (of B).
 inline bool build_plan(unsigned fa, unsigned fb, KPlan* out, int algo = kAlgoBilinear) {
@@ -334,6 +395,15 @@ inline bool build_plan(unsigned fa, unsigned fb, KPlan* out, int algo = kAlgoBil
   fb &= 0xFFu;
   std::vector<Product> chosen;
   int strategy;
+  if (algo == kAlgoBilinear4M) {
+    KPlan g;
+    if (!build_plan(fa, fb, &g, kAlgoBilinear)) return false;
+    if (!g.bilinear_full) {
+      *out = g;
+      return true;
+    }
+    return four_m_plan(g, out);
+  }
   if (algo == kAlgoStandard) {
     chosen = standard_products(fa, fb);
     strategy = 2;

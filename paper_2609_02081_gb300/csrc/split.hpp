@@ -52,6 +52,10 @@ inline int crt_rows_per_block(bool all_full) { return all_full ? 1 : kCrtRows; }
 // residue sum satisfies |4Q| <= 36 * 127 = 4572, which the CRT's integer
 // residue step relies on.  Plans above it are refused.
 constexpr int kMaxWeightSum = 36;
+// Largest inner dimension for which HMAT_CFORM_AUTO takes the four-
+// multiplication form: its products (two terms of depth k) then fit one
+// 1024-deep exact chunk of the residue GEMM.
+constexpr int64_t kFourMMaxK = kChunkK / 2;
 
 struct SplitParams {
   int nmod = 0;
@@ -66,8 +70,9 @@ hmat_status split_params(int64_t k, double tol, SplitParams* out);
 struct SplitShape {
   int64_t m, n, k;
   int np, nlf, nrf;
-  int full = 0;                     // the plan is the paper's full 24-product plan (KPlan::bilinear_full)
+  int full = 0;                     // the plan is the paper's full plan (KPlan::bilinear_full), either form
   uint32_t fa = 0xFFu, fb = 0xFFu;  // component flags of op(A), op(B) (the tile table may depend on them)
+  int four_m = 0;                   // two-term products (KPlan::four_m): the GEMM runs over 2 k
 };
 
 // Split-mode tile-width tables: kTileBins x kTileBins codes (0 = built-in
@@ -93,8 +98,11 @@ struct SplitJob {
   int32_t nmod, bits, bn;           // moduli, integer width, tile N
   int32_t tiles_m, tiles_n, nkb;    // 128-row tiles, bn-column tiles, 64-wide k blocks
   int32_t np, nlf, nrf;
-  int32_t full;                     // the plan is the paper's full 24-product plan (KPlan::bilinear_full)
+  int32_t full;                     // the plan is the paper's full plan (KPlan::bilinear_full), either form
+  int32_t four_m;                   // two-term products: p is pl pr + (-1 if bit p of neg2) pl2 pr2
   int8_t pl[kMaxProducts], pr[kMaxProducts];
+  int8_t pl2[kMaxProducts], pr2[kMaxProducts];
+  uint64_t neg2;
   int64_t off_sexp, off_texp;       // int32 exponents (bytes into workspace)
   int64_t off_encA, off_encB;       // BF16 factor tiles
   int64_t off_res;                  // int8 product residues
@@ -148,7 +156,8 @@ struct SplitPrep {
   int64_t exp_units = 0, encA_units = 0, encB_units = 0, items = 0, crt_units = 0;
   int64_t ws_needed = 0;
   int max_bits = 0, max_nmod = 0, max_np = 0, max_nkb = 0;
-  bool all_full = true;             // every job uses the paper's full plan
+  bool all_full = true;             // every job uses the paper's full plan (Gauss or four-multiplication form)
+  int n_four_m = 0;                 // jobs in the four-multiplication form
   // one job whose A-side exponents and encoded factor tiles are already in the
   // workspace from the previous call with the same A block and the same shape
   bool reuse_a = false;
@@ -174,6 +183,7 @@ struct SplitUnits {
   int64_t exp = 0, encA = 0, encB = 0, items = 0, crt = 0, ws_bytes = 0;
   int max_bits = 0, max_nmod = 0, max_np = 0, max_nkb = 0;
   bool all_full = false;
+  bool four_m = false;
 };
 hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, const TileTables& tables, SplitJob* out,
                                 SplitUnits* units);
@@ -210,15 +220,19 @@ cudaError_t launch_split_exponents(const SplitJob* d_jobs, int njobs, int64_t un
 // units are blocks: encode tiles of 32 rows x 32 k, CRT blocks of 256 elements
 cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int side, int64_t units,
                                 cudaStream_t s, unsigned char* ws, int max_bits);
-// max_nkb: the most 64-deep k-blocks of any job (the one-chunk kernel form
-// serves launches whose jobs all have at most 16)
+// max_nkb: the most 64-deep k-blocks of any job's products (two-term products
+// count both terms; the one-chunk kernel form serves launches whose jobs all
+// have at most 16)
 cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, int grid, cudaStream_t s,
                               unsigned char* ws, int max_nkb);
-// all_full: every job uses the paper's full plan (structured recombination);
-// else plans of at most 24 products take the packed-weight kernel with the
-// same layout, larger ones (the component-wise comparison plan) the generic one
+// all_full: every job uses the paper's full plan (structured recombination),
+// full_form: 0 all in Gauss's form, 1 all in the four-multiplication form, 2
+// both; else plans of at most 24 products take the packed-weight kernel with
+// the same layout, larger ones (the component-wise comparison plan) the
+// generic one
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full);
+                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full,
+                             int full_form);
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const int32_t* crt_d, const uint32_t* crt_P,
                                    const uint32_t* crt_off);
 

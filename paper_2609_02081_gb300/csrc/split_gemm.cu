@@ -3,7 +3,10 @@
 // Work item = (problem, modulus l, product p, 128 x bn output tile).  For the
 // item the kernel computes T = L_f R_g^T over the padded inner dimension, where
 // L_f / R_g are the BF16-encoded residues of the plan's left / right factors
-// (values in [-128, 128]), and stores T mod p_l (centred int8).
+// (values in [-128, 128]), and stores T mod p_l (centred int8).  A two-term
+// product (the four-multiplication form of a complex product) accumulates
+// L_f R_g^T +- L_f' R_g'^T in one accumulator: the k-blocks of the second
+// term follow those of the first, its sign through the negate-B bit.
 //
 // Exactness: every BF16 product is an integer of magnitude <= 2^14 and FP32
 // partial sums of at most 1024 of them stay <= 2^24, so the tensor-memory
@@ -127,6 +130,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   d |= (uint64_t)2u << 61;                      // 128-byte swizzle
   return d;
 }
+// Instruction descriptor bit that negates the B operand (bit 14 of the
+// kind::f16 descriptor; bit 13 negates A, bits 15 / 16 select their majorness).
+constexpr uint32_t kNegateB = 1u << 14;
 // Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, M = 128, N = n.
 __device__ __forceinline__ uint32_t instr_desc(int n) {
   return (1u << 4)                      // D format F32
@@ -156,9 +162,13 @@ __device__ __forceinline__ uint32_t instr_desc(int n) {
 struct Item {
   const uint8_t* a;   // first k-block tile of the left factor
   const uint8_t* b;   // first k-block tile of the right factor
+  const uint8_t* a2;  // two-term products: the second term's factors (k-blocks kb2 .. nkb - 1)
+  const uint8_t* b2;
   int8_t* out;        // residue tile origin (row 0, column 0 of the tile)
   int64_t ncols;      // residue row pitch
-  int nkb, bn, l;
+  int nkb, bn, l;     // nkb: k-blocks of all terms
+  int kb2;            // first k-block of the second term (nkb: one term)
+  bool neg;           // the second term is subtracted
   int rows, cols;     // rows and columns of the tile inside the product (the rest is padding)
   uint32_t a_bytes, b_bytes;   // bytes copied per k-block: the 8-row groups holding those rows / columns
 };
@@ -201,7 +211,9 @@ __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int job, int64
   const int tm = (int)(grp * kRasterGroup + (within - tn32 * rows_here));
   const int tn = (int)tn32;
   Item it;
-  it.nkb = sj.nkb;
+  it.nkb = sj.four_m ? 2 * sj.nkb : sj.nkb;
+  it.kb2 = sj.four_m ? sj.nkb : it.nkb;
+  it.neg = sj.four_m && ((sj.neg2 >> p) & 1ull);
   it.bn = sj.bn;
   it.l = l;
   it.rows = min(kTileM, sj.d.m - tm * kTileM);
@@ -215,6 +227,12 @@ __device__ __forceinline__ Item decode_item(const SplitJob* jobs, int job, int64
   const int64_t b_tile = (int64_t)sj.bn * kTileK * 2;
   it.a = ws + sj.off_encA + ((int64_t)l * sj.nlf + sj.pl[p]) * sj.encA_plane + ((int64_t)tm * sj.nkb) * a_tile;
   it.b = ws + sj.off_encB + ((int64_t)l * sj.nrf + sj.pr[p]) * sj.encB_plane + ((int64_t)tn * sj.nkb) * b_tile;
+  it.a2 = it.a;
+  it.b2 = it.b;
+  if (sj.four_m) {
+    it.a2 = ws + sj.off_encA + ((int64_t)l * sj.nlf + sj.pl2[p]) * sj.encA_plane + ((int64_t)tm * sj.nkb) * a_tile;
+    it.b2 = ws + sj.off_encB + ((int64_t)l * sj.nrf + sj.pr2[p]) * sj.encB_plane + ((int64_t)tn * sj.nkb) * b_tile;
+  }
   it.ncols = (int64_t)sj.tiles_n * sj.bn;
   const int64_t plane = sj.res_plane;
   it.out = reinterpret_cast<int8_t*>(ws + sj.off_res) + ((int64_t)l * sj.np + p) * plane +
@@ -308,9 +326,11 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         for (int kb = 0; kb < it.nkb; ++kb) {
           if (!mbar_wait(smem_u32(&s.empty[stage]), phase ^ 1u, abort_flag, err, kErrWaitProducer)) { ok = false; break; }
           const uint32_t fb = smem_u32(&s.full[stage]);
+          const bool second = kb >= it.kb2;
+          const int kt = second ? kb - it.kb2 : kb;
           mbar_arrive_tx(fb, it.a_bytes + it.b_bytes);
-          bulk_g2s(smem_u32(s.a[stage]), it.a + (int64_t)kb * kATileBytes, it.a_bytes, fb);
-          bulk_g2s(smem_u32(s.b[stage]), it.b + (int64_t)kb * bstride, it.b_bytes, fb);
+          bulk_g2s(smem_u32(s.a[stage]), (second ? it.a2 : it.a) + (int64_t)kt * kATileBytes, it.a_bytes, fb);
+          bulk_g2s(smem_u32(s.b[stage]), (second ? it.b2 : it.b) + (int64_t)kt * bstride, it.b_bytes, fb);
           armed[stage] = (int)phase;
           if (++stage == kStages) { stage = 0; phase ^= 1u; }
         }
@@ -338,6 +358,8 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
         job = advance_job(jobs, njobs, item, job);
         const Item it = decode_item(jobs, job, item, ws);
         const uint32_t idesc = instr_desc(it.bn);
+        // the subtracted second term of a two-term product: negate B
+        const uint32_t idesc2 = it.neg ? (idesc | kNegateB) : idesc;
         const int nchunks = (it.nkb + kKbPerChunk - 1) / kKbPerChunk;
         for (int c = 0; ok && c < nchunks; ++c) {
           const uint32_t buf = chunk_ctr & 1u, aph = (chunk_ctr >> 1) & 1u;
@@ -350,10 +372,11 @@ split_residue_gemm_kernel(const SplitJob* __restrict__ jobs, int njobs, int64_t 
             tc_fence_after();
             const uint64_t ad = smem_desc(smem_u32(s.a[stage]));
             const uint64_t bd = smem_desc(smem_u32(s.b[stage]));
+            const uint32_t id = kb >= it.kb2 ? idesc2 : idesc;
 #pragma unroll
             for (int kk = 0; kk < kTileK / 16; ++kk) {
               // advance 16 BF16 = 32 bytes along K inside the swizzled row (+2 in 16-byte units)
-              tc_mma(d_tmem, ad + 2ull * kk, bd + 2ull * kk, idesc, (kb > kb0 || kk > 0) ? 1u : 0u);
+              tc_mma(d_tmem, ad + 2ull * kk, bd + 2ull * kk, id, (kb > kb0 || kk > 0) ? 1u : 0u);
             }
             issued = true;
             tc_commit(smem_u32(&s.empty[stage]));

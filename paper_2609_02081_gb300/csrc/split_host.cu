@@ -201,11 +201,22 @@ static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double to
   sj->nlf = sh.nlf;
   sj->nrf = sh.nrf;
   sj->full = (plan ? plan->bilinear_full != 0 : sh.full != 0) ? 1 : 0;
+  sj->four_m = (plan ? plan->four_m != 0 : sh.four_m != 0) ? 1 : 0;
   if (plan) {
+    // every factor slot a product names lies inside the job's planes
+    for (int p = 0; p < plan->np; ++p) {
+      if (plan->pl[p] < 0 || plan->pl[p] >= sh.nlf || plan->pr[p] < 0 || plan->pr[p] >= sh.nrf)
+        return HMAT_STATUS_INTERNAL;
+      if (plan->four_m && (plan->pl2[p] < 0 || plan->pl2[p] >= sh.nlf || plan->pr2[p] < 0 || plan->pr2[p] >= sh.nrf))
+        return HMAT_STATUS_INTERNAL;
+    }
     for (int p = 0; p < kMaxProducts; ++p) {
       sj->pl[p] = plan->pl[p];
       sj->pr[p] = plan->pr[p];
+      sj->pl2[p] = plan->four_m ? plan->pl2[p] : 0;
+      sj->pr2[p] = plan->four_m ? plan->pr2[p] : 0;
     }
+    sj->neg2 = plan->four_m ? plan->neg2 : 0;
   }
   // Plane strides get a skew so that the many planes a single encode / CRT
   // thread touches do not sit at power-of-two distances (which maps them onto
@@ -267,7 +278,7 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     SplitJob sj;
     std::memset(&sj, 0, sizeof(sj));
     sj.d = d;
-    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full, d.fa, d.fb};
+    SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full, d.fa, d.fb, P.four_m};
     hmat_status st = layout_job(sh, &P, tol, tables, &sj, &off);
     if (st != HMAT_STATUS_SUCCESS) return st;
     sj.exp_begin = sp.exp_units;
@@ -284,8 +295,9 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     sp.max_bits = std::max(sp.max_bits, sj.bits);
     sp.max_nmod = std::max(sp.max_nmod, sj.nmod);
     sp.max_np = std::max(sp.max_np, sj.np);
-    sp.max_nkb = std::max(sp.max_nkb, sj.nkb);
+    sp.max_nkb = std::max(sp.max_nkb, sj.four_m ? 2 * sj.nkb : sj.nkb);
     sp.all_full = sp.all_full && sj.full;
+    sp.n_four_m += sj.four_m ? 1 : 0;
     sp.jobs.push_back(sj);
   }
   // the CRT kernel, and with it the rows per block, depends on every job's plan
@@ -305,7 +317,7 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   SplitJob sj;
   std::memset(&sj, 0, sizeof(sj));
   sj.d = d;
-  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full, d.fa, d.fb};
+  SplitShape sh{d.m, d.n, d.k, P.np, P.nlf, P.nrf, P.bilinear_full, d.fa, d.fb, P.four_m};
   int64_t off = 0;
   hmat_status st = layout_job(sh, &P, tol, tables, &sj, &off);
   if (st != HMAT_STATUS_SUCCESS) return st;
@@ -318,8 +330,9 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   units->max_bits = sj.bits;
   units->max_nmod = sj.nmod;
   units->max_np = sj.np;
-  units->max_nkb = sj.nkb;
+  units->max_nkb = sj.four_m ? 2 * sj.nkb : sj.nkb;
   units->all_full = sj.full != 0;
+  units->four_m = sj.four_m != 0;
   units->ws_bytes = off;
   *out = sj;
   return HMAT_STATUS_SUCCESS;
@@ -355,7 +368,9 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
   if (e != cudaSuccess) return split_cuda_error(e);
   {
     ProfScope ps(h, 4, stream);
-    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod, sp.max_np, sp.all_full);
+    const int full_form = sp.n_four_m == 0 ? 0 : (sp.n_four_m == njobs ? 1 : 2);
+    e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod, sp.max_np, sp.all_full,
+                         full_form);
   }
   return e == cudaSuccess ? HMAT_STATUS_SUCCESS : split_cuda_error(e);
 }

@@ -715,7 +715,7 @@ __global__ void __launch_bounds__(2 * kCrtCols, L <= 4 ? 3 : 2)
     }
     cp_async_commit();
   };
-  const bool structured = sj.full != 0;     // the paper's full plan
+  const bool structured = sj.full != 0 && !sj.four_m;     // the paper's full plan in Gauss's form
   // outputs of this half with a nonzero weight (a subalgebra plan leaves some
   // components identically zero: they skip the sums and convert to +0)
   uint32_t emask = 0xFu;          // the full plan weights every output
@@ -839,8 +839,10 @@ __device__ __forceinline__ void crt_pipeline(int rows, int nm_dyn, Issue&& issue
   }
 }
 
-// CRT of the paper's full plan, for launches whose jobs all use it: the 24
-// product planes per modulus in a twelve-slot ring (36 KB) six moduli ahead,
+// CRT of the paper's full plan, for launches whose jobs all use it (in either
+// form, chosen per block by its job): the 24 (Gauss) or 16 (four-
+// multiplication form) product planes per modulus in a twelve-slot ring
+// (36 KB) six moduli ahead,
 // one barrier per three moduli, the modulus loop unrolled for the usual
 // modulus counts (13 and 14: k up to 8192 at tol 1e-12) so that the CRT
 // digits and the modulus constants are compile-time addresses, and 64
@@ -849,26 +851,33 @@ constexpr int kFullPlanes = 24;
 constexpr int kFullSlots = 12;
 constexpr int kFullGroup = 3;                   // moduli per barrier
 
+// kFourM: the four-multiplication form, 16 planes per modulus (Re P_r in
+// plane 2r, Im P_r in plane 2r + 1) instead of Gauss's 24.
 template <int L, int NM>
 __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], const unsigned char* rowbase,
                                                     int64_t plane, int cmax, int nm_dyn, int tid, int col, int half,
-                                                    uint8_t (*ring)[kFullPlanes][kCrtCols]) {
+                                                    uint8_t (*ring)[kFullPlanes][kCrtCols], bool kFourM) {
   const int nm = NM > 0 ? NM : nm_dyn;
-  // thread tid < 192 prefetches 16-byte chunk tid % 8 of plane tid / 8
+  const int kPlanes = kFourM ? 16 : kFullPlanes;
+  // thread tid < 8 kPlanes prefetches 16-byte chunk tid % 8 of plane tid / 8
   const int pc = tid >> 3, cc = tid & 7;
-  const bool has = tid < kFullPlanes * (kCrtCols / 16) && cc < cmax;
+  const bool has = tid < kPlanes * (kCrtCols / 16) && cc < cmax;
   const int64_t src0 = (int64_t)pc * plane + cc * 16;
   const int dst0 = pc * kCrtCols + cc * 16;
   auto issue = [&](int l) {
     if (l < nm && has)
-      cp_async16(&ring[l % kFullSlots][0][0] + dst0, rowbase + (int64_t)l * kFullPlanes * plane + src0);
+      cp_async16(&ring[l % kFullSlots][0][0] + dst0, rowbase + (int64_t)l * kPlanes * plane + src0);
     cp_async_commit();
   };
   auto compute = [&](int l) {
     const uint8_t(*slot)[kCrtCols] = ring[l % kFullSlots];
-    // P_r = (T1 - T2) + i (T3 - T1 - T2); 4 Q_e = +-8 P_e +- P5 +- P6 +- P7 +- P8
+    // Gauss: P_r = (T1 - T2) + i (T3 - T1 - T2); four-multiplication form:
+    // Re P_r and Im P_r themselves.  4 Q_e = +-8 P_e +- P5 +- P6 +- P7 +- P8
     int v[8];
-    if (half == 0) {
+    if (kFourM) {
+#pragma unroll
+      for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[2 * r + half][col];
+    } else if (half == 0) {
 #pragma unroll
       for (int r = 0; r < 8; ++r) v[r] = (int)(int8_t)slot[3 * r][col] - (int)(int8_t)slot[3 * r + 1][col];
     } else {
@@ -906,7 +915,8 @@ __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], cons
   }
 }
 
-template <int L>
+// kForm: 0 every job in Gauss's form, 2 each block takes its job's form
+template <int L, int kForm>
 __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const SplitJob* __restrict__ jobs, int njobs,
                                                                          unsigned char* __restrict__ ws) {
   __shared__ __align__(16) uint8_t ring[kFullSlots][kFullPlanes][kCrtCols];
@@ -932,9 +942,10 @@ __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const S
 #pragma unroll
     for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
   const int64_t pl = sj.res_plane;
-  if (L == 4 && nm == 13) crt_full_accumulate<L, 13>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
-  else if (L == 4 && nm == 14) crt_full_accumulate<L, 14>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
-  else crt_full_accumulate<L, 0>(acc, rowbase, pl, cmax, nm, tid, col, half, ring);
+  const bool four = kForm == 2 && sj.four_m != 0;   // block-uniform
+  if (L == 4 && nm == 13) crt_full_accumulate<L, 13>(acc, rowbase, pl, cmax, nm, tid, col, half, ring, four);
+  else if (L == 4 && nm == 14) crt_full_accumulate<L, 14>(acc, rowbase, pl, cmax, nm, tid, col, half, ring, four);
+  else crt_full_accumulate<L, 0>(acc, rowbase, pl, cmax, nm, tid, col, half, ring, four);
   crt_output<L>(acc, 0xFu, sj, d, ws, nm, i, j, half, col, xch);
 }
 
@@ -1126,13 +1137,22 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
 }
 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full) {
+                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full, int full_form) {
   if (units <= 0) return cudaSuccess;
   // 4 limbs hold sum_l r_l c_l < nmod * 255 * P below 2^128 (nmod <= 14)
   const unsigned grid = (unsigned)units, block = 2 * kCrtCols;
   if (all_full) {
-    if (max_nmod <= 14) split_crt_full_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
-    else split_crt_full_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    const bool l4 = max_nmod <= 14;
+    // launches with four-multiplication jobs take the per-block form also
+    // when all their jobs have it (that instantiation keeps the 64 registers
+    // without spills; the fixed four-multiplication one spills)
+    if (full_form == 0) {
+      if (l4) split_crt_full_kernel<4, 0><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      else split_crt_full_kernel<kLimbs, 0><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    } else {
+      if (l4) split_crt_full_kernel<4, 2><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      else split_crt_full_kernel<kLimbs, 2><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    }
   } else if (max_np <= kFullPlanes) {
     if (max_nmod <= 14) split_crt_plan_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
     else split_crt_plan_kernel<kLimbs><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);

@@ -91,6 +91,39 @@ def test_plan_reproduces_structure_tensor(fa, fb):
                 assert np.all(V[:, c] == 0)
 
 
+def test_four_multiplication_form_reproduces_structure_tensor():
+    """The split mode's four-multiplication form of the full plan (the eight
+    complex products of Eq. bilinearH, each as Re = Re X Re Y - Im X Im Y and
+    Im = Re X Im Y + Im X Re Y): 16 products of two terms each reproduce the
+    product for every op pair, use only Re and Im factors (no Gauss sums), 16
+    per side, and both terms of a product carry its weight (the second with
+    its sign)."""
+    for opA, opB in itertools.product(OPS, OPS):
+        P, U, V, W, strategy = hm.plan_info(opA, opB, bi.BQ, bi.BQ, algo="four_m")
+        assert P == 32 and strategy == 0
+        T = structure_tensor(opA, opB)
+        got = np.einsum("ep,pc,pd->ecd", W, U.astype(float), V.astype(float))
+        np.testing.assert_array_equal(got, T)
+        for side in (U, V):
+            for row in side:
+                assert not (np.any(row[:4]) and np.any(row[4:])), "a Gauss Re + Im factor"
+            assert len({tuple(r) for r in side}) == 16
+        for q in range(16):
+            a, b = np.abs(W[:, 2 * q]), np.abs(W[:, 2 * q + 1])
+            np.testing.assert_array_equal(a, b)
+            assert np.count_nonzero(a) in (1, 4)
+    # the same eight complex products as Gauss's plan: per output, the weights
+    # of the products (not the terms) sum to at most 12 / 4 in magnitude
+    _, _, _, W, _ = hm.plan_info("N", "N", bi.BQ, bi.BQ, algo="four_m")
+    assert np.abs(W[:, 0::2]).sum(axis=1).max() == 3.0
+    # other flag pairs keep the bilinear plan
+    for fa, fb in [(bi.TRS, bi.BQ), (bi.COMPLEX, bi.COMPLEX), (bi.BQ, bi.TRA)]:
+        four, gauss = hm.plan_info("N", "N", fa, fb, algo="four_m"), hm.plan_info("N", "N", fa, fb)
+        assert four[0] == gauss[0]
+        for x, y in zip(four[1:4], gauss[1:4]):
+            np.testing.assert_array_equal(x, y)
+
+
 def test_bilinear_24_and_reduced_counts():
     """Sec. III B: 64 -> 24 for full biquaternions, 16 -> 8 for real / imaginary quaternions."""
     counts = {(FLAG_NAME[a], FLAG_NAME[b]): hm.plan_info("N", "N", a, b)[0] for a in FLAGS for b in FLAGS}

@@ -399,6 +399,109 @@ def test_one_chunk_and_general_gemm_forms_agree(handle):
     np.testing.assert_array_equal(Cb.cpu().numpy(), oracle.bq_gemm(Ab.numpy(), Bb.numpy()))
 
 
+@pytest.fixture(scope="module")
+def gauss_handle():
+    h = hm.Handle()
+    h.set_complex_form("gauss")
+    yield h
+    h.close()
+
+
+@pytest.mark.parametrize("shape,ops,al,be", [((200, 300, 130), ("N", "N"), 1.0, 0.0),
+                                             ((129, 257, 512), ("T", "H"), 2 - 1j, 0.5 + 0.25j),
+                                             ((40, 33, 33), ("C", "QC"), -1.0, 1.0),
+                                             ((300, 200, 700), ("H", "T"), 0.5j, -0.5)])
+def test_four_multiplication_form_gives_gausss_bits(handle, gauss_handle, shape, ops, al, be):
+    """Split mode forms each complex product of the full plan either with
+    Gauss's three real products (24 residue GEMMs) or as two real products
+    over twice the inner dimension (16 residue GEMMs, the subtracted term
+    through the MMA's negate bit).  Every residue is exact, so both forms give
+    the same bits: at k <= 512 (the default takes the four-multiplication
+    form) and at k = 700 with the form forced (two 1024-deep chunks, the
+    general GEMM form); the four-multiplication workspace is smaller."""
+    dev = torch.device("cuda")
+    (m, n, k), (oa, ob) = shape, ops
+    A = bi.uniform(600 + k, *stored(oa, m, k)).to(dev)
+    B = bi.uniform(610 + k, *stored(ob, k, n)).to(dev)
+    C0 = bi.uniform(620 + k, m, n).to(dev)
+    with hm.Handle() as four:
+        four.set_complex_form("four_m")
+        outs = []
+        for h in (gauss_handle, four, handle):
+            C = C0.clone()
+            hm.hmat_bq_gemm(h, A, B, C, oa, ob, alpha=al, beta=be, mode="split", tol=TOL)
+            outs.append(C)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[1], outs[0])
+        assert torch.equal(outs[2], outs[0])
+        desc = [hm.make_desc(A, B, C0, oa, ob)]
+        ws_g = hm.hmat_workspace_size(gauss_handle, desc, "split", TOL)
+        ws_f = hm.hmat_workspace_size(four, desc, "split", TOL)
+        ws_a = hm.hmat_workspace_size(handle, desc, "split", TOL)
+        assert ws_f < ws_g
+        assert ws_a == (ws_f if k <= 512 else ws_g)
+        assert four.device_error() == 0
+    want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy(), oa, ob, alpha=al, beta=be, C=C0.cpu().numpy())
+    assert rel(outs[0].cpu().numpy(), want) < 1e-12
+
+
+def test_four_multiplication_form_exact_integers(handle):
+    """Four-multiplication form on small integers: the oracle's bits, through
+    the one-chunk GEMM form (k = 512) and, forced, the general form (k = 1100,
+    three chunks of the doubled depth), eager and grouped."""
+    dev = torch.device("cuda")
+    with hm.Handle() as four:
+        four.set_complex_form("four_m")
+        for i, (m, n, k) in enumerate([(96, 80, 512), (70, 130, 1100)]):
+            A, B = bi.small_int(640 + i, m, k), bi.small_int(650 + i, k, n)
+            for h in (handle, four):
+                C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+                hm.hmat_bq_gemm(h, A.to(dev), B.to(dev), C, mode="split", tol=TOL)
+                torch.cuda.synchronize()
+                np.testing.assert_array_equal(C.cpu().numpy(), oracle.bq_gemm(A.numpy(), B.numpy()))
+        assert four.device_error() == 0
+
+
+@pytest.mark.parametrize("use_graph,with_trs", [(False, False), (True, False), (False, True)])
+def test_grouped_mixed_complex_forms(handle, gauss_handle, use_graph, with_trs):
+    """One grouped call whose full-plan products take both forms under the
+    default (k = 64 and 512: four multiplications; k = 513 and 1000: Gauss):
+    the CRT's full-plan kernel picks each block's form; with a TRS x BQ
+    product (its own plan) beside them the packed-weight CRT kernel serves all
+    of them.  The outputs equal an all-Gauss handle's bit for bit."""
+    dev = torch.device("cuda")
+    shapes = [(130, 70, 64, bi.BQ), (64, 300, 512, bi.BQ), (200, 90, 513, bi.BQ), (33, 260, 1000, bi.BQ)]
+    if with_trs:
+        shapes.append((100, 100, 300, bi.TRS))
+    mats = []
+    for i, (m, n, k, fa) in enumerate(shapes):
+        A = bi.uniform(660 + i, m, k, flags=fa).to(dev)
+        B = bi.uniform(670 + i, k, n).to(dev)
+        mats.append((A, B, fa, (m, n)))
+    res = []
+    for h in (handle, gauss_handle):
+        Cs = [torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev) for _, _, _, (m, n) in mats]
+        descs = [hm.make_desc(A, B, C, flagsA=fa) for (A, B, fa, _), C in zip(mats, Cs)]
+        for _ in range(2 if use_graph else 1):
+            hm.hmat_bq_gemm_grouped(h, descs, mode="split", tol=TOL, stream=torch.cuda.current_stream(),
+                                    use_graph=use_graph)
+        torch.cuda.synchronize()
+        res.append(Cs)
+    for a, b in zip(*res):
+        assert torch.equal(a, b)
+    for (A, B, fa, _), C in zip(mats, res[0]):
+        want = oracle.bq_gemm(A.cpu().numpy(), B.cpu().numpy())
+        assert rel(C.cpu().numpy(), want) < 1e-12
+    assert handle.device_error() == 0
+
+
+def test_complex_form_rejects_unknown_values(handle):
+    with pytest.raises(hm.HmatError):
+        handle.set_complex_form(3)
+    with pytest.raises(hm.HmatError):
+        handle.set_algorithm(3)
+
+
 def _splitk_table(code):
     t = np.zeros((16, 16), dtype=np.int8)
     t[:, :] = code
