@@ -375,6 +375,8 @@ __global__ void __launch_bounds__(kEncThreads, 4) split_encode_kernel(const Spli
 #pragma unroll
       for (int h = 0; h < 2; ++h) v1[h] = reduced ? im[h] : fmod_c2(im[h], mc);
       put(s_slot[gi][1], v1, l);
+      // the Gauss factor Re + Im (the four-multiplication form has none)
+      if (s_slot[gi][2] < 0) return;
 #pragma unroll
       for (int h = 0; h < 2; ++h) v2[h] = fmod_c2(__fadd2_rn(v0[h], v1[h]), mc);
       put(s_slot[gi][2], v2, l);
