@@ -222,6 +222,18 @@ def test_tile_table_codes_are_validated():
     # host-only: the setter rejects codes outside 0..3 before touching the device
     L = hm.lib()
     assert L.hmat_set_tile_table(None, None) == 7     # no handle
+    assert L.hmat_set_complex_form(None, 0) == 7
+    assert L.hmat_set_algorithm(None, 0) == 7
+
+
+def test_plan_info_four_m_is_host_only_and_validated():
+    """hmat_plan_info's four-multiplication view needs no device, and the
+    form's plan value is not an algorithm the handle accepts (host checks)."""
+    P, U, V, W, _ = hm.plan_info("N", "N", bi.BQ, bi.BQ, algo="four_m")
+    assert P == 32 and U.shape == (32, 8) and W.shape == (8, 32)
+    L = hm.lib()
+    n = hm.ctypes.c_int32()
+    assert L.hmat_plan_info(4, 0, 0, 0xFF, 0xFF, hm.ctypes.byref(n), None, None, None, None) == 1   # INVALID_VALUE
 
 
 @pytest.mark.parametrize("fa,fb", list(itertools.product(FLAGS, FLAGS)))
