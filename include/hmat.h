@@ -273,9 +273,11 @@ hmat_status hmat_workspace_size_modes(hmat_handle handle, int32_t count,
  * plug-in whose host forbids cudaMalloc because it synchronises the device
  * or may fail in the middle of a real-time loop.
  *   - Capacity: hmat_split_noalloc_capacity() bytes (48 MiB), held on every
- *     GPU that loads the library until the process exits.  A product is
- *     accepted when its split workspace, as hmat_workspace_size reports it
- *     on the same handle, fits; otherwise it is rejected
+ *     GPU that loads the library until the process exits.  The call uses the
+ *     BILINEAR algorithm in the handle's complex form (hmat_set_complex_form).
+ *     A product is accepted when its split workspace, as hmat_workspace_size
+ *     reports it on the same handle with the BILINEAR algorithm, fits;
+ *     otherwise it is rejected
  *     with HMAT_STATUS_WORKSPACE_TOO_SMALL before anything is launched.  With
  *     tol = 1e-12, full biquaternions with m = n = 96 and k = 256 fit, and
  *     m = n = k = 1024 does not.
@@ -334,8 +336,8 @@ hmat_status hmat_set_algorithm(hmat_handle handle, int32_t algo);
  *                      where a product's two terms fit one exact FP32
  *                      accumulation chunk of the residue GEMM, GAUSS above.
  * Every residue is exact in both forms, so both give the same bits.
- * Other flag pairs, FP64 mode, streamed products and
- * hmat_bq_gemm_split_noalloc always use Gauss's form.  hmat_workspace_size
+ * Other flag pairs, FP64 mode and streamed products always use Gauss's
+ * form; hmat_bq_gemm_split_noalloc follows the setting.  hmat_workspace_size
  * and hmat_workspace_size_modes follow the setting (FOUR_M needs less).
  * Errors: NOT_INITIALIZED, INVALID_VALUE (unknown form). */
 HMAT_API

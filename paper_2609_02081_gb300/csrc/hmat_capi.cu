@@ -1035,7 +1035,8 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
   if (st != HMAT_STATUS_SUCCESS) return st;
   if (j.m == 0 || j.n == 0) return HMAT_STATUS_SUCCESS;
   int slot = 0;
-  st = plan_slot(h, j.fa, j.fb, kAlgoBilinear, stream, &slot);
+  // the bilinear algorithm, in the handle's complex form
+  st = plan_slot(h, j.fa, j.fb, split_plan_algo(h->cform, kAlgoBilinear, j.fa, j.fb, j.k), stream, &slot);
   if (st != HMAT_STATUS_SUCCESS) return st;
   j.plan = slot;
   // the fixed scratch serves the split pipeline only: an empty product (k == 0

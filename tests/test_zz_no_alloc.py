@@ -7,7 +7,8 @@ by keeping the split-mode workspace in a fixed array inside the library.
 
 The tests call it through the C ABI, twice in a row with different operands,
 ops and scalars, and require the same bits as the ordinary workspace-taking
-hmat_bq_gemm (both run the same deterministic kernels); on small integers,
+hmat_bq_gemm (both run the same deterministic kernels, in either complex
+form, which the entry point takes from the handle); on small integers,
 where every step is exact, the result must also equal the CPU oracle.  They
 pin the size limit the header documents and check that a product too large
 for the fixed array is refused.  This file sorts last so that a run stopping
@@ -44,7 +45,18 @@ def _noalloc(handle, A, B, C, opA, opB, fa, fb, alpha, beta):
                                         torch.cuda.current_stream().cuda_stream)
 
 
-def test_noalloc_equals_workspace_path_bit_for_bit_twice(handle):
+@pytest.mark.parametrize("form", ["auto", "gauss"])
+def test_noalloc_equals_workspace_path_bit_for_bit_twice(handle, form):
+    """Both follow the handle's complex form (the default takes the four-
+    multiplication form at this k, Gauss's form is the paper's)."""
+    handle.set_complex_form(form)
+    try:
+        _bit_for_bit(handle)
+    finally:
+        handle.set_complex_form("auto")
+
+
+def _bit_for_bit(handle):
     dev = torch.device("cuda")
     m, n, k = 96, 112, 200
     calls = [(bi.uniform(501, m, k), bi.uniform(502, k, n), "N", "N", bi.BQ, bi.BQ, 1.0, 0.0),
@@ -92,6 +104,35 @@ def test_noalloc_size_limit_is_the_workspace_size(handle):
 
     assert need(96, 96, 256) <= cap
     assert need(1024, 1024, 1024) > cap
+
+
+def test_noalloc_size_limit_follows_the_complex_form(handle):
+    """m = n = 128, k = 320 full biquaternions: the four-multiplication form's
+    workspace fits the fixed array and Gauss's form's does not, so the call
+    succeeds under the default form (with the workspace path's bits) and is
+    refused, before any launch, under Gauss's form."""
+    dev = torch.device("cuda")
+    m = n = 128
+    k = 320
+    cap = hm.lib().hmat_split_noalloc_capacity()
+    A, B = bi.uniform(520, m, k).to(dev), bi.uniform(521, k, n).to(dev)
+    C0 = bi.uniform(522, m, n).to(dev)
+    d = [hm.make_desc(A, B, C0)]
+    need_auto = hm.hmat_workspace_size(handle, d, "split", TOL)
+    with hm.Handle() as gauss:
+        gauss.set_complex_form("gauss")
+        need_gauss = hm.hmat_workspace_size(gauss, d, "split", TOL)
+        assert need_auto <= cap < need_gauss
+        got = C0.clone()
+        assert _noalloc(gauss, A, B, got, "N", "N", bi.BQ, bi.BQ, 1.0, 0.0) == 4    # WORKSPACE_TOO_SMALL
+        torch.cuda.synchronize()
+        assert torch.equal(got, C0)                                                 # nothing launched
+    ref = C0.clone()
+    hm.hmat_bq_gemm(handle, A, B, ref, mode="split", tol=TOL)
+    got = C0.clone()
+    assert _noalloc(handle, A, B, got, "N", "N", bi.BQ, bi.BQ, 1.0, 0.0) == 0
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
 
 
 def test_noalloc_refuses_products_beyond_its_scratch(handle):
