@@ -162,8 +162,9 @@ def _product_tensor():
     return T
 
 
+@pytest.mark.parametrize("form", ["auto", "four_m"])
 @pytest.mark.parametrize("tol,k", [(1e-12, 11776), (1e-13, 8900)])
-def test_split_crt_worst_case_magnitude(handle, tol, k):
+def test_split_crt_worst_case_magnitude(handle, tol, k, form):
     """Outputs at the top of the integer range the modulus count allows.
 
     Every entry of op(A) is one biquaternion a and every entry of B one b, all
@@ -174,7 +175,9 @@ def test_split_crt_worst_case_magnitude(handle, tol, k):
     b = 50 with 15 moduli, 5 limbs and 3-limb encoding), the least margin the
     modulus count leaves (|Q| / P = 0.418 and 0.419).  Every output is
     k N_e c^2 with an integer N_e, and split mode rounds the exact integer
-    once: bit-exact against the rational value.
+    once: bit-exact against the rational value.  At these k the default takes
+    Gauss's form; the four-multiplication form, forced, reaches the same
+    outputs through two-term products over 2 k (many chunks).
     """
     from fractions import Fraction
     moduli, bits = hm.split_info(k, tol)
@@ -195,11 +198,15 @@ def test_split_crt_worst_case_magnitude(handle, tol, k):
     A = torch.from_numpy(np.broadcast_to((signs[sa] * c)[:, None, None], (8, m, k)).copy()).to(dev)
     B = torch.from_numpy(np.broadcast_to((signs[sb] * c)[:, None, None], (8, k, n)).copy()).to(dev)
     want = np.array([float(Fraction(int(N[e]) * k) * Fraction(c) ** 2) for e in range(8)])
-    for sign in (1.0, -1.0):            # both signs of the extreme component
-        C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
-        hm.hmat_bq_gemm(handle, sign * A, B, C, mode="split", tol=tol)
-        torch.cuda.synchronize()
-        np.testing.assert_array_equal(C.cpu().numpy(), np.broadcast_to((sign * want)[:, None, None], (8, m, n)))
+    handle.set_complex_form(form)
+    try:
+        for sign in (1.0, -1.0):            # both signs of the extreme component
+            C = torch.full((8, m, n), float("nan"), dtype=torch.float64, device=dev)
+            hm.hmat_bq_gemm(handle, sign * A, B, C, mode="split", tol=tol)
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(C.cpu().numpy(), np.broadcast_to((sign * want)[:, None, None], (8, m, n)))
+    finally:
+        handle.set_complex_form("auto")
 
 
 def test_strided_views(handle):
