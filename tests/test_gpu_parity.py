@@ -744,3 +744,56 @@ def test_two_threads_two_handles_concurrently():
     for t in range(2):
         A, B = cases[t]
         np.testing.assert_array_equal(results[t], oracle.bq_gemm(A.numpy(), B.numpy()))
+
+
+def _random_cases(seed, count):
+    """Seeded random products: ragged m, n, k in [1, 300] (some k just above and
+    below the four-multiplication limit 512), op pairs, subalgebra flags (full
+    biquaternions twice as often), small-integer complex alpha and beta."""
+    import random
+    rng = random.Random(seed)
+    flag_choices = FLAGS + [bi.BQ, bi.BQ]
+    cases = []
+    for i in range(count):
+        m, n = rng.randint(1, 300), rng.randint(1, 300)
+        k = rng.choice([rng.randint(1, 300), rng.randint(505, 520)])
+        opA, opB = rng.choice(OPS), rng.choice(OPS)
+        fa, fb = rng.choice(flag_choices), rng.choice(flag_choices)
+        alpha = complex(rng.randint(-3, 3), rng.randint(-3, 3)) or 1.0
+        beta = complex(rng.randint(-2, 2), rng.randint(-2, 2))
+        cases.append((m, n, k, opA, opB, fa, fb, alpha, beta))
+    return cases
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_random_products_exact_in_both_forms(handle, gauss_handle, seed):
+    """24 seeded random products on small integers (every step exact): split
+    mode in the default form (the four-multiplication form for full
+    biquaternions with k <= 512) and in Gauss's form, and FP64 mode, each call
+    alone, equal the oracle bit for bit; the same products in one grouped
+    split-mode call, eager and replayed from a graph, give the same bits."""
+    dev = torch.device("cuda")
+    cases = _random_cases(seed, 24)
+    prods = []
+    for i, (m, n, k, opA, opB, fa, fb, alpha, beta) in enumerate(cases):
+        A = bi.small_int(9000 + 10 * seed + 3 * i, *stored(opA, m, k), flags=fa)
+        B = bi.small_int(9001 + 10 * seed + 3 * i, *stored(opB, k, n), flags=fb)
+        C0 = bi.small_int(9002 + 10 * seed + 3 * i, m, n)
+        want = oracle.bq_gemm(A.numpy(), B.numpy(), opA, opB, alpha=alpha, beta=beta, C=C0.numpy())
+        for h, mode in ((handle, "split"), (gauss_handle, "split"), (handle, "fp64")):
+            got = run(h, A, B, opA, opB, fa, fb, alpha=alpha, beta=beta, C0=C0, mode=mode)
+            np.testing.assert_array_equal(got, want, err_msg=f"case {i} {cases[i]} {mode}")
+        prods.append((A.to(dev), B.to(dev), C0.to(dev), want, cases[i]))
+    for use_graph in (False, True):
+        Cs = [p[2].clone() for p in prods]
+        descs = [hm.make_desc(p[0], p[1], C, p[4][3], p[4][4], p[4][5], p[4][6], alpha=p[4][7], beta=p[4][8])
+                 for p, C in zip(prods, Cs)]
+        for _ in range(2 if use_graph else 1):
+            for C, p in zip(Cs, prods):
+                C.copy_(p[2])
+            hm.hmat_bq_gemm_grouped(handle, descs, "split", TOL, stream=torch.cuda.current_stream(),
+                                    use_graph=use_graph)
+        torch.cuda.synchronize()
+        for C, p in zip(Cs, prods):
+            np.testing.assert_array_equal(C.cpu().numpy(), p[3], err_msg=f"grouped {p[4]}")
+    assert handle.device_error() == 0 and gauss_handle.device_error() == 0
