@@ -1059,7 +1059,7 @@ hmat_status hmat_bq_gemm_split_noalloc(hmat_handle h, int32_t opA, int32_t opB, 
     e = launch_split_gemm(a.job, 1, u.items, (int)std::min<int64_t>(u.items, h->sm_count), stream, a.scratch,
                           u.max_nkb);
   if (e == cudaSuccess) e = launch_split_crt(a.job, 1, h->d_plans, u.crt, stream, a.scratch, u.max_nmod, u.max_np, u.all_full,
-                                                u.four_m ? 1 : 0);
+                                                u.four_m ? 1 : 0, sj.crt_w == kCrtCols);
   return cuda_status(e);
 }
 

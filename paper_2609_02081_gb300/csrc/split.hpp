@@ -43,10 +43,13 @@ constexpr int kTileK = 64;         // BF16 elements per 128-byte swizzled row
 constexpr int kChunkK = 1024;      // inner steps per exact FP32 accumulation chunk
 constexpr int kTileBins = 16;      // tile-width table: bins of ceil(log2 m) x ceil(log2 n)
 constexpr int kCrtCols = 128;      // CRT output columns per block (two threads per element)
-// CRT output rows per block: one for the full-plan kernel (launches whose
-// jobs all use the paper's full plan), kCrtRows for the others
+// CRT output rows per block: kCrtRows for the plan and generic kernels; the
+// full-plan kernel (launches whose jobs all use the paper's full plan) takes
+// kCrtCols / crt_width(n) rows of crt_width(n) columns: one row of 128 for
+// wide products, four rows of 32 for narrower ones, whose ragged column
+// blocks would leave threads idle
 constexpr int kCrtRows = 4;
-inline int crt_rows_per_block(bool all_full) { return all_full ? 1 : kCrtRows; }
+inline int crt_width(int64_t n) { return n >= 1024 ? kCrtCols : 32; }
 // Largest sum_p |w4[e][p]| of a plan (the paper's full plan: 8 + 4 x 1 on the
 // three Gauss terms); with centred product residues |T| <= 127 every output
 // residue sum satisfies |4Q| <= 36 * 127 = 4572, which the CRT's integer
@@ -100,6 +103,7 @@ struct SplitJob {
   int32_t np, nlf, nrf;
   int32_t full;                     // the plan is the paper's full plan (KPlan::bilinear_full), either form
   int32_t four_m;                   // two-term products: p is pl pr + (-1 if bit p of neg2) pl2 pr2
+  int32_t crt_w;                    // full-plan CRT: columns per block row (kCrtCols / crt_w rows)
   int8_t pl[kMaxProducts], pr[kMaxProducts];
   int8_t pl2[kMaxProducts], pr2[kMaxProducts];
   uint64_t neg2;
@@ -158,6 +162,7 @@ struct SplitPrep {
   int max_bits = 0, max_nmod = 0, max_np = 0, max_nkb = 0;
   bool all_full = true;             // every job uses the paper's full plan (Gauss or four-multiplication form)
   int n_four_m = 0;                 // jobs in the four-multiplication form
+  bool all_wide = true;             // every job's full-plan CRT blocks are one row of kCrtCols columns
   // one job whose A-side exponents and encoded factor tiles are already in the
   // workspace from the previous call with the same A block and the same shape
   bool reuse_a = false;
@@ -227,12 +232,13 @@ cudaError_t launch_split_gemm(const SplitJob* d_jobs, int njobs, int64_t items, 
                               unsigned char* ws, int max_nkb);
 // all_full: every job uses the paper's full plan (structured recombination),
 // full_form: 0 all in Gauss's form, 1 all in the four-multiplication form, 2
-// both; else plans of at most 24 products take the packed-weight kernel with
+// both; all_wide: every job's full-plan CRT blocks are one row of kCrtCols
+// columns; else plans of at most 24 products take the packed-weight kernel with
 // the same layout, larger ones (the component-wise comparison plan) the
 // generic one
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
                              cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full,
-                             int full_form);
+                             int full_form, bool all_wide);
 cudaError_t split_upload_constants(const int* moduli, int nmod_table, const int32_t* crt_d, const uint32_t* crt_P,
                                    const uint32_t* crt_off);
 

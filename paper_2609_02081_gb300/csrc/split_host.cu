@@ -177,6 +177,18 @@ static inline int64_t enc_blocks(int64_t rows, int64_t nkb) { return ((rows + 15
 static inline int64_t crt_blocks(int64_t m, int64_t n, int rows) {
   return ((m + rows - 1) / rows) * ((n + kCrtCols - 1) / kCrtCols);
 }
+// CRT blocks of a job and its block width: the full-plan kernel's blocks are
+// kCrtCols / crt_width(n) rows of crt_width(n) columns, the other kernels'
+// kCrtRows rows of kCrtCols columns
+static inline int64_t crt_job_blocks(SplitJob& sj, bool all_full) {
+  if (!all_full) {
+    sj.crt_w = kCrtCols;
+    return crt_blocks(sj.d.m, sj.d.n, kCrtRows);
+  }
+  sj.crt_w = crt_width(sj.d.n);
+  const int64_t rows = kCrtCols / sj.crt_w;
+  return ((sj.d.m + rows - 1) / rows) * ((sj.d.n + sj.crt_w - 1) / sj.crt_w);
+}
 
 // Fill the layout fields of sj (everything except the JobDesc and the unit prefixes).
 static hmat_status layout_job(const SplitShape& sh, const KPlan* plan, double tol, const TileTables& tables, SplitJob* sj,
@@ -300,11 +312,11 @@ hmat_status split_prepare(const std::vector<JobDesc>& jobs, const KPlan* h_plans
     sp.n_four_m += sj.four_m ? 1 : 0;
     sp.jobs.push_back(sj);
   }
-  // the CRT kernel, and with it the rows per block, depends on every job's plan
-  const int crt_rows = crt_rows_per_block(sp.all_full);
+  // the CRT kernel, and with it the block shape, depends on every job's plan
   for (SplitJob& sj : sp.jobs) {
     sj.crt_begin = sp.crt_units;
-    sp.crt_units += crt_blocks(sj.d.m, sj.d.n, crt_rows);
+    sp.crt_units += crt_job_blocks(sj, sp.all_full);
+    sp.all_wide = sp.all_wide && sj.crt_w == kCrtCols;
   }
   if ((size_t)off > ws_bytes) return HMAT_STATUS_WORKSPACE_TOO_SMALL;
   sp.ws_needed = off;
@@ -326,7 +338,7 @@ hmat_status split_layout_single(const JobDesc& d, const KPlan& P, double tol, co
   units->encB = enc_blocks(d.n, sj.nkb);
   units->items = (int64_t)sj.nmod * sj.np * sj.tiles_m * sj.tiles_n;
   if (units->items >= ((int64_t)1 << 31)) return HMAT_STATUS_UNSUPPORTED;
-  units->crt = crt_blocks(d.m, d.n, crt_rows_per_block(sj.full != 0));
+  units->crt = crt_job_blocks(sj, sj.full != 0);
   units->max_bits = sj.bits;
   units->max_nmod = sj.nmod;
   units->max_np = sj.np;
@@ -370,7 +382,7 @@ hmat_status split_launch(hmat_context* h, const SplitPrep& sp, const SplitJob* d
     ProfScope ps(h, 4, stream);
     const int full_form = sp.n_four_m == 0 ? 0 : (sp.n_four_m == njobs ? 1 : 2);
     e = launch_split_crt(d_jobs, njobs, d_plans, sp.crt_units, stream, ws, sp.max_nmod, sp.max_np, sp.all_full,
-                         full_form);
+                         full_form, sp.all_wide);
   }
   return e == cudaSuccess ? HMAT_STATUS_SUCCESS : split_cuda_error(e);
 }

@@ -571,7 +571,7 @@ template <int L>
 __device__ __forceinline__ void crt_output(const long long (&acc)[4][L], uint32_t emask, const SplitJob& sj,
                                            const JobDesc& d, const unsigned char* ws, int nm, int i, int j, int half,
                                            int col, double (*xch)[kCrtCols]) {
-  const bool valid = j < d.n;
+  const bool valid = i < d.m && j < d.n;
   double q4v[4] = {0.0, 0.0, 0.0, 0.0};
   if (valid) {
     const int s_i = reinterpret_cast<const int32_t*>(ws + sj.off_sexp)[i];
@@ -855,16 +855,19 @@ constexpr int kFullGroup = 3;                   // moduli per barrier
 
 // kFourM: the four-multiplication form, 16 planes per modulus (Re P_r in
 // plane 2r, Im P_r in plane 2r + 1) instead of Gauss's 24.
+// Thread tid < 8 planes prefetches 16-byte chunk tid % 8 of plane tid / 8 of
+// the block's residue rows: chunk_off is that chunk's byte offset from rowbase
+// inside a plane, chunk_ok whether it lies inside the product.
 template <int L, int NM>
 __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], const unsigned char* rowbase,
-                                                    int64_t plane, int cmax, int nm_dyn, int tid, int col, int half,
+                                                    int64_t plane, int64_t chunk_off, bool chunk_ok, int nm_dyn,
+                                                    int tid, int col, int half,
                                                     uint8_t (*ring)[kFullPlanes][kCrtCols], bool kFourM) {
   const int nm = NM > 0 ? NM : nm_dyn;
   const int kPlanes = kFourM ? 16 : kFullPlanes;
-  // thread tid < 8 kPlanes prefetches 16-byte chunk tid % 8 of plane tid / 8
   const int pc = tid >> 3, cc = tid & 7;
-  const bool has = tid < kPlanes * (kCrtCols / 16) && cc < cmax;
-  const int64_t src0 = (int64_t)pc * plane + cc * 16;
+  const bool has = tid < kPlanes * (kCrtCols / 16) && chunk_ok;
+  const int64_t src0 = (int64_t)pc * plane + chunk_off;
   const int dst0 = pc * kCrtCols + cc * 16;
   auto issue = [&](int l) {
     if (l < nm && has)
@@ -917,8 +920,10 @@ __device__ __forceinline__ void crt_full_accumulate(long long (&acc)[4][L], cons
   }
 }
 
-// kForm: 0 every job in Gauss's form, 2 each block takes its job's form
-template <int L, int kForm>
+// kForm: 0 every job in Gauss's form, 2 each block takes its job's form;
+// kWide: every job's blocks are one row of kCrtCols columns (else each job's
+// crt_w gives its block shape)
+template <int L, int kForm, bool kWide>
 __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const SplitJob* __restrict__ jobs, int njobs,
                                                                          unsigned char* __restrict__ ws) {
   __shared__ __align__(16) uint8_t ring[kFullSlots][kFullPlanes][kCrtCols];
@@ -929,15 +934,20 @@ __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const S
   const int nm = sj.nmod;
   const int tid = threadIdx.x;
   const int col = tid % kCrtCols, half = tid / kCrtCols;
+  // the block: kCrtCols / w rows of w columns (w = 128 for wide products, 32
+  // for narrower ones); byte col of a ring row is column col % w of row col / w
+  const int w = kWide ? kCrtCols : sj.crt_w;
   const int64_t local = blk - sj.crt_begin;
-  const int colblocks = (d.n + kCrtCols - 1) / kCrtCols;
-  const int i = (int)(local / colblocks);
+  const int colblocks = (d.n + w - 1) / w;
+  const int i0 = (int)(local / colblocks) * (kCrtCols / w);
   const int jb = (int)(local % colblocks);
-  const int j = jb * kCrtCols + col;
   const int64_t ncols = (int64_t)sj.tiles_n * sj.bn;
-  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i * ncols + (int64_t)jb * kCrtCols;
-  const int64_t cavail = (ncols - (int64_t)jb * kCrtCols) / 16;
-  const int cmax = cavail < kCrtCols / 16 ? (int)cavail : kCrtCols / 16;
+  const unsigned char* rowbase = ws + sj.off_res + (int64_t)i0 * ncols + (int64_t)jb * w;
+  // this thread's copy chunk: row cc / (w / 16), 16 bytes at column (cc % (w / 16)) * 16
+  const int cc = tid & 7, cw = w / 16;
+  const int crow = cc / cw, ccol = (cc % cw) * 16;
+  const int64_t chunk_off = (int64_t)crow * ncols + ccol;
+  const bool chunk_ok = i0 + crow < d.m && (int64_t)jb * w + ccol < ncols;
   long long acc[4][L];
 #pragma unroll
   for (int e = 0; e < 4; ++e)
@@ -945,10 +955,24 @@ __global__ void __launch_bounds__(2 * kCrtCols, 4) split_crt_full_kernel(const S
     for (int q = 0; q < L; ++q) acc[e][q] = (long long)c_off[nm][q];
   const int64_t pl = sj.res_plane;
   const bool four = kForm == 2 && sj.four_m != 0;   // block-uniform
-  if (L == 4 && nm == 13) crt_full_accumulate<L, 13>(acc, rowbase, pl, cmax, nm, tid, col, half, ring, four);
-  else if (L == 4 && nm == 14) crt_full_accumulate<L, 14>(acc, rowbase, pl, cmax, nm, tid, col, half, ring, four);
-  else crt_full_accumulate<L, 0>(acc, rowbase, pl, cmax, nm, tid, col, half, ring, four);
-  crt_output<L>(acc, 0xFu, sj, d, ws, nm, i, j, half, col, xch);
+  if (L == 4 && nm == 13)
+    crt_full_accumulate<L, 13>(acc, rowbase, pl, chunk_off, chunk_ok, nm, tid, col, half, ring, four);
+  else if (L == 4 && nm == 14)
+    crt_full_accumulate<L, 14>(acc, rowbase, pl, chunk_off, chunk_ok, nm, tid, col, half, ring, four);
+  else
+    crt_full_accumulate<L, 0>(acc, rowbase, pl, chunk_off, chunk_ok, nm, tid, col, half, ring, four);
+  if constexpr (kWide) {
+    crt_output<L>(acc, 0xFu, sj, d, ws, nm, i0, jb * kCrtCols + col, half, col, xch);
+  } else {
+    // the element of this thread, derived again here (fewer values live
+    // across the sums)
+    const int ww = sj.crt_w;
+    const int64_t loc = blk - sj.crt_begin;
+    const int cb = (d.n + ww - 1) / ww;
+    const int i = (int)(loc / cb) * (kCrtCols / ww) + col / ww;
+    const int j = (int)(loc % cb) * ww + col % ww;
+    crt_output<L>(acc, 0xFu, sj, d, ws, nm, i, j, half, col, xch);
+  }
 }
 
 // CRT of any plan of at most 24 products (the subalgebra plans, and grouped
@@ -1139,7 +1163,8 @@ cudaError_t launch_split_encode(const SplitJob* d_jobs, int njobs, const KPlan* 
 }
 
 cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_plans, int64_t units,
-                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full, int full_form) {
+                             cudaStream_t s, unsigned char* ws, int max_nmod, int max_np, bool all_full, int full_form,
+                             bool all_wide) {
   if (units <= 0) return cudaSuccess;
   // 4 limbs hold sum_l r_l c_l < nmod * 255 * P below 2^128 (nmod <= 14)
   const unsigned grid = (unsigned)units, block = 2 * kCrtCols;
@@ -1148,12 +1173,18 @@ cudaError_t launch_split_crt(const SplitJob* d_jobs, int njobs, const KPlan* d_p
     // launches with four-multiplication jobs take the per-block form also
     // when all their jobs have it (that instantiation keeps the 64 registers
     // without spills; the fixed four-multiplication one spills)
-    if (full_form == 0) {
-      if (l4) split_crt_full_kernel<4, 0><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
-      else split_crt_full_kernel<kLimbs, 0><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    if (full_form == 0 && all_wide) {
+      if (l4) split_crt_full_kernel<4, 0, true><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      else split_crt_full_kernel<kLimbs, 0, true><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    } else if (full_form == 0) {
+      if (l4) split_crt_full_kernel<4, 0, false><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      else split_crt_full_kernel<kLimbs, 0, false><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+    } else if (all_wide) {
+      if (l4) split_crt_full_kernel<4, 2, true><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      else split_crt_full_kernel<kLimbs, 2, true><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
     } else {
-      if (l4) split_crt_full_kernel<4, 2><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
-      else split_crt_full_kernel<kLimbs, 2><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      if (l4) split_crt_full_kernel<4, 2, false><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
+      else split_crt_full_kernel<kLimbs, 2, false><<<grid, block, 0, s>>>(d_jobs, njobs, ws);
     }
   } else if (max_np <= kFullPlanes) {
     if (max_nmod <= 14) split_crt_plan_kernel<4><<<grid, block, 0, s>>>(d_jobs, njobs, d_plans, ws);
